@@ -1,0 +1,250 @@
+/*
+ * psweep.h — C ABI of the GB300 fisheye plane-sweep + TSDF fusion library
+ * (libpsweep.so).
+ *
+ * The library computes the data-parallel hot path of "Real-Time Dense Mapping
+ * for Self-Driving Vehicles using Fisheye Cameras" (Cui et al.):
+ *   - multi-scale fisheye plane-sweep stereo with a windowed ZNCC cost
+ *     (Sec. III-A: plane sweeping, fronto-parallel and ground-parallel plane
+ *     sets, ZNCC matching cost, multi-scale strategy),
+ *   - masking of dynamic-object boxes in the depth map (Sec. III overview,
+ *     Sec. III-B),
+ *   - TSDF fusion of fisheye depth maps into voxel blocks (Sec. III-C,
+ *     Eq. 1 back-projection, Eq. 2 running average, local map).
+ *
+ * Conventions (all entry points):
+ *   - Pixel centres sit at integer coordinates; images are row-major with
+ *     u = column, v = row; the camera frame is x right, y down, z forward.
+ *   - Intensities are uint8; the method works on I / 255.
+ *   - Depth is the range along the pixel's unit viewing ray (|X|), float32,
+ *     with 0 meaning "no depth".
+ *   - A pose {R, t} maps source to destination coordinates,
+ *     X_dst = R X_src + t, R row-major.
+ *   - Pointers documented "device" must point to memory of the current CUDA
+ *     device; "host" pointers are ordinary CPU memory.  The caller owns every
+ *     buffer it passes; the library owns its handles' scratch memory, which
+ *     is allocated only in *_create and freed only in *_destroy.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls documented "asynchronous" only enqueue work on it.
+ *   - Every int-returning call returns a PS_* status.  On a non-zero status
+ *     ps_last_error() gives a message for the calling thread.  Device-side
+ *     failures (hash table or block pool full, bounded probe gave up) are
+ *     latched in the handle and reported by the next synchronising call
+ *     (tsdf_status, tsdf_extract, tsdf_count).  No call traps the device.
+ */
+#ifndef PSWEEP_H
+#define PSWEEP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PS_OK 0
+#define PS_ERR_ARG 1        /* invalid argument: null pointer, bad size, unsupported option */
+#define PS_ERR_OOM 2        /* device or host allocation failed in *_create */
+#define PS_ERR_CAPACITY 3   /* TSDF hash table or voxel-block pool is full */
+#define PS_ERR_CUDA 4       /* a CUDA runtime call failed */
+#define PS_ERR_TIMEOUT 5    /* a bounded device loop (hash probing) gave up */
+
+/* Unified omnidirectional camera (Sec. III-C, Eq. 1, after Mei) with
+ * radial-tangential distortion of the normalised coordinates:
+ *   x_d = x (1 + k1 r^2 + k2 r^4) + 2 p1 x y + p2 (r^2 + 2 x^2)
+ *   y_d = y (1 + k1 r^2 + k2 r^4) + p1 (r^2 + 2 y^2) + 2 p2 x y,
+ *   u = fx x_d + cx, v = fy y_d + cy.
+ * r2_max bounds x^2 + y^2 of accepted undistorted coordinates (keeps the
+ * polynomial one-to-one); a point projects only where its unit-sphere z
+ * exceeds -min(xi, 1/xi). */
+typedef struct {
+    double xi, fx, fy, cx, cy, k1, k2, p1, p2, r2_max;
+    int32_t width, height;
+} ps_camera;
+
+typedef struct {
+    double R[9];
+    double t[3];
+} ps_pose;
+
+#define PS_PLANES_FRONTO 0  /* n = (0,0,1); inverse depth uniform on [1/b, 1/a], index 0 farthest */
+#define PS_PLANES_GROUND 1  /* n . X = h, h uniform on [a, b], index 0 at h = a; n = ground normal */
+
+/* One set of sweep planes (Sec. III-A: one set parallel to the reference
+ * image plane, one set parallel to the ground from the extrinsic
+ * calibration). */
+typedef struct {
+    int32_t family;
+    int32_t count;          /* >= 1 */
+    double a, b;            /* fronto: near, far (m); ground: lowest, highest offset (m) */
+    double n[3];            /* ground normal in the reference frame (normalised by the library) */
+} ps_plane_set;
+
+#define PS_LEVEL_DOWNSAMPLE 0  /* all images box-averaged by `factor` */
+#define PS_LEVEL_CROP 1        /* centred crop_w x crop_h window of the reference at full
+                                  resolution, matched against full-resolution matching images */
+#define PS_MAX_SETS 4
+#define PS_MAX_CAMS 4
+#define PS_MAX_LEVELS 2
+
+/* One resolution level of the multi-scale strategy (Sec. III-A). */
+typedef struct {
+    int32_t kind;
+    int32_t factor;         /* DOWNSAMPLE: 1, 2 or 4 (image sizes must divide) */
+    int32_t crop_w, crop_h; /* CROP: window size; offset ((W - crop_w)/2, (H - crop_h)/2) */
+    int32_t window;         /* side of the square ZNCC window: 5, 7 or 9 */
+    int32_t n_sets;         /* 1 .. PS_MAX_SETS */
+    ps_plane_set sets[PS_MAX_SETS];
+} ps_level;
+
+typedef struct {
+    ps_camera ref;                 /* reference camera at full resolution */
+    int32_t n_cams;                /* matching cameras, 1 .. PS_MAX_CAMS */
+    const ps_camera* cams;         /* host, n_cams entries */
+    const ps_pose* ref_to_cam;     /* host, n_cams entries: X_cam = R X_ref + t */
+    int32_t n_levels;              /* 1 .. PS_MAX_LEVELS: at most one DOWNSAMPLE and one CROP */
+    const ps_level* levels;        /* host */
+} ps_sweep_desc;
+
+/* Half-open pixel rectangle [x0, x1) x [y0, y1) in full-resolution
+ * reference pixels: a dynamic-object detection (Sec. III-B). */
+typedef struct {
+    int32_t x0, y0, x1, y1;
+} ps_box;
+
+/* Optional per-level outputs, each a device array of the level's size
+ * (DOWNSAMPLE: (H/factor) x (W/factor); CROP: crop_h x crop_w), any may be
+ * NULL.  best_cost / second_cost: lowest and second-lowest aggregated cost
+ * over the planes (+inf where none); plane_idx: winning plane (-1 = none);
+ * depth: the level's range map before merging. */
+typedef struct {
+    float* depth;
+    float* best_cost;
+    float* second_cost;
+    int32_t* plane_idx;
+} ps_level_out;
+
+typedef struct psweep_s psweep_t;
+typedef struct tsdf_s tsdf_t;
+
+/* Validate the rig and levels, build the per-level ray tables (Eq. 1 per
+ * reference pixel), plane tables and scratch images.  The only sweep call
+ * that allocates.  On success *out receives the handle; on failure *out is
+ * NULL and the status says why (PS_ERR_ARG, PS_ERR_OOM, PS_ERR_CUDA). */
+int psweep_create(const ps_sweep_desc* desc, psweep_t** out);
+
+/* Depth map of the reference camera for one synchronised frame (Sec. III-A):
+ * per level, warp each matching image through every plane, ZNCC cost over
+ * the window, minimum over matching cameras, winner-take-all with parabolic
+ * sub-plane refinement; then merge the levels at full resolution (crop depth
+ * where valid, else the downsampled level's depth at (u/factor, v/factor))
+ * and zero the pixels inside the boxes.
+ *   images    host array of 1 + n_cams device pointers: [0] reference, then
+ *             the matching cameras, each a contiguous uint8 H x W image of
+ *             its camera's full-resolution size.
+ *   boxes     host array of n_boxes boxes (may be NULL when n_boxes == 0).
+ *   depth_out device float32 H x W (reference full resolution).
+ *   level_out host array of n_levels entries or NULL.
+ * Asynchronous on `stream`; allocates nothing. */
+int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_box* boxes, int32_t n_boxes,
+                 float* depth_out, const ps_level_out* level_out, void* stream);
+
+void psweep_destroy(psweep_t* h);
+
+/* TSDF volume (Sec. III-C).  Voxels hold {D, w}: D in [-1, 1] is the
+ * truncated signed distance normalised by mu (positive in front of
+ * surfaces), w the number of fused observations capped at w_max.
+ * Blocks are 8^3 voxels.  dense_dim != 0 gives a fixed grid of
+ * dense_dim[0] x dense_dim[1] x dense_dim[2] voxels (multiples of 8) at
+ * `origin`; otherwise blocks are allocated on demand in a hash table of
+ * hash_slots (power of two) slots backed by a pool of pool_blocks blocks,
+ * keyed by block index floor((X - origin) / (8 voxel_size)).  local_half
+ * != 0 restricts allocation to blocks whose centre lies within
+ * local_half of the local-map centre passed to tsdf_integrate. */
+typedef struct {
+    ps_camera cam;            /* camera of the fused depth maps (full resolution) */
+    double voxel_size;
+    double mu;
+    double w_max;
+    int32_t block_dim;        /* must be 8 */
+    int32_t dense_dim[3];
+    double origin[3];
+    double local_half[3];
+    int64_t hash_slots;
+    int64_t pool_blocks;
+} ps_tsdf_desc;
+
+/* Allocates the voxel pool (zeroed), hash table and per-frame scratch and
+ * builds the depth camera's ray table (Eq. 1 per pixel). */
+int tsdf_create(const ps_tsdf_desc* desc, tsdf_t** out);
+
+/* Fuse one depth map (Sec. III-C): allocate the blocks crossed by the
+ * segment [d - mu, d + mu] (starting no closer than the camera centre)
+ * along every valid pixel's ray, inside the local map; list the allocated
+ * blocks a pixel of this frame can update; apply Eq. 2 to their voxels:
+ * with eta = d(nearest pixel of the voxel's projection) - |X_d|, voxels with
+ * eta >= -mu get D <- (w D + min(1, eta/mu)) / (w + 1), w <- min(w + 1, w_max).
+ *   depth         device float32 H x W range map of the desc's camera (0 = no depth).
+ *   world_to_cam  host, pose of the camera for this frame.
+ *   local_center  host double[3] or NULL (required when local_half != 0).
+ * Asynchronous on `stream`; allocates nothing.  A full hash table or pool
+ * is latched (PS_ERR_CAPACITY) and the affected blocks are skipped. */
+int tsdf_integrate(tsdf_t* t, const float* depth, const ps_pose* world_to_cam, const double* local_center,
+                   void* stream);
+
+/* Synchronises `stream`; *n_blocks = number of allocated blocks.  Returns
+ * the latched device status (then clears it). */
+int tsdf_count(tsdf_t* t, int64_t* n_blocks, void* stream);
+
+/* Synchronises `stream` and copies out every allocated block, in pool
+ * order: keys (device int32, capacity x 3 block indices), D and W (device
+ * float32, capacity x 512 voxels each, voxel index x + 8 y + 64 z).
+ * Voxels with w < min_weight are reported with W = 0 and D = 0 (Sec. III-C:
+ * only voxels with at least 3 observations are kept; pass 0 for all).
+ * *n_out = number of blocks written (min(count, capacity)).  Returns the
+ * latched device status, or PS_ERR_CAPACITY if capacity < count. */
+int tsdf_extract(tsdf_t* t, float min_weight, int32_t* keys, float* D, float* W, int64_t capacity,
+                 int64_t* n_out, void* stream);
+
+/* Synchronises `stream`, returns and clears the latched device status. */
+int tsdf_status(tsdf_t* t, void* stream);
+
+void tsdf_destroy(tsdf_t* t);
+
+/* One frame end to end from host memory: copy the 1 + n_cams host images
+ * (uint8, pinned memory gives asynchronous copies) to library-owned device
+ * buffers, run psweep_depth, fuse the depth map with tsdf_integrate (t may
+ * be NULL to skip fusion; its camera must be the reference camera) at pose
+ * world_to_ref, and
+ * copy the full-resolution depth map back to host_depth_out (float32 H x W,
+ * may be NULL).  Synchronises `stream` before returning. */
+int psweep_frame_host(psweep_t* h, tsdf_t* t, const uint8_t* const* host_images, const ps_box* boxes,
+                      int32_t n_boxes, const ps_pose* world_to_ref, const double* local_center,
+                      float* host_depth_out, void* stream);
+
+/* Stage timing for measurement tools.  psweep_profile(h, capacity) with
+ * capacity > 0 creates 2 x stages x capacity CUDA events (this allocates:
+ * call it outside timed or captured regions) and makes the next `capacity`
+ * psweep_depth calls record events around their stages on their stream:
+ * stage 0 level preparation (downsampling, quad images), stage 1 the sweep
+ * kernel, stage 2 the merge.  capacity 0 turns recording off and frees the
+ * events.  psweep_profile_read synchronises those events and returns the
+ * summed milliseconds per stage (host double[3]) and the number of calls
+ * recorded, then restarts the count.  tsdf_profile / tsdf_profile_read do
+ * the same for tsdf_integrate with 4 stages: 0 depth maximum, 1 block
+ * allocation, 2 visible-block list, 3 integration. */
+int psweep_profile(psweep_t* h, int32_t capacity);
+int psweep_profile_read(psweep_t* h, double* stage_ms, int32_t* n_calls);
+int tsdf_profile(tsdf_t* t, int32_t capacity);
+int tsdf_profile_read(tsdf_t* t, double* stage_ms, int32_t* n_calls);
+
+/* Message for the calling thread's last non-zero status ("" if none). */
+const char* ps_last_error(void);
+
+/* Library version string. */
+const char* ps_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSWEEP_H */

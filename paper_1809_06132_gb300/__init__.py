@@ -1,0 +1,9 @@
+"""GB300-native fisheye plane-sweep stereo and TSDF fusion (Cui et al.,
+"Real-Time Dense Mapping for Self-Driving Vehicles using Fisheye Cameras").
+
+The compute path is libpsweep.so (hand-written sm_103a CUDA kernels behind
+the C ABI in include/psweep.h); this package is its thin Python binding.
+"""
+from .psweep import (EXPORTS, PsError, Sweep, Tsdf, load, lib_path, version,  # noqa: F401
+                     PS_OK, PS_ERR_ARG, PS_ERR_OOM, PS_ERR_CAPACITY, PS_ERR_CUDA, PS_ERR_TIMEOUT)
+from ._build import build  # noqa: F401

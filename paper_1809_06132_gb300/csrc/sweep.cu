@@ -1,0 +1,904 @@
+// Fisheye plane-sweep stereo at multiple scales (Sec. III-A) on sm_103a.
+//
+// Kernels:
+//   ray_table_kernel   Eq. 1 back-projection of every reference pixel of a
+//                      level, in double precision, stored as float4 (once
+//                      per rig, at psweep_create).
+//   ref_level_kernel   reference image of a level (s x s box mean, or the
+//                      centred crop), centred intensities I/255 - 1/2.
+//   quad_level_kernel  matching image of a level in "quad" layout: entry
+//                      (x, y) holds the 2 x 2 neighbourhood used by one
+//                      bilinear sample, so a sample is one 16-byte gather.
+//   sweep_kernel       the hot loop.  One CTA owns a TW x TH tile of output
+//                      pixels of one level and walks every plane and every
+//                      matching camera: warp the tile + window halo through
+//                      the plane into shared memory, box-sum w, w^2, r w and
+//                      the invalid count with separable sums, ZNCC -> cost,
+//                      minimum over cameras, and a streaming winner-take-all
+//                      that keeps the best, second best and the winner's two
+//                      neighbours in registers.  The cost volume never
+//                      leaves the SM.  Both levels' tiles share one launch.
+//   merge_kernel       full-resolution merge of the levels and box masks.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace ps {
+
+namespace {
+
+constexpr int TW = 64;   // output tile width (pixels)
+constexpr int TH = 16;   // output tile height
+constexpr int NT = 256;  // threads per CTA: one thread per 4-pixel run of a tile row
+static_assert(NT == (TW / 4) * TH, "one thread per 4-pixel output run");
+
+struct PlaneD {
+    float nx, ny, nz, d;  // plane n . X = d (reference frame)
+};
+
+struct SetD {
+    int family, start, count;
+    float a, b;
+    float nx, ny, nz;
+};
+
+struct CamJ {
+    float R[9], t[3];  // reference -> matching camera
+    CamF cam;          // intrinsics at this level
+    const float4* quad;
+};
+
+struct LevelD {
+    int W, H, rho;
+    int n_planes, n_sets;
+    SetD sets[PS_MAX_SETS];
+    const PlaneD* planes;
+    const float4* rays;  // (rx, ry, rz, 0), NaN where the pixel has no ray
+    const float* ref;    // centred intensities
+    int n_cams;
+    CamJ cams[PS_MAX_CAMS];
+    int tiles_x, tiles_y, tile_begin;
+    float* depth;
+    float* c1;
+    float* c2;
+    int32_t* kstar;
+};
+
+struct SweepParams {
+    int n_levels;
+    LevelD lv[PS_MAX_LEVELS];
+};
+
+// ------------------------------------------------------------- ray table
+
+__device__ void distort_d(const ps_camera& c, double x, double y, double* xd, double* yd) {
+    double r2 = x * x + y * y;
+    double rad = 1.0 + c.k1 * r2 + c.k2 * r2 * r2;
+    *xd = x * rad + 2.0 * c.p1 * x * y + c.p2 * (r2 + 2.0 * x * x);
+    *yd = y * rad + c.p1 * (r2 + 2.0 * y * y) + 2.0 * c.p2 * x * y;
+}
+
+// Unit ray of pixel (u, v) by Eq. 1, undistorting first by Newton
+// iteration (residual < 1e-13 within 100 steps, else no ray).  Returns false
+// where the pixel has no ray.
+__device__ bool ray_of(const ps_camera& c, double u, double v, double r[3]) {
+    double xd = (u - c.cx) / c.fx, yd = (v - c.cy) / c.fy;
+    double X = xd, Y = yd;
+    bool ok = false;
+    for (int it = 0; it < 100; ++it) {
+        double fx, fy;
+        distort_d(c, X, Y, &fx, &fy);
+        double ex = fx - xd, ey = fy - yd;
+        if (fabs(ex) < 1e-13 && fabs(ey) < 1e-13) {
+            ok = true;
+            break;
+        }
+        double r2 = X * X + Y * Y;
+        double rad = 1.0 + c.k1 * r2 + c.k2 * r2 * r2;
+        double dr = c.k1 + 2.0 * c.k2 * r2;
+        double a = rad + 2.0 * X * X * dr + 2.0 * c.p1 * Y + 6.0 * c.p2 * X;
+        double b = 2.0 * X * Y * dr + 2.0 * c.p1 * X + 2.0 * c.p2 * Y;
+        double d = rad + 2.0 * Y * Y * dr + 6.0 * c.p1 * Y + 2.0 * c.p2 * X;
+        double det = a * d - b * b;
+        if (det == 0.0) break;
+        X -= (d * ex - b * ey) / det;
+        Y -= (a * ey - b * ex) / det;
+    }
+    if (!ok) return false;
+    double s = X * X + Y * Y;
+    double disc = 1.0 + (1.0 - c.xi * c.xi) * s;
+    if (s > c.r2_max || disc < 0.0) return false;
+    double f = (c.xi + sqrt(disc)) / (s + 1.0);
+    r[0] = f * X;
+    r[1] = f * Y;
+    r[2] = f - c.xi;
+    return true;
+}
+
+// Per-pixel rays of a camera, float4 (x, y, z, 0) with NaN where there is none.
+__global__ void ray_table_kernel(ps_camera c, int W, int H, float4* rays) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y;
+    if (x >= W || y >= H) return;
+    const float nan = __int_as_float(0x7fc00000);
+    double r[3];
+    float4 out = make_float4(nan, nan, nan, 0.f);
+    if (ray_of(c, x, y, r)) out = make_float4((float)r[0], (float)r[1], (float)r[2], 0.f);
+    rays[(size_t)y * W + x] = out;
+}
+
+// Widest polar angle of a ray through the image, taken on the border of the
+// image grown by one pixel (the polar angle grows with the distance from the
+// principal point under a one-to-one distortion); a border point without a
+// ray counts as pi.  Result: float bits in *out (atomicMax on positive floats).
+__global__ void view_angle_kernel(ps_camera c, int W, int H, unsigned* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int per_row = W + 2, per_col = H;
+    int n = 2 * per_row + 2 * per_col;
+    if (i >= n) return;
+    double u, v;
+    if (i < per_row) {
+        u = i - 1;
+        v = -1;
+    } else if (i < 2 * per_row) {
+        u = i - per_row - 1;
+        v = H;
+    } else if (i < 2 * per_row + per_col) {
+        u = -1;
+        v = i - 2 * per_row;
+    } else {
+        u = W;
+        v = i - 2 * per_row - per_col;
+    }
+    double r[3];
+    float ang = 3.14159266f;
+    if (ray_of(c, u, v, r)) ang = (float)acos(fmin(1.0, fmax(-1.0, r[2])));
+    atomicMax(out, __float_as_uint(ang));
+}
+
+// ------------------------------------------------------------- level images
+
+// Centred intensity of the s x s block at level pixel (x, y), clamped to the image.
+__device__ __forceinline__ float level_px(const uint8_t* img, int W, int Wl, int Hl, int s, int x, int y) {
+    x = min(x, Wl - 1);
+    y = min(y, Hl - 1);
+    int acc = 0;
+    for (int dy = 0; dy < s; ++dy)
+        for (int dx = 0; dx < s; ++dx) acc += img[(size_t)(s * y + dy) * W + (s * x + dx)];
+    return (float)acc * (1.0f / (255.0f * s * s)) - 0.5f;
+}
+
+__global__ void ref_level_kernel(const uint8_t* img, int W, int s, int x0, int y0, int Wl, int Hl, float* out) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y;
+    if (x >= Wl || y >= Hl) return;
+    float v;
+    if (s > 0)
+        v = level_px(img, W, Wl, Hl, s, x, y);
+    else
+        v = img[(size_t)(y0 + y) * W + (x0 + x)] * (1.0f / 255.0f) - 0.5f;
+    out[(size_t)y * Wl + x] = v;
+}
+
+__global__ void quad_level_kernel(const uint8_t* img, int W, int s, int Wl, int Hl, float4* out) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y;
+    if (x >= Wl || y >= Hl) return;
+    float4 q;
+    q.x = level_px(img, W, Wl, Hl, s, x, y);
+    q.y = level_px(img, W, Wl, Hl, s, x + 1, y);
+    q.z = level_px(img, W, Wl, Hl, s, x, y + 1);
+    q.w = level_px(img, W, Wl, Hl, s, x + 1, y + 1);
+    out[(size_t)y * Wl + x] = q;
+}
+
+// ------------------------------------------------------------- sweep
+
+// Bilinear sample of matching camera j at the projection of X_j (camera
+// frame); NaN when the point does not project (sphere side, distortion
+// range) or lands outside [0, W-1] x [0, H-1].
+__device__ __forceinline__ float warp_sample(const CamJ& C, float X, float Y, float Z) {
+    const CamF& c = C.cam;
+    float n = sqrtf(fmaf(X, X, fmaf(Y, Y, Z * Z)));
+    float den = fmaf(c.xi, n, Z);
+    float inv = 1.0f / den;
+    float mx = X * inv, my = Y * inv;
+    float r2 = fmaf(mx, mx, my * my);
+    float rad = fmaf(r2, fmaf(c.k2, r2, c.k1), 1.0f);
+    float mxy = mx * my;
+    float xd = fmaf(mx, rad, fmaf(2.0f * c.p1, mxy, c.p2 * fmaf(2.0f * mx, mx, r2)));
+    float yd = fmaf(my, rad, fmaf(c.p1, fmaf(2.0f * my, my, r2), 2.0f * c.p2 * mxy));
+    float u = fmaf(c.fx, xd, c.cx);
+    float v = fmaf(c.fy, yd, c.cy);
+    bool ok = (Z > c.lim * n) && (r2 <= c.r2_max) && (u >= 0.0f) && (u <= (float)(c.width - 1)) &&
+              (v >= 0.0f) && (v <= (float)(c.height - 1));
+    if (!ok) return __int_as_float(0x7fc00000);
+    int x0 = (int)u, y0 = (int)v;
+    float ax = u - (float)x0, ay = v - (float)y0;
+    float4 q = __ldg(&C.quad[(size_t)y0 * c.width + x0]);
+    float top = fmaf(ax, q.y - q.x, q.x);
+    float bot = fmaf(ax, q.w - q.z, q.z);
+    return fmaf(ay, bot - top, top);
+}
+
+template <int RHO>
+struct Tile {
+    static constexpr int HWL = TW + 2 * RHO;          // logical halo width
+    static constexpr int HW = (HWL + 3) & ~3;         // padded row stride (float4 rows)
+    static constexpr int HH = TH + 2 * RHO;
+    static constexpr int NPOS = HH * HWL;
+    static constexpr int N = (2 * RHO + 1) * (2 * RHO + 1);
+    static constexpr int NV = (4 + 2 * RHO + 3) / 4;  // float4 loads per 4-output run
+    static constexpr size_t smem_bytes =
+        sizeof(float) * 2 * HH * HW + sizeof(float4) * (4 * HH * (TW / 4) + NPOS);
+};
+
+template <int RHO>
+__device__ void sweep_tile(const LevelD& L, int tile, unsigned char* smem_raw) {
+    using T = Tile<RHO>;
+    constexpr int HW = T::HW, HH = T::HH, HWL = T::HWL, NPOS = T::NPOS, N = T::N;
+    float* Rs = reinterpret_cast<float*>(smem_raw);
+    float* Ws = Rs + HH * HW;
+    float4* Hs = reinterpret_cast<float4*>(Ws + HH * HW);  // [4][HH][TW/4]
+    float4* Ray = Hs + 4 * HH * (TW / 4);                  // [NPOS]
+    const int tid = threadIdx.x;
+    const int tx = tile % L.tiles_x, ty = tile / L.tiles_x;
+    const int gx0 = tx * TW - RHO, gy0 = ty * TH - RHO;  // halo origin in level pixels
+    const float nan = __int_as_float(0x7fc00000);
+    const float inf = __int_as_float(0x7f800000);
+
+    for (int p = tid; p < NPOS; p += NT) {
+        int hy = p / HWL, hx = p - hy * HWL;
+        int gx = gx0 + hx, gy = gy0 + hy;
+        bool in = gx >= 0 && gy >= 0 && gx < L.W && gy < L.H;
+        Rs[hy * HW + hx] = in ? L.ref[(size_t)gy * L.W + gx] : 0.0f;
+        Ray[p] = in ? L.rays[(size_t)gy * L.W + gx] : make_float4(nan, nan, nan, 0.f);
+    }
+    __syncthreads();
+
+    // this thread's outputs: run c (4 pixels) of tile row oy
+    const int c = tid % (TW / 4), oy = tid / (TW / 4);
+    float mu_r[4], var_r[4];
+    bool ovalid[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int gx = tx * TW + 4 * c + i, gy = ty * TH + oy;
+        float s = 0.f;
+        for (int dy = 0; dy <= 2 * RHO; ++dy)
+            for (int dx = 0; dx <= 2 * RHO; ++dx) s += Rs[(oy + dy) * HW + 4 * c + i + dx];
+        float m = s / (float)N;
+        float v = 0.f;
+        for (int dy = 0; dy <= 2 * RHO; ++dy)
+            for (int dx = 0; dx <= 2 * RHO; ++dx) {
+                float e = Rs[(oy + dy) * HW + 4 * c + i + dx] - m;
+                v = fmaf(e, e, v);
+            }
+        mu_r[i] = m;
+        var_r[i] = v;
+        ovalid[i] = gx >= RHO && gy >= RHO && gx < L.W - RHO && gy < L.H - RHO && v >= (float)N * 1e-8f;
+    }
+
+    // streaming winner-take-all state
+    float c1[4], c2[4], cprev[4], cminus[4], cplus[4];
+    int kb[4];
+    bool needp[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        c1[i] = c2[i] = cprev[i] = cminus[i] = cplus[i] = inf;
+        kb[i] = -1;
+        needp[i] = false;
+    }
+
+    for (int s = 0; s < L.n_sets; ++s) {
+        const SetD S = L.sets[s];
+        for (int p = tid; p < NPOS; p += NT) {
+            float4 r = Ray[p];
+            float nr = S.nx * r.x + S.ny * r.y + S.nz * r.z;
+            Ray[p].w = nr > 0.0f ? 1.0f / nr : nan;
+        }
+        __syncthreads();
+        for (int k = S.start; k < S.start + S.count; ++k) {
+            const float d = L.planes[k].d;
+            float cmin[4] = {inf, inf, inf, inf};
+            for (int j = 0; j < L.n_cams; ++j) {
+                const CamJ& C = L.cams[j];
+                // phase A: warped samples of the tile + halo
+                for (int p = tid; p < NPOS; p += NT) {
+                    float4 r = Ray[p];
+                    float lam = d * r.w;
+                    float X = lam * r.x, Y = lam * r.y, Z = lam * r.z;
+                    float Xj = fmaf(C.R[0], X, fmaf(C.R[1], Y, fmaf(C.R[2], Z, C.t[0])));
+                    float Yj = fmaf(C.R[3], X, fmaf(C.R[4], Y, fmaf(C.R[5], Z, C.t[1])));
+                    float Zj = fmaf(C.R[6], X, fmaf(C.R[7], Y, fmaf(C.R[8], Z, C.t[2])));
+                    int hy = p / HWL, hx = p - hy * HWL;
+                    Ws[hy * HW + hx] = warp_sample(C, Xj, Yj, Zj);
+                }
+                __syncthreads();
+                // phase H: horizontal window sums of w, w^2, r w, invalid count per 4-pixel run
+                for (int it = tid; it < HH * (TW / 4); it += NT) {
+                    int hy = it / (TW / 4), cc = it - hy * (TW / 4);
+                    float wv[4 * T::NV], rv[4 * T::NV];
+#pragma unroll
+                    for (int q = 0; q < T::NV; ++q) {
+                        float4 a = *reinterpret_cast<const float4*>(&Ws[hy * HW + 4 * cc + 4 * q]);
+                        float4 b = *reinterpret_cast<const float4*>(&Rs[hy * HW + 4 * cc + 4 * q]);
+                        wv[4 * q] = a.x; wv[4 * q + 1] = a.y; wv[4 * q + 2] = a.z; wv[4 * q + 3] = a.w;
+                        rv[4 * q] = b.x; rv[4 * q + 1] = b.y; rv[4 * q + 2] = b.z; rv[4 * q + 3] = b.w;
+                    }
+                    float m[4 + 2 * RHO];
+#pragma unroll
+                    for (int q = 0; q < 4 + 2 * RHO; ++q) {
+                        bool bad = isnan(wv[q]);
+                        m[q] = bad ? 1.0f : 0.0f;
+                        wv[q] = bad ? 0.0f : wv[q];
+                    }
+                    float hw[4], hww[4], hrw[4], hm[4];
+#pragma unroll
+                    for (int o = 0; o < 4; ++o) {
+                        float a = 0.f, b = 0.f, e = 0.f, f = 0.f;
+#pragma unroll
+                        for (int q = 0; q <= 2 * RHO; ++q) {
+                            float w = wv[o + q];
+                            a += w;
+                            b = fmaf(w, w, b);
+                            e = fmaf(rv[o + q], w, e);
+                            f += m[o + q];
+                        }
+                        hw[o] = a;
+                        hww[o] = b;
+                        hrw[o] = e;
+                        hm[o] = f;
+                    }
+                    const int base = hy * (TW / 4) + cc;
+                    Hs[base] = make_float4(hw[0], hw[1], hw[2], hw[3]);
+                    Hs[HH * (TW / 4) + base] = make_float4(hww[0], hww[1], hww[2], hww[3]);
+                    Hs[2 * HH * (TW / 4) + base] = make_float4(hrw[0], hrw[1], hrw[2], hrw[3]);
+                    Hs[3 * HH * (TW / 4) + base] = make_float4(hm[0], hm[1], hm[2], hm[3]);
+                }
+                __syncthreads();
+                // phase V: vertical sums, ZNCC, cost, minimum over cameras
+                float4 sw = make_float4(0, 0, 0, 0), sww = sw, srw = sw, sm = sw;
+#pragma unroll
+                for (int dy = 0; dy <= 2 * RHO; ++dy) {
+                    const int base = (oy + dy) * (TW / 4) + c;
+                    float4 a = Hs[base], b = Hs[HH * (TW / 4) + base], e = Hs[2 * HH * (TW / 4) + base],
+                           f = Hs[3 * HH * (TW / 4) + base];
+                    sw.x += a.x; sw.y += a.y; sw.z += a.z; sw.w += a.w;
+                    sww.x += b.x; sww.y += b.y; sww.z += b.z; sww.w += b.w;
+                    srw.x += e.x; srw.y += e.y; srw.z += e.z; srw.w += e.w;
+                    sm.x += f.x; sm.y += f.y; sm.z += f.z; sm.w += f.w;
+                }
+                const float vw[4] = {sw.x, sw.y, sw.z, sw.w}, vww[4] = {sww.x, sww.y, sww.z, sww.w},
+                            vrw[4] = {srw.x, srw.y, srw.z, srw.w}, vm[4] = {sm.x, sm.y, sm.z, sm.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float var_w = vww[i] - vw[i] * vw[i] * (1.0f / (float)N);
+                    float cov = vrw[i] - mu_r[i] * vw[i];
+                    bool ok = ovalid[i] && vm[i] == 0.0f && var_w >= (float)N * 1e-8f;
+                    float z = cov * rsqrtf(var_r[i] * var_w);
+                    float cost = fmaf(-0.5f, z, 0.5f);
+                    if (ok) cmin[i] = fminf(cmin[i], cost);
+                }
+            }
+            // winner-take-all update with the plane's aggregated cost
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float cc = cmin[i];
+                if (needp[i]) {
+                    cplus[i] = cc;
+                    needp[i] = false;
+                }
+                if (cc < c1[i]) {
+                    c2[i] = c1[i];
+                    c1[i] = cc;
+                    kb[i] = k;
+                    cminus[i] = cprev[i];
+                    cplus[i] = inf;
+                    needp[i] = true;
+                } else if (cc < c2[i]) {
+                    c2[i] = cc;
+                }
+                cprev[i] = cc;
+            }
+        }
+        __syncthreads();
+    }
+
+    // parabola through the winner and its neighbours in the same set; range
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int gx = tx * TW + 4 * c + i, gy = ty * TH + oy;
+        if (gx >= L.W || gy >= L.H) continue;
+        size_t o = (size_t)gy * L.W + gx;
+        float depth = 0.f;
+        if (kb[i] >= 0) {
+            int s = 0;
+            while (s + 1 < L.n_sets && L.sets[s + 1].start <= kb[i]) ++s;
+            const SetD S = L.sets[s];
+            int li = kb[i] - S.start;
+            float delta = 0.f;
+            if (li > 0 && li < S.count - 1 && cminus[i] < inf && cplus[i] < inf) {
+                float den = cminus[i] - 2.0f * c1[i] + cplus[i];
+                if (den > 0.f) delta = fminf(0.5f, fmaxf(-0.5f, (cminus[i] - cplus[i]) / (2.0f * den)));
+            }
+            float t = S.count > 1 ? ((float)li + delta) / (float)(S.count - 1) : 0.f;
+            float param = S.family == PS_PLANES_FRONTO ? 1.0f / fmaf(t, 1.0f / S.a - 1.0f / S.b, 1.0f / S.b)
+                                                       : fmaf(t, S.b - S.a, S.a);
+            float4 r = L.rays[o];
+            float nr = S.nx * r.x + S.ny * r.y + S.nz * r.z;
+            depth = param / nr;
+        }
+        if (L.depth) L.depth[o] = depth;
+        if (L.c1) L.c1[o] = c1[i];
+        if (L.c2) L.c2[o] = c2[i];
+        if (L.kstar) L.kstar[o] = kb[i];
+    }
+}
+
+__global__ void __launch_bounds__(NT) sweep_kernel(const __grid_constant__ SweepParams P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int b = blockIdx.x;
+    int l = 0;
+    while (l + 1 < P.n_levels && b >= P.lv[l + 1].tile_begin) ++l;
+    const LevelD& L = P.lv[l];
+    int tile = b - L.tile_begin;
+    switch (L.rho) {
+        case 2: sweep_tile<2>(L, tile, smem); break;
+        case 3: sweep_tile<3>(L, tile, smem); break;
+        default: sweep_tile<4>(L, tile, smem); break;
+    }
+}
+
+// ------------------------------------------------------------- merge
+
+struct MergeP {
+    int W, H;
+    const float* low;
+    int s, Wl, Hl;
+    const float* crop;
+    int cx0, cy0, cw, ch;
+    int n_boxes;
+    ps_box boxes[16];
+    const ps_box* boxes_dev;  // when n_boxes > 16
+};
+
+__global__ void merge_kernel(const __grid_constant__ MergeP P, const ps_box* boxes, float* out) {
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    int v = blockIdx.y;
+    if (u >= P.W || v >= P.H) return;
+    float val = 0.f;
+    if (P.low) val = P.low[(size_t)min(v / P.s, P.Hl - 1) * P.Wl + min(u / P.s, P.Wl - 1)];
+    if (P.crop && u >= P.cx0 && u < P.cx0 + P.cw && v >= P.cy0 && v < P.cy0 + P.ch) {
+        float c = P.crop[(size_t)(v - P.cy0) * P.cw + (u - P.cx0)];
+        if (c > 0.f) val = c;
+    }
+    for (int b = 0; b < P.n_boxes; ++b) {
+        ps_box bx = b < 16 ? P.boxes[b] : boxes[b];
+        if (u >= bx.x0 && u < bx.x1 && v >= bx.y0 && v < bx.y1) val = 0.f;
+    }
+    out[(size_t)v * P.W + u] = val;
+}
+
+}  // namespace
+
+// ===================================================================== host
+
+int build_rays(const ps_camera& cam, float4* rays, double* max_angle) {
+    const int W = cam.width, H = cam.height;
+    ray_table_kernel<<<dim3((W + 127) / 128, H), 128>>>(cam, W, H, rays);
+    PS_CUDA(cudaGetLastError());
+    if (max_angle) {
+        unsigned* bits = nullptr;
+        PS_CUDA(cudaMalloc(&bits, sizeof(unsigned)));
+        cudaMemset(bits, 0, sizeof(unsigned));
+        int n = 2 * (W + 2) + 2 * H;
+        view_angle_kernel<<<(n + 255) / 256, 256>>>(cam, W, H, bits);
+        unsigned hb = 0;
+        cudaError_t e = cudaMemcpy(&hb, bits, sizeof(unsigned), cudaMemcpyDeviceToHost);
+        cudaFree(bits);
+        if (e != cudaSuccess) return cuda_fail(e, "view angle");
+        float a;
+        std::memcpy(&a, &hb, sizeof(a));
+        *max_angle = a;
+    }
+    return PS_OK;
+}
+
+CamF to_camf(const ps_camera& c) {
+    CamF f;
+    f.xi = (float)c.xi;
+    f.fx = (float)c.fx;
+    f.fy = (float)c.fy;
+    f.cx = (float)c.cx;
+    f.cy = (float)c.cy;
+    f.k1 = (float)c.k1;
+    f.k2 = (float)c.k2;
+    f.p1 = (float)c.p1;
+    f.p2 = (float)c.p2;
+    f.r2_max = c.r2_max > 3.0e38 ? 3.0e38f : (float)c.r2_max;
+    double lim = c.xi > 0 ? std::min(c.xi, 1.0 / c.xi) : 0.0;
+    f.lim = (float)(-lim);
+    f.width = c.width;
+    f.height = c.height;
+    return f;
+}
+
+}  // namespace ps
+
+using namespace ps;
+
+struct psweep_s {
+    ps_camera ref;
+    int n_cams;
+    ps_camera cams[PS_MAX_CAMS];
+    ps_pose poses[PS_MAX_CAMS];
+    int n_levels;
+    ps_level levels[PS_MAX_LEVELS];
+    // per level
+    ps_camera lref[PS_MAX_LEVELS];              // reference camera at the level
+    ps_camera lcam[PS_MAX_LEVELS][PS_MAX_CAMS];  // matching cameras at the level
+    int lW[PS_MAX_LEVELS], lH[PS_MAX_LEVELS];
+    int cx0[PS_MAX_LEVELS], cy0[PS_MAX_LEVELS];
+    float4* rays[PS_MAX_LEVELS] = {};
+    PlaneD* planes[PS_MAX_LEVELS] = {};
+    float* ref_img[PS_MAX_LEVELS] = {};
+    float4* quad[PS_MAX_LEVELS][PS_MAX_CAMS] = {};
+    float* out_depth[PS_MAX_LEVELS] = {};
+    float* out_c1[PS_MAX_LEVELS] = {};
+    float* out_c2[PS_MAX_LEVELS] = {};
+    int32_t* out_k[PS_MAX_LEVELS] = {};
+    ps_box* boxes_dev = nullptr;
+    int boxes_cap = 0;
+    SetD sets[PS_MAX_LEVELS][PS_MAX_SETS];
+    int n_planes[PS_MAX_LEVELS];
+    // host-frame staging (psweep_frame_host)
+    uint8_t* stage_img[1 + PS_MAX_CAMS] = {};
+    float* stage_depth = nullptr;
+    StageProfiler prof;
+};
+
+namespace {
+
+void free_sweep(psweep_t* h) {
+    if (!h) return;
+    h->prof.release();
+    for (int l = 0; l < PS_MAX_LEVELS; ++l) {
+        cudaFree(h->rays[l]);
+        cudaFree(h->planes[l]);
+        cudaFree(h->ref_img[l]);
+        for (int j = 0; j < PS_MAX_CAMS; ++j) cudaFree(h->quad[l][j]);
+        cudaFree(h->out_depth[l]);
+        cudaFree(h->out_c1[l]);
+        cudaFree(h->out_c2[l]);
+        cudaFree(h->out_k[l]);
+    }
+    cudaFree(h->boxes_dev);
+    for (int i = 0; i <= PS_MAX_CAMS; ++i) cudaFree(h->stage_img[i]);
+    cudaFree(h->stage_depth);
+    delete h;
+}
+
+int check_camera(const ps_camera& c, const char* what) {
+    PS_ARG(c.width > 0 && c.height > 0 && c.width <= 16384 && c.height <= 16384, "%s: bad image size %dx%d", what,
+           c.width, c.height);
+    PS_ARG(std::isfinite(c.fx) && std::isfinite(c.fy) && c.fx > 0 && c.fy > 0, "%s: focal lengths must be > 0",
+           what);
+    PS_ARG(std::isfinite(c.xi) && c.xi >= 0, "%s: xi must be >= 0", what);
+    PS_ARG(std::isfinite(c.cx) && std::isfinite(c.cy), "%s: principal point not finite", what);
+    PS_ARG(c.r2_max > 0, "%s: r2_max must be > 0", what);
+    return PS_OK;
+}
+
+ps_camera scaled_camera(const ps_camera& c, int s) {
+    ps_camera o = c;
+    o.fx = c.fx / s;
+    o.fy = c.fy / s;
+    o.cx = (c.cx - (s - 1) / 2.0) / s;
+    o.cy = (c.cy - (s - 1) / 2.0) / s;
+    o.width = c.width / s;
+    o.height = c.height / s;
+    return o;
+}
+
+}  // namespace
+
+extern "C" int psweep_create(const ps_sweep_desc* d, psweep_t** out) {
+    clear_error();
+    PS_ARG(out != nullptr, "psweep_create: out is NULL");
+    *out = nullptr;
+    PS_ARG(d != nullptr, "psweep_create: desc is NULL");
+    int st = check_camera(d->ref, "reference camera");
+    if (st) return st;
+    PS_ARG(d->n_cams >= 1 && d->n_cams <= PS_MAX_CAMS, "n_cams must be in 1..%d", PS_MAX_CAMS);
+    PS_ARG(d->cams && d->ref_to_cam, "cams / ref_to_cam are NULL");
+    PS_ARG(d->n_levels >= 1 && d->n_levels <= PS_MAX_LEVELS, "n_levels must be in 1..%d", PS_MAX_LEVELS);
+    PS_ARG(d->levels != nullptr, "levels is NULL");
+    int n_down = 0, n_crop = 0;
+    for (int l = 0; l < d->n_levels; ++l) {
+        const ps_level& L = d->levels[l];
+        PS_ARG(L.window == 5 || L.window == 7 || L.window == 9, "level %d: window must be 5, 7 or 9", l);
+        PS_ARG(L.n_sets >= 1 && L.n_sets <= PS_MAX_SETS, "level %d: n_sets must be in 1..%d", l, PS_MAX_SETS);
+        for (int s = 0; s < L.n_sets; ++s) {
+            const ps_plane_set& P = L.sets[s];
+            PS_ARG(P.count >= 1 && P.count <= 4096, "level %d set %d: count must be in 1..4096", l, s);
+            PS_ARG(P.family == PS_PLANES_FRONTO || P.family == PS_PLANES_GROUND, "level %d set %d: bad family", l,
+                   s);
+            if (P.family == PS_PLANES_FRONTO)
+                PS_ARG(P.a > 0 && P.b >= P.a, "level %d set %d: need 0 < near <= far", l, s);
+            else {
+                double nn = std::sqrt(P.n[0] * P.n[0] + P.n[1] * P.n[1] + P.n[2] * P.n[2]);
+                PS_ARG(nn > 0 && P.a > 0 && P.b >= P.a, "level %d set %d: need a normal and 0 < a <= b", l, s);
+            }
+        }
+        if (L.kind == PS_LEVEL_DOWNSAMPLE) {
+            ++n_down;
+            PS_ARG(L.factor == 1 || L.factor == 2 || L.factor == 4, "level %d: factor must be 1, 2 or 4", l);
+            PS_ARG(d->ref.width % L.factor == 0 && d->ref.height % L.factor == 0,
+                   "level %d: factor must divide the reference size", l);
+            for (int j = 0; j < d->n_cams; ++j)
+                PS_ARG(d->cams[j].width % L.factor == 0 && d->cams[j].height % L.factor == 0,
+                       "level %d: factor must divide camera %d's size", l, j);
+        } else if (L.kind == PS_LEVEL_CROP) {
+            ++n_crop;
+            PS_ARG(L.crop_w > 0 && L.crop_h > 0 && L.crop_w <= d->ref.width && L.crop_h <= d->ref.height,
+                   "level %d: bad crop size", l);
+        } else {
+            PS_ARG(false, "level %d: unknown kind %d", l, L.kind);
+        }
+    }
+    PS_ARG(n_down <= 1 && n_crop <= 1, "at most one downsample level and one crop level");
+    for (int j = 0; j < d->n_cams; ++j) {
+        st = check_camera(d->cams[j], "matching camera");
+        if (st) return st;
+    }
+
+    psweep_t* h = new psweep_t();
+    h->ref = d->ref;
+    h->n_cams = d->n_cams;
+    h->n_levels = d->n_levels;
+    for (int j = 0; j < d->n_cams; ++j) {
+        h->cams[j] = d->cams[j];
+        h->poses[j] = d->ref_to_cam[j];
+    }
+#define PS_TRY(call)                                 \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) {                     \
+            free_sweep(h);                           \
+            set_error("%s: %s", #call, cudaGetErrorString(e_)); \
+            return e_ == cudaErrorMemoryAllocation ? PS_ERR_OOM : PS_ERR_CUDA; \
+        }                                            \
+    } while (0)
+    for (int l = 0; l < d->n_levels; ++l) {
+        const ps_level& L = d->levels[l];
+        h->levels[l] = L;
+        if (L.kind == PS_LEVEL_DOWNSAMPLE) {
+            h->lref[l] = scaled_camera(d->ref, L.factor);
+            for (int j = 0; j < d->n_cams; ++j) h->lcam[l][j] = scaled_camera(d->cams[j], L.factor);
+            h->cx0[l] = h->cy0[l] = 0;
+        } else {
+            int x0 = (d->ref.width - L.crop_w) / 2, y0 = (d->ref.height - L.crop_h) / 2;
+            h->lref[l] = d->ref;
+            h->lref[l].cx -= x0;
+            h->lref[l].cy -= y0;
+            h->lref[l].width = L.crop_w;
+            h->lref[l].height = L.crop_h;
+            for (int j = 0; j < d->n_cams; ++j) h->lcam[l][j] = d->cams[j];
+            h->cx0[l] = x0;
+            h->cy0[l] = y0;
+        }
+        const int W = h->lref[l].width, H = h->lref[l].height;
+        h->lW[l] = W;
+        h->lH[l] = H;
+        // plane table (double on the host, stored as float)
+        std::vector<PlaneD> planes;
+        for (int s = 0; s < L.n_sets; ++s) {
+            const ps_plane_set& P = L.sets[s];
+            SetD S;
+            S.family = P.family;
+            S.start = (int)planes.size();
+            S.count = P.count;
+            S.a = (float)P.a;
+            S.b = (float)P.b;
+            double n[3] = {0, 0, 1};
+            if (P.family == PS_PLANES_GROUND) {
+                double nn = std::sqrt(P.n[0] * P.n[0] + P.n[1] * P.n[1] + P.n[2] * P.n[2]);
+                for (int i = 0; i < 3; ++i) n[i] = P.n[i] / nn;
+            }
+            S.nx = (float)n[0];
+            S.ny = (float)n[1];
+            S.nz = (float)n[2];
+            h->sets[l][s] = S;
+            for (int i = 0; i < P.count; ++i) {
+                double t = P.count > 1 ? (double)i / (P.count - 1) : 0.0;
+                double dd = P.family == PS_PLANES_FRONTO ? 1.0 / (1.0 / P.b + t * (1.0 / P.a - 1.0 / P.b))
+                                                         : P.a + t * (P.b - P.a);
+                planes.push_back({(float)n[0], (float)n[1], (float)n[2], (float)dd});
+            }
+        }
+        h->n_planes[l] = (int)planes.size();
+        PS_TRY(cudaMalloc(&h->planes[l], sizeof(PlaneD) * planes.size()));
+        PS_TRY(cudaMemcpy(h->planes[l], planes.data(), sizeof(PlaneD) * planes.size(), cudaMemcpyHostToDevice));
+        PS_TRY(cudaMalloc(&h->rays[l], sizeof(float4) * (size_t)W * H));
+        if (build_rays(h->lref[l], h->rays[l], nullptr)) {
+            free_sweep(h);
+            return PS_ERR_CUDA;
+        }
+        PS_TRY(cudaMalloc(&h->ref_img[l], sizeof(float) * (size_t)W * H));
+        for (int j = 0; j < d->n_cams; ++j) {
+            const ps_camera& cj = h->lcam[l][j];
+            PS_TRY(cudaMalloc(&h->quad[l][j], sizeof(float4) * (size_t)cj.width * cj.height));
+        }
+        PS_TRY(cudaMalloc(&h->out_depth[l], sizeof(float) * (size_t)W * H));
+        PS_TRY(cudaMalloc(&h->out_c1[l], sizeof(float) * (size_t)W * H));
+        PS_TRY(cudaMalloc(&h->out_c2[l], sizeof(float) * (size_t)W * H));
+        PS_TRY(cudaMalloc(&h->out_k[l], sizeof(int32_t) * (size_t)W * H));
+    }
+    PS_TRY(cudaMalloc(&h->boxes_dev, sizeof(ps_box) * 256));
+    h->boxes_cap = 256;
+    PS_TRY(cudaMalloc(&h->stage_img[0], (size_t)d->ref.width * d->ref.height));
+    for (int j = 0; j < d->n_cams; ++j)
+        PS_TRY(cudaMalloc(&h->stage_img[1 + j], (size_t)d->cams[j].width * d->cams[j].height));
+    PS_TRY(cudaMalloc(&h->stage_depth, sizeof(float) * (size_t)d->ref.width * d->ref.height));
+    PS_TRY(cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Tile<4>::smem_bytes));
+    PS_TRY(cudaDeviceSynchronize());
+#undef PS_TRY
+    *out = h;
+    return PS_OK;
+}
+
+extern "C" void psweep_destroy(psweep_t* h) { free_sweep(h); }
+
+extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_box* boxes, int32_t n_boxes,
+                            float* depth_out, const ps_level_out* level_out, void* stream) {
+    clear_error();
+    PS_ARG(h != nullptr, "psweep_depth: handle is NULL");
+    PS_ARG(images != nullptr, "psweep_depth: images is NULL");
+    for (int i = 0; i <= h->n_cams; ++i) PS_ARG(images[i] != nullptr, "psweep_depth: images[%d] is NULL", i);
+    PS_ARG(depth_out != nullptr, "psweep_depth: depth_out is NULL");
+    PS_ARG(n_boxes >= 0 && n_boxes <= h->boxes_cap, "psweep_depth: n_boxes must be in 0..%d", h->boxes_cap);
+    PS_ARG(n_boxes == 0 || boxes != nullptr, "psweep_depth: boxes is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+
+    SweepParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.n_levels = h->n_levels;
+    int tiles = 0;
+    h->prof.mark(0, s);
+    // larger windows first so the heavier tiles start early
+    for (int l = 0; l < h->n_levels; ++l) {
+        const ps_level& L = h->levels[l];
+        const int W = h->lW[l], H = h->lH[l];
+        if (L.kind == PS_LEVEL_DOWNSAMPLE) {
+            int sf = L.factor;
+            ref_level_kernel<<<dim3((W + 127) / 128, H), 128, 0, s>>>(images[0], h->ref.width, sf, 0, 0, W, H,
+                                                                       h->ref_img[l]);
+            for (int j = 0; j < h->n_cams; ++j) {
+                const ps_camera& cj = h->lcam[l][j];
+                quad_level_kernel<<<dim3((cj.width + 127) / 128, cj.height), 128, 0, s>>>(
+                    images[1 + j], h->cams[j].width, sf, cj.width, cj.height, h->quad[l][j]);
+            }
+        } else {
+            ref_level_kernel<<<dim3((W + 127) / 128, H), 128, 0, s>>>(images[0], h->ref.width, 0, h->cx0[l],
+                                                                       h->cy0[l], W, H, h->ref_img[l]);
+            for (int j = 0; j < h->n_cams; ++j) {
+                const ps_camera& cj = h->lcam[l][j];
+                quad_level_kernel<<<dim3((cj.width + 127) / 128, cj.height), 128, 0, s>>>(
+                    images[1 + j], h->cams[j].width, 1, cj.width, cj.height, h->quad[l][j]);
+            }
+        }
+        LevelD& D = P.lv[l];
+        D.W = W;
+        D.H = H;
+        D.rho = L.window / 2;
+        D.n_planes = h->n_planes[l];
+        D.n_sets = L.n_sets;
+        for (int k = 0; k < L.n_sets; ++k) D.sets[k] = h->sets[l][k];
+        D.planes = h->planes[l];
+        D.rays = h->rays[l];
+        D.ref = h->ref_img[l];
+        D.n_cams = h->n_cams;
+        for (int j = 0; j < h->n_cams; ++j) {
+            for (int i = 0; i < 9; ++i) D.cams[j].R[i] = (float)h->poses[j].R[i];
+            for (int i = 0; i < 3; ++i) D.cams[j].t[i] = (float)h->poses[j].t[i];
+            D.cams[j].cam = to_camf(h->lcam[l][j]);
+            D.cams[j].quad = h->quad[l][j];
+        }
+        D.tiles_x = (W + TW - 1) / TW;
+        D.tiles_y = (H + TH - 1) / TH;
+        D.tile_begin = tiles;
+        tiles += D.tiles_x * D.tiles_y;
+        const ps_level_out* lo = level_out ? &level_out[l] : nullptr;
+        D.depth = lo && lo->depth ? lo->depth : h->out_depth[l];
+        D.c1 = lo && lo->best_cost ? lo->best_cost : h->out_c1[l];
+        D.c2 = lo && lo->second_cost ? lo->second_cost : h->out_c2[l];
+        D.kstar = lo && lo->plane_idx ? lo->plane_idx : h->out_k[l];
+    }
+    PS_CUDA(cudaGetLastError());
+    size_t smem = 0;
+    for (int l = 0; l < h->n_levels; ++l) {
+        int r = P.lv[l].rho;
+        size_t b = r == 2 ? Tile<2>::smem_bytes : r == 3 ? Tile<3>::smem_bytes : Tile<4>::smem_bytes;
+        smem = std::max(smem, b);
+    }
+    h->prof.mark(1, s);
+    sweep_kernel<<<tiles, NT, smem, s>>>(P);
+    PS_CUDA(cudaGetLastError());
+    h->prof.mark(2, s);
+
+    MergeP M;
+    std::memset(&M, 0, sizeof(M));
+    M.W = h->ref.width;
+    M.H = h->ref.height;
+    M.s = 1;
+    M.Wl = M.Hl = 1;
+    for (int l = 0; l < h->n_levels; ++l) {
+        const ps_level& L = h->levels[l];
+        if (L.kind == PS_LEVEL_DOWNSAMPLE) {
+            M.low = P.lv[l].depth;
+            M.s = L.factor;
+            M.Wl = h->lW[l];
+            M.Hl = h->lH[l];
+        } else {
+            M.crop = P.lv[l].depth;
+            M.cx0 = h->cx0[l];
+            M.cy0 = h->cy0[l];
+            M.cw = L.crop_w;
+            M.ch = L.crop_h;
+        }
+    }
+    M.n_boxes = n_boxes;
+    for (int b = 0; b < n_boxes && b < 16; ++b) M.boxes[b] = boxes[b];
+    if (n_boxes > 16)
+        PS_CUDA(cudaMemcpyAsync(h->boxes_dev, boxes, sizeof(ps_box) * n_boxes, cudaMemcpyHostToDevice, s));
+    merge_kernel<<<dim3((M.W + 127) / 128, M.H), 128, 0, s>>>(M, h->boxes_dev, depth_out);
+    PS_CUDA(cudaGetLastError());
+    h->prof.mark(3, s);
+    h->prof.end_call();
+    return PS_OK;
+}
+
+extern "C" int psweep_profile(psweep_t* h, int32_t capacity) {
+    clear_error();
+    PS_ARG(h != nullptr && capacity >= 0 && capacity <= (1 << 20), "psweep_profile: bad arguments");
+    return h->prof.enable(3, capacity);
+}
+
+extern "C" int psweep_profile_read(psweep_t* h, double* stage_ms, int32_t* n_calls) {
+    clear_error();
+    PS_ARG(h != nullptr && stage_ms != nullptr, "psweep_profile_read: NULL argument");
+    PS_ARG(h->prof.cap > 0, "psweep_profile_read: profiling is off");
+    return h->prof.read(stage_ms, n_calls);
+}
+
+extern "C" int psweep_frame_host(psweep_t* h, tsdf_t* t, const uint8_t* const* host_images, const ps_box* boxes,
+                                 int32_t n_boxes, const ps_pose* world_to_ref, const double* local_center,
+                                 float* host_depth_out, void* stream) {
+    clear_error();
+    PS_ARG(h != nullptr && host_images != nullptr, "psweep_frame_host: handle or images NULL");
+    PS_ARG(t == nullptr || world_to_ref != nullptr, "psweep_frame_host: world_to_ref is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint8_t* dev[1 + PS_MAX_CAMS];
+    for (int i = 0; i <= h->n_cams; ++i) {
+        PS_ARG(host_images[i] != nullptr, "psweep_frame_host: host_images[%d] is NULL", i);
+        const ps_camera& c = i == 0 ? h->ref : h->cams[i - 1];
+        PS_CUDA(cudaMemcpyAsync(h->stage_img[i], host_images[i], (size_t)c.width * c.height,
+                                cudaMemcpyHostToDevice, s));
+        dev[i] = h->stage_img[i];
+    }
+    int st = psweep_depth(h, dev, boxes, n_boxes, h->stage_depth, nullptr, stream);
+    if (st) return st;
+    if (t) {
+        st = tsdf_integrate(t, h->stage_depth, world_to_ref, local_center, stream);
+        if (st) return st;
+    }
+    if (host_depth_out)
+        PS_CUDA(cudaMemcpyAsync(host_depth_out, h->stage_depth, sizeof(float) * (size_t)h->ref.width * h->ref.height,
+                                cudaMemcpyDeviceToHost, s));
+    PS_CUDA(cudaStreamSynchronize(s));
+    return PS_OK;
+}

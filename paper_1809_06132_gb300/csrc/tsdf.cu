@@ -1,0 +1,558 @@
+// TSDF fusion of fisheye depth maps into voxel blocks (Sec. III-C) on sm_103a.
+//
+// Per frame (all asynchronous on the caller's stream, no host sync):
+//   depth_max_kernel  largest range of the frame (bounds the visible test)
+//   alloc_kernel      per valid pixel: the blocks crossed by the segment
+//                     [d - mu, d + mu] of its ray (slab test of the segment
+//                     against each block of its bounding box), gated by the
+//                     local map, inserted into an open-addressing hash table
+//                     (bounded linear probing; overflow latches a status)
+//   visible_kernel    allocated blocks that some pixel of this frame can
+//                     update: a conservative sphere test on range and view
+//                     angle, compacted into a list
+//   integrate_kernel  Eq. 2 on every voxel of the listed blocks: one CTA per
+//                     block, 256 threads x 2 voxels, 16-byte loads and
+//                     stores of the interleaved {D, w} pairs
+//   extract_kernel    copy-out with the minimum-observation filter
+//
+// The signed distance eta = d - |X_d| subtracts two ranges of tens of
+// metres; float32 alone would lose ~1e-5 m there.  The kernel therefore
+// carries the voxel-to-camera offset as an exact integer voxel offset plus a
+// sub-voxel remainder, forms |X_d|^2 with an exact integer part, and
+// refines sqrt with one Newton step in split (hi + lo) float arithmetic, so
+// eta keeps ~1e-7 m absolute accuracy at any range.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace ps {
+namespace {
+
+constexpr int B = 8;            // voxels per block edge
+constexpr int B3 = B * B * B;   // voxels per block
+constexpr int IT = 256;         // integrate threads per block (2 voxels each)
+constexpr unsigned long long EMPTY = ~0ull;
+constexpr int MAX_PROBE = 4096;
+constexpr long long MAX_CANDIDATES = 4096;  // blocks in one segment's bounding box
+
+__host__ __device__ __forceinline__ unsigned long long pack_key(int x, int y, int z) {
+    return ((unsigned long long)(x + (1 << 20)) & 0x1FFFFF) | (((unsigned long long)(y + (1 << 20)) & 0x1FFFFF) << 21) |
+           (((unsigned long long)(z + (1 << 20)) & 0x1FFFFF) << 42);
+}
+
+__device__ __forceinline__ unsigned long long hash64(unsigned long long k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+struct FrameP {
+    // camera (float) and pose
+    CamF cam;
+    float R[9];        // world -> camera rotation
+    float Rt[9];       // camera -> world rotation
+    float C[3];        // camera centre relative to the grid origin (m)
+    int ic[3];         // camera centre in voxel units: ic + fc = (C_world - origin) / voxel
+    float fb[3];       // 1/2 - fc: sub-voxel part of a voxel centre's offset from the camera
+    float vox, vox_lo; // voxel size split into float hi + lo
+    float mu, inv_mu, w_max;
+    float block;       // block edge (m)
+    // local-map gate (block centre within half of centre), relative to origin
+    int gate;
+    float lc[3], lh[3];
+    // visible test
+    float cos_view;    // cosine of the widest view angle of a valid ray (margin included)
+    float view_angle;
+};
+
+struct TsdfDev {
+    unsigned long long* hkeys;
+    int* hvals;
+    long long slot_mask;
+    float2* vox;
+    int4* pool_keys;
+    int* n_alloc;
+    int pool_cap;
+    int* vis;
+    int* n_vis;
+    unsigned* status;
+    unsigned* dmax_bits;
+    const float4* rays;  // depth camera rays (camera frame), NaN = none
+};
+
+// ----------------------------------------------------------------- hash
+
+// Insert (or find) a block key; returns its pool index or -1 on failure.
+__device__ int hash_insert(const TsdfDev& T, int bx, int by, int bz) {
+    unsigned long long key = pack_key(bx, by, bz);
+    long long h = (long long)(hash64(key) & (unsigned long long)T.slot_mask);
+    for (int probe = 0; probe < MAX_PROBE; ++probe) {
+        unsigned long long k = *((volatile unsigned long long*)&T.hkeys[h]);
+        if (k == key) return 0;
+        if (k == EMPTY) {
+            unsigned long long prev = atomicCAS(&T.hkeys[h], EMPTY, key);
+            if (prev == EMPTY) {
+                int idx = atomicAdd(T.n_alloc, 1);
+                if (idx >= T.pool_cap) {
+                    atomicOr(T.status, DEV_CAPACITY);
+                    T.hvals[h] = -2;
+                    return -1;
+                }
+                T.pool_keys[idx] = make_int4(bx, by, bz, 0);
+                T.hvals[h] = idx;
+                return 0;
+            }
+            if (prev == key) return 0;
+        }
+        h = (h + 1) & T.slot_mask;
+    }
+    atomicOr(T.status, DEV_TIMEOUT | DEV_CAPACITY);
+    return -1;
+}
+
+// ----------------------------------------------------------------- kernels
+
+__global__ void depth_max_kernel(const float* depth, int n, unsigned* dmax_bits) {
+    float m = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float d = depth[i];
+        if (d > m && d < 3.0e38f) m = d;
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(dmax_bits, __float_as_uint(m));
+}
+
+// Length of segment [A, B] inside box [lo, hi] (slab method).
+__device__ __forceinline__ float seg_box(const float A[3], const float D[3], const float lo[3], const float hi[3]) {
+    float t0 = 0.f, t1 = 1.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (D[k] == 0.f) {
+            if (A[k] < lo[k] || A[k] > hi[k]) return 0.f;
+            continue;
+        }
+        float inv = 1.0f / D[k];
+        float ta = (lo[k] - A[k]) * inv, tb = (hi[k] - A[k]) * inv;
+        t0 = fmaxf(t0, fminf(ta, tb));
+        t1 = fminf(t1, fmaxf(ta, tb));
+    }
+    return t1 > t0 ? (t1 - t0) : 0.f;
+}
+
+__global__ void alloc_kernel(const __grid_constant__ FrameP F, TsdfDev T, const float* depth) {
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    int v = blockIdx.y;
+    if (u >= F.cam.width || v >= F.cam.height) return;
+    size_t o = (size_t)v * F.cam.width + u;
+    float d = depth[o];
+    if (!(d > 0.f) || !(d < 3.0e38f)) return;
+    float4 r = T.rays[o];
+    if (isnan(r.x)) return;
+    float dw[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dw[i] = F.Rt[3 * i] * r.x + F.Rt[3 * i + 1] * r.y + F.Rt[3 * i + 2] * r.z;
+    float s0 = fmaxf(0.f, d - F.mu), s1 = d + F.mu;
+    float A[3], Dv[3];
+    int lo[3], hi[3];
+    long long n_cand = 1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        A[i] = fmaf(s0, dw[i], F.C[i]);
+        float Bp = fmaf(s1, dw[i], F.C[i]);
+        Dv[i] = Bp - A[i];
+        float flo = floorf(fminf(A[i], Bp) / F.block), fhi = floorf(fmaxf(A[i], Bp) / F.block);
+        // block keys hold 21-bit signed indices; a segment outside that range cannot be stored
+        if (!(flo >= -1048575.f && fhi <= 1048575.f)) {
+            atomicOr(T.status, DEV_CAPACITY);
+            return;
+        }
+        lo[i] = (int)flo;
+        hi[i] = (int)fhi;
+        n_cand *= (long long)(hi[i] - lo[i] + 1);
+    }
+    if (n_cand > MAX_CANDIDATES) {  // segment spans more blocks than any sane mu / block ratio gives
+        atomicOr(T.status, DEV_CAPACITY);
+        return;
+    }
+    for (int bz = lo[2]; bz <= hi[2]; ++bz)
+        for (int by = lo[1]; by <= hi[1]; ++by)
+            for (int bx = lo[0]; bx <= hi[0]; ++bx) {
+                float blo[3] = {bx * F.block, by * F.block, bz * F.block};
+                float bhi[3] = {(bx + 1) * F.block, (by + 1) * F.block, (bz + 1) * F.block};
+                if (seg_box(A, Dv, blo, bhi) <= 0.f) continue;
+                if (F.gate) {
+                    float c0 = (bx + 0.5f) * F.block, c1 = (by + 0.5f) * F.block, c2 = (bz + 0.5f) * F.block;
+                    if (fabsf(c0 - F.lc[0]) > F.lh[0] || fabsf(c1 - F.lc[1]) > F.lh[1] ||
+                        fabsf(c2 - F.lc[2]) > F.lh[2])
+                        continue;
+                }
+                hash_insert(T, bx, by, bz);
+            }
+}
+
+// Blocks a pixel of this frame can update: within range dmax + mu of the
+// camera (eta >= -mu needs |X_d| <= d + mu) and inside the widest view cone
+// (both tested on the block's bounding sphere).
+__global__ void visible_kernel(const __grid_constant__ FrameP F, TsdfDev T) {
+    int n = min(*T.n_alloc, T.pool_cap);
+    float dmax = __uint_as_float(*T.dmax_bits);
+    float rb = F.block * 0.8660254f * 1.001f + 1e-4f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int4 k = T.pool_keys[i];
+        float c[3] = {(k.x + 0.5f) * F.block - F.C[0], (k.y + 0.5f) * F.block - F.C[1],
+                      (k.z + 0.5f) * F.block - F.C[2]};
+        float Xc[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) Xc[a] = F.R[3 * a] * c[0] + F.R[3 * a + 1] * c[1] + F.R[3 * a + 2] * c[2];
+        float dist = sqrtf(Xc[0] * Xc[0] + Xc[1] * Xc[1] + Xc[2] * Xc[2]);
+        bool vis = dmax > 0.f && dist - rb <= dmax + F.mu;
+        if (vis && dist > rb) {
+            float ang = acosf(fminf(1.f, fmaxf(-1.f, Xc[2] / dist)));
+            float half = asinf(fminf(1.f, rb / dist));
+            vis = ang - half <= F.view_angle;
+        }
+        if (vis) {
+            int slot = atomicAdd(T.n_vis, 1);
+            T.vis[slot] = i;
+        }
+    }
+}
+
+// Eq. 2 on one voxel.  a = voxel index - camera voxel (exact int), F.fb the
+// sub-voxel part, so the voxel centre sits at vox * (a + fb) from the camera.
+__device__ __forceinline__ void update_voxel(const FrameP& F, const float* depth, int ax, int ay, int az, float2& dw) {
+    const CamF& c = F.cam;
+    float bx = F.fb[0], by = F.fb[1], bz = F.fb[2];
+    float vx = ((float)ax + bx) * F.vox, vy = ((float)ay + by) * F.vox, vz = ((float)az + bz) * F.vox;
+    float X = F.R[0] * vx + F.R[1] * vy + F.R[2] * vz;
+    float Y = F.R[3] * vx + F.R[4] * vy + F.R[5] * vz;
+    float Z = F.R[6] * vx + F.R[7] * vy + F.R[8] * vz;
+    // projection (unified model + distortion) and nearest pixel
+    float n = sqrtf(fmaf(X, X, fmaf(Y, Y, Z * Z)));
+    float inv = 1.0f / fmaf(c.xi, n, Z);
+    float mx = X * inv, my = Y * inv;
+    float r2 = fmaf(mx, mx, my * my);
+    float rad = fmaf(r2, fmaf(c.k2, r2, c.k1), 1.0f);
+    float mxy = mx * my;
+    float xd = fmaf(mx, rad, fmaf(2.0f * c.p1, mxy, c.p2 * fmaf(2.0f * mx, mx, r2)));
+    float yd = fmaf(my, rad, fmaf(c.p1, fmaf(2.0f * my, my, r2), 2.0f * c.p2 * mxy));
+    float u = fmaf(c.fx, xd, c.cx), v = fmaf(c.fy, yd, c.cy);
+    if (!((Z > c.lim * n) && (r2 <= c.r2_max))) return;
+    float pu = floorf(u + 0.5f), pv = floorf(v + 0.5f);
+    if (!(pu >= 0.f && pv >= 0.f && pu < (float)c.width && pv < (float)c.height)) return;
+    float d = __ldg(&depth[(size_t)pv * c.width + (size_t)pu]);
+    if (!(d > 0.f) || !(d < 3.0e38f)) return;
+    // |X_d| in voxel units: (a + b)^2 = a^2 (exact int) + (2a + b) b
+    int A2 = ax * ax + ay * ay + az * az;
+    float Bs = fmaf(fmaf(2.0f, (float)ax, bx), bx, fmaf(fmaf(2.0f, (float)ay, by), by, fmaf(2.0f, (float)az, bz) * bz));
+    float y = sqrtf((float)A2 + Bs);
+    float p = y * y;
+    float pe = fmaf(y, y, -p);  // p + pe = y^2 exactly
+    float diff = A2 < (1 << 24) ? (float)A2 - p : (float)(A2 - __float2int_rn(p));
+    float corr = ((diff - pe) + Bs) / (2.0f * y);  // |X_d| = y + corr (voxel units)
+    // eta = d - vox * (y + corr), with the product vox * y split exactly
+    float q = F.vox * y;
+    float qe = fmaf(F.vox, y, -q);
+    float eta = ((d - q) - qe) - fmaf(F.vox_lo, y, F.vox * corr);
+    if (eta < -F.mu) return;
+    float sdf = fminf(1.0f, eta * F.inv_mu);
+    float w = dw.y;
+    dw.x = (w * dw.x + sdf) / (w + 1.0f);
+    dw.y = fminf(w + 1.0f, F.w_max);
+}
+
+__global__ void __launch_bounds__(IT) integrate_kernel(const __grid_constant__ FrameP F, TsdfDev T,
+                                                       const float* depth) {
+    int nv = *T.n_vis;
+    for (int e = blockIdx.x; e < nv; e += gridDim.x) {
+        int bi = T.vis[e];
+        int4 k = T.pool_keys[bi];
+        float4* blk = reinterpret_cast<float4*>(T.vox + (size_t)bi * B3);
+        float4 pr = blk[threadIdx.x];
+        int v0 = 2 * threadIdx.x;  // voxels v0, v0 + 1: same y, z; x and x + 1
+        int x = v0 & 7, y = (v0 >> 3) & 7, z = v0 >> 6;
+        int ax = k.x * B + x - F.ic[0], ay = k.y * B + y - F.ic[1], az = k.z * B + z - F.ic[2];
+        float2 a = make_float2(pr.x, pr.y), b = make_float2(pr.z, pr.w);
+        update_voxel(F, depth, ax, ay, az, a);
+        update_voxel(F, depth, ax + 1, ay, az, b);
+        blk[threadIdx.x] = make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+
+__global__ void extract_kernel(TsdfDev T, int n, float min_w, int* keys, float* D, float* W) {
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int4 k = T.pool_keys[i];
+            keys[3 * i] = k.x;
+            keys[3 * i + 1] = k.y;
+            keys[3 * i + 2] = k.z;
+        }
+        for (int v = threadIdx.x; v < B3; v += blockDim.x) {
+            float2 dw = T.vox[(size_t)i * B3 + v];
+            bool keep = dw.y >= min_w && dw.y > 0.f;
+            D[(size_t)i * B3 + v] = keep ? dw.x : 0.f;
+            W[(size_t)i * B3 + v] = keep ? dw.y : 0.f;
+        }
+    }
+}
+
+__global__ void dense_keys_kernel(int4* keys, int nx, int ny, int nz) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx * ny * nz) return;
+    keys[i] = make_int4(i % nx, (i / nx) % ny, i / (nx * ny), 0);
+}
+
+}  // namespace
+
+// ray table of the depth camera (defined with the sweep's ray kernel)
+int build_rays(const ps_camera& cam, float4* rays, double* max_angle);
+
+}  // namespace ps
+
+using namespace ps;
+
+struct tsdf_s {
+    ps_tsdf_desc d;
+    bool dense = false;
+    TsdfDev T{};
+    int sms = 0;
+    float4* rays = nullptr;
+    double view_angle = 0;
+    StageProfiler prof;
+};
+
+namespace {
+
+void free_tsdf(tsdf_t* t) {
+    if (!t) return;
+    t->prof.release();
+    cudaFree(t->T.hkeys);
+    cudaFree(t->T.hvals);
+    cudaFree(t->T.vox);
+    cudaFree(t->T.pool_keys);
+    cudaFree(t->T.n_alloc);
+    cudaFree(t->T.vis);
+    cudaFree(t->T.n_vis);
+    cudaFree(t->T.status);
+    cudaFree(t->T.dmax_bits);
+    cudaFree(t->rays);
+    delete t;
+}
+
+int read_status(tsdf_t* t, cudaStream_t s) {
+    unsigned st = 0;
+    PS_CUDA(cudaMemcpyAsync(&st, t->T.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    PS_CUDA(cudaStreamSynchronize(s));
+    if (st) {
+        PS_CUDA(cudaMemsetAsync(t->T.status, 0, sizeof(unsigned), s));
+        PS_CUDA(cudaStreamSynchronize(s));
+        if (st & DEV_TIMEOUT) {
+            set_error("TSDF hash probing gave up after %d probes (table too full)", MAX_PROBE);
+            return PS_ERR_TIMEOUT;
+        }
+        set_error("TSDF voxel-block pool or hash table is full");
+        return PS_ERR_CAPACITY;
+    }
+    return PS_OK;
+}
+
+}  // namespace
+
+extern "C" int tsdf_create(const ps_tsdf_desc* d, tsdf_t** out) {
+    clear_error();
+    PS_ARG(out != nullptr, "tsdf_create: out is NULL");
+    *out = nullptr;
+    PS_ARG(d != nullptr, "tsdf_create: desc is NULL");
+    PS_ARG(d->block_dim == 8, "tsdf_create: block_dim must be 8");
+    PS_ARG(d->voxel_size > 0 && d->mu > 0 && d->w_max >= 1, "tsdf_create: need voxel_size > 0, mu > 0, w_max >= 1");
+    PS_ARG(d->cam.width > 0 && d->cam.height > 0 && d->cam.fx > 0 && d->cam.fy > 0 && d->cam.xi >= 0,
+           "tsdf_create: bad camera");
+    bool dense = d->dense_dim[0] || d->dense_dim[1] || d->dense_dim[2];
+    int64_t pool = 0;
+    if (dense) {
+        for (int i = 0; i < 3; ++i)
+            PS_ARG(d->dense_dim[i] > 0 && d->dense_dim[i] % 8 == 0, "tsdf_create: dense_dim must be multiples of 8");
+        pool = (int64_t)(d->dense_dim[0] / 8) * (d->dense_dim[1] / 8) * (d->dense_dim[2] / 8);
+        PS_ARG(pool <= (1 << 24), "tsdf_create: dense grid too large");
+    } else {
+        PS_ARG(d->hash_slots >= 1024 && (d->hash_slots & (d->hash_slots - 1)) == 0 && d->hash_slots <= (1ll << 31),
+               "tsdf_create: hash_slots must be a power of two in [2^10, 2^31]");
+        PS_ARG(d->pool_blocks >= 1 && d->pool_blocks <= (1ll << 26), "tsdf_create: pool_blocks must be in [1, 2^26]");
+        pool = d->pool_blocks;
+    }
+    tsdf_t* t = new tsdf_t();
+    t->d = *d;
+    t->dense = dense;
+#define PS_TRY(call)                                                        \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) {                                            \
+            free_tsdf(t);                                                   \
+            set_error("%s: %s", #call, cudaGetErrorString(e_));             \
+            return e_ == cudaErrorMemoryAllocation ? PS_ERR_OOM : PS_ERR_CUDA; \
+        }                                                                   \
+    } while (0)
+    int dev = 0;
+    PS_TRY(cudaGetDevice(&dev));
+    PS_TRY(cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, dev));
+    t->T.pool_cap = (int)pool;
+    PS_TRY(cudaMalloc(&t->T.vox, sizeof(float2) * (size_t)pool * B3));
+    PS_TRY(cudaMemset(t->T.vox, 0, sizeof(float2) * (size_t)pool * B3));
+    PS_TRY(cudaMalloc(&t->T.pool_keys, sizeof(int4) * (size_t)pool));
+    PS_TRY(cudaMalloc(&t->T.n_alloc, sizeof(int)));
+    PS_TRY(cudaMalloc(&t->T.vis, sizeof(int) * (size_t)pool));
+    PS_TRY(cudaMalloc(&t->T.n_vis, sizeof(int)));
+    PS_TRY(cudaMalloc(&t->T.status, sizeof(unsigned)));
+    PS_TRY(cudaMemset(t->T.status, 0, sizeof(unsigned)));
+    PS_TRY(cudaMalloc(&t->T.dmax_bits, sizeof(unsigned)));
+    if (dense) {
+        int nx = d->dense_dim[0] / 8, ny = d->dense_dim[1] / 8, nz = d->dense_dim[2] / 8;
+        dense_keys_kernel<<<(int)((pool + 255) / 256), 256>>>(t->T.pool_keys, nx, ny, nz);
+        PS_TRY(cudaGetLastError());
+        int n = (int)pool;
+        PS_TRY(cudaMemcpy(t->T.n_alloc, &n, sizeof(int), cudaMemcpyHostToDevice));
+    } else {
+        PS_TRY(cudaMalloc(&t->T.hkeys, sizeof(unsigned long long) * (size_t)d->hash_slots));
+        PS_TRY(cudaMemset(t->T.hkeys, 0xFF, sizeof(unsigned long long) * (size_t)d->hash_slots));
+        PS_TRY(cudaMalloc(&t->T.hvals, sizeof(int) * (size_t)d->hash_slots));
+        PS_TRY(cudaMemset(t->T.hvals, 0xFF, sizeof(int) * (size_t)d->hash_slots));
+        PS_TRY(cudaMemset(t->T.n_alloc, 0, sizeof(int)));
+        t->T.slot_mask = d->hash_slots - 1;
+    }
+    PS_TRY(cudaMalloc(&t->rays, sizeof(float4) * (size_t)d->cam.width * d->cam.height));
+    t->T.rays = t->rays;
+    int st = build_rays(d->cam, t->rays, &t->view_angle);
+    if (st) {
+        free_tsdf(t);
+        return st;
+    }
+    PS_TRY(cudaDeviceSynchronize());
+#undef PS_TRY
+    *out = t;
+    return PS_OK;
+}
+
+extern "C" void tsdf_destroy(tsdf_t* t) { free_tsdf(t); }
+
+extern "C" int tsdf_integrate(tsdf_t* t, const float* depth, const ps_pose* w2c, const double* lc, void* stream) {
+    clear_error();
+    PS_ARG(t != nullptr && depth != nullptr && w2c != nullptr, "tsdf_integrate: NULL argument");
+    const ps_tsdf_desc& d = t->d;
+    bool gate = !t->dense && (d.local_half[0] > 0 || d.local_half[1] > 0 || d.local_half[2] > 0);
+    PS_ARG(!gate || lc != nullptr, "tsdf_integrate: local_center is required with a local map");
+    for (int i = 0; i < 12; ++i) PS_ARG(std::isfinite(i < 9 ? w2c->R[i] : w2c->t[i - 9]), "tsdf_integrate: pose not finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    FrameP F;
+    std::memset(&F, 0, sizeof(F));
+    F.cam = to_camf(d.cam);
+    double Cw[3];
+    for (int i = 0; i < 3; ++i) {
+        Cw[i] = -(w2c->R[i] * w2c->t[0] + w2c->R[3 + i] * w2c->t[1] + w2c->R[6 + i] * w2c->t[2]);
+        for (int k = 0; k < 3; ++k) {
+            F.R[3 * i + k] = (float)w2c->R[3 * i + k];
+            F.Rt[3 * i + k] = (float)w2c->R[3 * k + i];
+        }
+    }
+    for (int i = 0; i < 3; ++i) {
+        double rel = Cw[i] - d.origin[i];
+        F.C[i] = (float)rel;
+        double cv = rel / d.voxel_size;
+        double ic = std::floor(cv + 0.5);
+        PS_ARG(std::fabs(ic) < 1e8, "tsdf_integrate: camera too far from the grid origin");
+        F.ic[i] = (int)ic;
+        F.fb[i] = (float)(0.5 - (cv - ic));
+    }
+    F.vox = (float)d.voxel_size;
+    F.vox_lo = (float)(d.voxel_size - (double)F.vox);
+    F.mu = (float)d.mu;
+    F.inv_mu = (float)(1.0 / d.mu);
+    F.w_max = (float)d.w_max;
+    F.block = (float)(8.0 * d.voxel_size);
+    F.gate = gate ? 1 : 0;
+    if (gate)
+        for (int i = 0; i < 3; ++i) {
+            F.lc[i] = (float)(lc[i] - d.origin[i]);
+            F.lh[i] = (float)d.local_half[i];
+        }
+    F.view_angle = (float)(t->view_angle + 1e-3);
+    const int W = d.cam.width, H = d.cam.height;
+    t->prof.mark(0, s);
+    PS_CUDA(cudaMemsetAsync(t->T.dmax_bits, 0, sizeof(unsigned), s));
+    depth_max_kernel<<<t->sms * 2, 256, 0, s>>>(depth, W * H, t->T.dmax_bits);
+    PS_CUDA(cudaGetLastError());
+    t->prof.mark(1, s);
+    if (!t->dense) {
+        alloc_kernel<<<dim3((W + 127) / 128, H), 128, 0, s>>>(F, t->T, depth);
+        PS_CUDA(cudaGetLastError());
+    }
+    t->prof.mark(2, s);
+    PS_CUDA(cudaMemsetAsync(t->T.n_vis, 0, sizeof(int), s));
+    visible_kernel<<<t->sms * 4, 256, 0, s>>>(F, t->T);
+    PS_CUDA(cudaGetLastError());
+    t->prof.mark(3, s);
+    integrate_kernel<<<t->sms * 8, IT, 0, s>>>(F, t->T, depth);
+    PS_CUDA(cudaGetLastError());
+    t->prof.mark(4, s);
+    t->prof.end_call();
+    return PS_OK;
+}
+
+extern "C" int tsdf_profile(tsdf_t* t, int32_t capacity) {
+    clear_error();
+    PS_ARG(t != nullptr && capacity >= 0 && capacity <= (1 << 20), "tsdf_profile: bad arguments");
+    return t->prof.enable(4, capacity);
+}
+
+extern "C" int tsdf_profile_read(tsdf_t* t, double* stage_ms, int32_t* n_calls) {
+    clear_error();
+    PS_ARG(t != nullptr && stage_ms != nullptr, "tsdf_profile_read: NULL argument");
+    PS_ARG(t->prof.cap > 0, "tsdf_profile_read: profiling is off");
+    return t->prof.read(stage_ms, n_calls);
+}
+
+extern "C" int tsdf_count(tsdf_t* t, int64_t* n_blocks, void* stream) {
+    clear_error();
+    PS_ARG(t != nullptr && n_blocks != nullptr, "tsdf_count: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int n = 0;
+    PS_CUDA(cudaMemcpyAsync(&n, t->T.n_alloc, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PS_CUDA(cudaStreamSynchronize(s));
+    *n_blocks = std::min<int64_t>(n, t->T.pool_cap);
+    return read_status(t, s);
+}
+
+extern "C" int tsdf_extract(tsdf_t* t, float min_weight, int32_t* keys, float* D, float* W, int64_t capacity,
+                            int64_t* n_out, void* stream) {
+    clear_error();
+    PS_ARG(t != nullptr && n_out != nullptr, "tsdf_extract: NULL argument");
+    PS_ARG(capacity >= 0, "tsdf_extract: negative capacity");
+    PS_ARG(capacity == 0 || (keys && D && W), "tsdf_extract: NULL output buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t n = 0;
+    int st = tsdf_count(t, &n, stream);
+    int64_t m = std::min(n, capacity);
+    if (m > 0) {
+        extract_kernel<<<(int)std::min<int64_t>(m, 65535), 256, 0, s>>>(t->T, (int)m, min_weight, keys, D, W);
+        PS_CUDA(cudaGetLastError());
+        PS_CUDA(cudaStreamSynchronize(s));
+    }
+    *n_out = m;
+    if (st) return st;
+    if (capacity < n) {
+        set_error("tsdf_extract: capacity %lld < %lld blocks", (long long)capacity, (long long)n);
+        return PS_ERR_CAPACITY;
+    }
+    return PS_OK;
+}
+
+extern "C" int tsdf_status(tsdf_t* t, void* stream) {
+    clear_error();
+    PS_ARG(t != nullptr, "tsdf_status: NULL handle");
+    return read_status(t, (cudaStream_t)stream);
+}

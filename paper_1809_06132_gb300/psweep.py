@@ -1,0 +1,329 @@
+"""Python binding of libpsweep.so (ctypes): argument marshalling only.
+
+Every step of the fisheye plane sweep and the TSDF fusion runs in the CUDA
+kernels behind the C ABI declared in include/psweep.h.  This module converts
+camera / pose / level descriptions (any objects with the attribute names
+used below) into the C structs, passes torch tensors as raw device pointers
+and torch streams as cudaStream_t, and raises on every non-zero status.
+There is no fallback: if the library cannot be loaded, importing it fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _build
+
+PS_OK, PS_ERR_ARG, PS_ERR_OOM, PS_ERR_CAPACITY, PS_ERR_CUDA, PS_ERR_TIMEOUT = range(6)
+STATUS_NAMES = {1: "PS_ERR_ARG", 2: "PS_ERR_OOM", 3: "PS_ERR_CAPACITY", 4: "PS_ERR_CUDA", 5: "PS_ERR_TIMEOUT"}
+MAX_SETS, MAX_CAMS, MAX_LEVELS = 4, 4, 2
+
+# every symbol include/psweep.h declares
+EXPORTS = ["psweep_create", "psweep_depth", "psweep_destroy", "tsdf_create", "tsdf_integrate", "tsdf_count",
+           "tsdf_extract", "tsdf_status", "tsdf_destroy", "psweep_frame_host", "psweep_profile",
+           "psweep_profile_read", "tsdf_profile", "tsdf_profile_read", "ps_last_error", "ps_version"]
+
+
+class PsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ps_camera(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("xi", "fx", "fy", "cx", "cy", "k1", "k2", "p1", "p2", "r2_max")] + \
+               [("width", C.c_int32), ("height", C.c_int32)]
+
+
+class ps_pose(C.Structure):
+    _fields_ = [("R", C.c_double * 9), ("t", C.c_double * 3)]
+
+
+class ps_plane_set(C.Structure):
+    _fields_ = [("family", C.c_int32), ("count", C.c_int32), ("a", C.c_double), ("b", C.c_double),
+                ("n", C.c_double * 3)]
+
+
+class ps_level(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("factor", C.c_int32), ("crop_w", C.c_int32), ("crop_h", C.c_int32),
+                ("window", C.c_int32), ("n_sets", C.c_int32), ("sets", ps_plane_set * MAX_SETS)]
+
+
+class ps_sweep_desc(C.Structure):
+    _fields_ = [("ref", ps_camera), ("n_cams", C.c_int32), ("cams", C.POINTER(ps_camera)),
+                ("ref_to_cam", C.POINTER(ps_pose)), ("n_levels", C.c_int32), ("levels", C.POINTER(ps_level))]
+
+
+class ps_box(C.Structure):
+    _fields_ = [("x0", C.c_int32), ("y0", C.c_int32), ("x1", C.c_int32), ("y1", C.c_int32)]
+
+
+class ps_level_out(C.Structure):
+    _fields_ = [("depth", C.c_void_p), ("best_cost", C.c_void_p), ("second_cost", C.c_void_p),
+                ("plane_idx", C.c_void_p)]
+
+
+class ps_tsdf_desc(C.Structure):
+    _fields_ = [("cam", ps_camera), ("voxel_size", C.c_double), ("mu", C.c_double), ("w_max", C.c_double),
+                ("block_dim", C.c_int32), ("dense_dim", C.c_int32 * 3), ("origin", C.c_double * 3),
+                ("local_half", C.c_double * 3), ("hash_slots", C.c_int64), ("pool_blocks", C.c_int64)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libpsweep.so (building it in-tree first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"libpsweep.so not built at {path}")
+        _build.build()
+    L = C.CDLL(path)
+    P = C.c_void_p
+    L.psweep_create.argtypes = [C.POINTER(ps_sweep_desc), C.POINTER(C.c_void_p)]
+    L.psweep_depth.argtypes = [P, P, P, C.c_int32, P, P, P]
+    L.psweep_destroy.argtypes = [P]
+    L.psweep_destroy.restype = None
+    L.tsdf_create.argtypes = [C.POINTER(ps_tsdf_desc), C.POINTER(C.c_void_p)]
+    L.tsdf_integrate.argtypes = [P, P, C.POINTER(ps_pose), P, P]
+    L.tsdf_count.argtypes = [P, C.POINTER(C.c_int64), P]
+    L.tsdf_extract.argtypes = [P, C.c_float, P, P, P, C.c_int64, C.POINTER(C.c_int64), P]
+    L.tsdf_status.argtypes = [P, P]
+    L.tsdf_destroy.argtypes = [P]
+    L.tsdf_destroy.restype = None
+    L.psweep_frame_host.argtypes = [P, P, P, P, C.c_int32, C.POINTER(ps_pose), P, P, P]
+    L.psweep_profile.argtypes = [P, C.c_int32]
+    L.psweep_profile_read.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int32)]
+    L.tsdf_profile.argtypes = [P, C.c_int32]
+    L.tsdf_profile_read.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int32)]
+    L.ps_last_error.restype = C.c_char_p
+    L.ps_version.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(st: int):
+    if st != PS_OK:
+        raise PsError(st, load().ps_last_error().decode())
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream or None
+
+
+def camera(c) -> ps_camera:
+    return ps_camera(xi=c.xi, fx=c.fx, fy=c.fy, cx=c.cx, cy=c.cy, k1=c.k1, k2=c.k2, p1=c.p1, p2=c.p2,
+                     r2_max=min(float(c.r2_max), 1e300), width=c.width, height=c.height)
+
+
+def pose(p) -> ps_pose:
+    o = ps_pose()
+    R = np.asarray(p.R, dtype=np.float64).reshape(-1)
+    t = np.asarray(p.t, dtype=np.float64).reshape(-1)
+    for i in range(9):
+        o.R[i] = R[i]
+    for i in range(3):
+        o.t[i] = t[i]
+    return o
+
+
+def level(lv) -> ps_level:
+    assert len(lv.sets) <= MAX_SETS
+    o = ps_level(kind=lv.kind, factor=lv.factor, crop_w=lv.crop_w, crop_h=lv.crop_h, window=lv.window,
+                 n_sets=len(lv.sets))
+    for i, s in enumerate(lv.sets):
+        o.sets[i].family = s.family
+        o.sets[i].count = s.count
+        o.sets[i].a = s.a
+        o.sets[i].b = s.b
+        for k in range(3):
+            o.sets[i].n[k] = s.n[k]
+    return o
+
+
+def boxes_array(boxes):
+    b = np.zeros((0, 4), dtype=np.int32) if boxes is None else np.ascontiguousarray(boxes, dtype=np.int32)
+    n = len(b)
+    arr = (ps_box * max(1, n))()
+    for i in range(n):
+        arr[i] = ps_box(*[int(v) for v in b[i]])
+    return arr, n
+
+
+def _dev(t: torch.Tensor, dtype, name: str) -> int:
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    return t.data_ptr()
+
+
+def level_shape(ref, lv):
+    if lv.kind == 0:
+        return ref.height // lv.factor, ref.width // lv.factor
+    return lv.crop_h, lv.crop_w
+
+
+class Sweep:
+    """Multi-scale fisheye plane sweep of one rig (psweep_create / psweep_depth)."""
+
+    def __init__(self, rig, levels):
+        L = load()
+        self.rig = rig
+        self.levels = list(levels)
+        self._cams = (ps_camera * len(rig.cams))(*[camera(c) for c in rig.cams])
+        self._poses = (ps_pose * len(rig.cams))(*[pose(p) for p in rig.ref_to_cam])
+        self._levels = (ps_level * len(self.levels))(*[level(lv) for lv in self.levels])
+        d = ps_sweep_desc(ref=camera(rig.ref), n_cams=len(rig.cams), cams=self._cams, ref_to_cam=self._poses,
+                          n_levels=len(self.levels), levels=self._levels)
+        h = C.c_void_p()
+        _check(L.psweep_create(C.byref(d), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().psweep_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def profile(self, capacity: int):
+        """Record stage events for the next `capacity` depth calls (0 = off)."""
+        _check(load().psweep_profile(self.h, int(capacity)))
+
+    def profile_read(self):
+        """(summed ms per stage [prep, sweep kernel, merge], calls recorded)."""
+        ms = (C.c_double * 3)()
+        n = C.c_int32()
+        _check(load().psweep_profile_read(self.h, ms, C.byref(n)))
+        return list(ms), n.value
+
+    def level_shapes(self):
+        return [level_shape(self.rig.ref, lv) for lv in self.levels]
+
+    def alloc_level_outputs(self, device="cuda"):
+        outs = []
+        for (h, w) in self.level_shapes():
+            outs.append(dict(depth=torch.empty((h, w), dtype=torch.float32, device=device),
+                             c1=torch.empty((h, w), dtype=torch.float32, device=device),
+                             c2=torch.empty((h, w), dtype=torch.float32, device=device),
+                             kstar=torch.empty((h, w), dtype=torch.int32, device=device)))
+        return outs
+
+    def depth(self, images: Sequence[torch.Tensor], boxes=None, out: Optional[torch.Tensor] = None,
+              level_outs=None, stream=None) -> torch.Tensor:
+        """images: [ref, cam_1, ...] contiguous uint8 CUDA tensors (H, W)."""
+        n = 1 + len(self.rig.cams)
+        if len(images) != n:
+            raise ValueError(f"expected {n} images")
+        ptrs = (C.c_void_p * n)(*[_dev(im, torch.uint8, f"images[{i}]") for i, im in enumerate(images)])
+        if out is None:
+            out = torch.empty((self.rig.ref.height, self.rig.ref.width), dtype=torch.float32,
+                              device=images[0].device)
+        bx, nb = boxes_array(boxes)
+        lo = None
+        if level_outs is not None:
+            lo = (ps_level_out * len(self.levels))()
+            for i, o in enumerate(level_outs):
+                lo[i] = ps_level_out(
+                    _dev(o["depth"], torch.float32, "depth") if o.get("depth") is not None else None,
+                    _dev(o["c1"], torch.float32, "c1") if o.get("c1") is not None else None,
+                    _dev(o["c2"], torch.float32, "c2") if o.get("c2") is not None else None,
+                    _dev(o["kstar"], torch.int32, "kstar") if o.get("kstar") is not None else None)
+        _check(load().psweep_depth(self.h, ptrs, bx, nb, _dev(out, torch.float32, "out"), lo, _stream_ptr(stream)))
+        return out
+
+    def frame_host(self, host_images: Sequence[np.ndarray], boxes=None, tsdf: "Tsdf" = None, world_to_ref=None,
+                   local_center=None, depth_out: Optional[np.ndarray] = None, stream=None):
+        """One frame from host memory: H2D copies, depth, optional fusion, D2H depth (synchronous)."""
+        n = 1 + len(self.rig.cams)
+        arrs = [np.ascontiguousarray(a, dtype=np.uint8) if isinstance(a, np.ndarray) else a for a in host_images]
+        ptrs = (C.c_void_p * n)(*[a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr() for a in arrs])
+        bx, nb = boxes_array(boxes)
+        pz = pose(world_to_ref) if world_to_ref is not None else None
+        lc = None if local_center is None else (C.c_double * 3)(*local_center)
+        dptr = None
+        if depth_out is not None:
+            dptr = depth_out.ctypes.data if isinstance(depth_out, np.ndarray) else depth_out.data_ptr()
+        _check(load().psweep_frame_host(self.h, tsdf.h if tsdf is not None else None, ptrs, bx, nb,
+                                        C.byref(pz) if pz is not None else None, lc, dptr, _stream_ptr(stream)))
+        return depth_out
+
+
+class Tsdf:
+    """TSDF volume of voxel blocks (tsdf_create / tsdf_integrate / tsdf_extract)."""
+
+    def __init__(self, params, cam):
+        L = load()
+        p = params
+        d = ps_tsdf_desc(cam=camera(cam), voxel_size=p.voxel_size, mu=p.mu, w_max=p.w_max, block_dim=p.block_dim,
+                         hash_slots=p.hash_slots, pool_blocks=p.pool_blocks)
+        if p.dense_dim is not None:
+            for i in range(3):
+                d.dense_dim[i] = p.dense_dim[i]
+        for i in range(3):
+            d.origin[i] = p.origin[i]
+            d.local_half[i] = p.local_half[i] if p.local_half is not None else 0.0
+        h = C.c_void_p()
+        _check(L.tsdf_create(C.byref(d), C.byref(h)))
+        self.h = h
+        self.params = p
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().tsdf_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def integrate(self, depth: torch.Tensor, world_to_cam, local_center=None, stream=None):
+        pz = pose(world_to_cam)
+        lc = None if local_center is None else (C.c_double * 3)(*local_center)
+        _check(load().tsdf_integrate(self.h, _dev(depth, torch.float32, "depth"), C.byref(pz), lc,
+                                     _stream_ptr(stream)))
+
+    def profile(self, capacity: int):
+        """Record stage events for the next `capacity` integrate calls (0 = off)."""
+        _check(load().tsdf_profile(self.h, int(capacity)))
+
+    def profile_read(self):
+        """(summed ms per stage [depth max, alloc, visible, integrate], calls recorded)."""
+        ms = (C.c_double * 4)()
+        n = C.c_int32()
+        _check(load().tsdf_profile_read(self.h, ms, C.byref(n)))
+        return list(ms), n.value
+
+    def count(self, stream=None) -> int:
+        n = C.c_int64()
+        _check(load().tsdf_count(self.h, C.byref(n), _stream_ptr(stream)))
+        return n.value
+
+    def status(self, stream=None) -> int:
+        return load().tsdf_status(self.h, _stream_ptr(stream))
+
+    def extract(self, min_weight: float = 0.0, device="cuda", stream=None):
+        """(keys (n, 3) int32, D (n, 512), W (n, 512)) as CUDA tensors, in pool order."""
+        n = self.count(stream)
+        keys = torch.empty((max(n, 1), 3), dtype=torch.int32, device=device)
+        D = torch.empty((max(n, 1), 512), dtype=torch.float32, device=device)
+        W = torch.empty((max(n, 1), 512), dtype=torch.float32, device=device)
+        m = C.c_int64()
+        _check(load().tsdf_extract(self.h, float(min_weight), keys.data_ptr(), D.data_ptr(), W.data_ptr(), n,
+                                   C.byref(m), _stream_ptr(stream)))
+        return keys[:m.value], D[:m.value], W[:m.value]
+
+
+def version() -> str:
+    return load().ps_version().decode()

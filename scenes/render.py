@@ -292,30 +292,37 @@ def cast(scene: Scene, origin: torch.Tensor, dirs: torch.Tensor):
         ok = ok & (a.abs() <= rc.a) & (b.abs() <= rc.b)
         take(s, ok, rc.tex_id, a, b, rc.texel)
 
-    for bx in scene.boxes:
-        lo = _vec(bx.lo, dev)
-        hi = _vec(bx.hi, dev)
-        inv = 1.0 / torch.where(dirs.abs() > 1e-15, dirs, torch.full_like(dirs, 1e-15))
-        t0 = (lo[None, :] - origin[None, :]) * inv
-        t1 = (hi[None, :] - origin[None, :]) * inv
+    if scene.boxes:
+        # all boxes at once: slab test of every ray against every box
+        lo = torch.tensor([b.lo for b in scene.boxes], dtype=torch.float64, device=dev)   # (M, 3)
+        hi = torch.tensor([b.hi for b in scene.boxes], dtype=torch.float64, device=dev)
+        texel = torch.tensor([b.texel for b in scene.boxes], dtype=torch.float64, device=dev)
+        tid = torch.tensor([b.tex_id for b in scene.boxes], dtype=torch.int64, device=dev)
+        inv = 1.0 / torch.where(dirs.abs() > 1e-15, dirs, torch.full_like(dirs, 1e-15))  # (N, 3)
+        t0 = (lo[None, :, :] - origin[None, None, :]) * inv[:, None, :]                    # (N, M, 3)
+        t1 = (hi[None, :, :] - origin[None, None, :]) * inv[:, None, :]
         tmin = torch.minimum(t0, t1)
         tmax = torch.maximum(t0, t1)
-        tenter, axis = tmin.max(dim=1)
-        texit = tmax.min(dim=1).values
+        del t0, t1
+        tenter, axis = tmin.max(dim=2)                                                   # (N, M)
+        texit = tmax.min(dim=2).values
+        del tmin, tmax
         hit = (tenter <= texit) & (tenter > eps)
-        P = origin[None, :] + tenter[:, None] * dirs
-        # face texture coordinates: the two axes other than the entry axis
-        su = torch.where(axis == 0, P[:, 2], P[:, 0])
-        sv = torch.where(axis == 1, P[:, 2], P[:, 1])
-        face = axis * 2 + (dirs.gather(1, axis[:, None])[:, 0] > 0).to(torch.int64)
-        take(tenter, hit, bx.tex_id * 8 + face, su, sv, bx.texel)
+        tenter = torch.where(hit, tenter, torch.full_like(tenter, math.inf))
+        tb, mb = tenter.min(dim=1)                                                       # nearest box per ray
+        ax = axis.gather(1, mb[:, None])[:, 0]
+        P = origin[None, :] + tb.clamp(max=1e300)[:, None] * dirs
+        su = torch.where(ax == 0, P[:, 2], P[:, 0])
+        sv = torch.where(ax == 1, P[:, 2], P[:, 1])
+        face = ax * 2 + (dirs.gather(1, ax[:, None])[:, 0] > 0).to(torch.int64)
+        take(tb, torch.isfinite(tb), tid[mb] * 8 + face, su, sv, texel[mb])
     return best, val
 
 
 class Renderer:
     """Caches per-camera subpixel rays and renders views of a scene."""
 
-    def __init__(self, cam: Camera, ss: int = 2, device: str = "cpu", chunk: int = 1 << 20):
+    def __init__(self, cam: Camera, ss: int = 2, device: str = "cpu", chunk: int = 1 << 18):
         self.cam = cam
         self.ss = ss
         self.device = device

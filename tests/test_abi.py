@@ -1,0 +1,76 @@
+"""The C ABI library builds for sm_103a, loads without a GPU, exports every
+entry point include/psweep.h declares, and rejects bad arguments before any
+CUDA call."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import paper_1809_06132_gb300 as P
+from paper_1809_06132_gb300 import psweep as B
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "psweep.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(\w+)\s*\(", txt, flags=re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = P.load()
+    names = _declared()
+    assert set(names) == set(P.EXPORTS)
+    for n in names:
+        assert hasattr(L, n), n
+    assert "sm_103a" in P.version()
+
+
+def test_struct_sizes_match_header_layout():
+    # the ctypes mirrors must match the C layout (natural alignment)
+    assert C.sizeof(B.ps_camera) == 10 * 8 + 2 * 4
+    assert C.sizeof(B.ps_pose) == 12 * 8
+    assert C.sizeof(B.ps_plane_set) == 8 + 2 * 8 + 3 * 8
+    assert C.sizeof(B.ps_level) == 6 * 4 + 4 * C.sizeof(B.ps_plane_set)
+    assert C.sizeof(B.ps_box) == 16
+
+
+def test_argument_errors_without_gpu():
+    L = P.load()
+    h = C.c_void_p()
+    assert L.psweep_create(None, C.byref(h)) == P.PS_ERR_ARG
+    assert b"NULL" in L.ps_last_error()
+    d = B.ps_sweep_desc()
+    d.ref = B.ps_camera(xi=1.0, fx=80, fy=80, cx=80, cy=64, r2_max=1e30, width=160, height=128)
+    d.n_cams = 0
+    assert L.psweep_create(C.byref(d), C.byref(h)) == P.PS_ERR_ARG
+    assert h.value is None
+    cams = (B.ps_camera * 1)(d.ref)
+    poses = (B.ps_pose * 1)()
+    lv = (B.ps_level * 1)()
+    lv[0].kind = 0
+    lv[0].factor = 1
+    lv[0].window = 6          # unsupported window
+    lv[0].n_sets = 1
+    lv[0].sets[0] = B.ps_plane_set(family=0, count=8, a=0.5, b=20.0)
+    d.n_cams, d.cams, d.ref_to_cam, d.n_levels, d.levels = 1, cams, poses, 1, lv
+    assert L.psweep_create(C.byref(d), C.byref(h)) == P.PS_ERR_ARG
+    assert b"window" in L.ps_last_error()
+    lv[0].window = 5
+    lv[0].factor = 3          # does not divide 160x128
+    assert L.psweep_create(C.byref(d), C.byref(h)) == P.PS_ERR_ARG
+    lv[0].factor = 1
+    lv[0].sets[0] = B.ps_plane_set(family=0, count=8, a=5.0, b=1.0)   # near > far
+    assert L.psweep_create(C.byref(d), C.byref(h)) == P.PS_ERR_ARG
+    td = B.ps_tsdf_desc()
+    td.cam = d.ref
+    td.voxel_size, td.mu, td.w_max, td.block_dim = 0.1, 0.5, 100.0, 4
+    assert L.tsdf_create(C.byref(td), C.byref(h)) == P.PS_ERR_ARG
+    td.block_dim = 8
+    td.hash_slots = 1000      # not a power of two
+    td.pool_blocks = 16
+    assert L.tsdf_create(C.byref(td), C.byref(h)) == P.PS_ERR_ARG
+    assert L.psweep_depth(None, None, None, 0, None, None, None) == P.PS_ERR_ARG
+    assert L.tsdf_integrate(None, None, None, None, None) == P.PS_ERR_ARG

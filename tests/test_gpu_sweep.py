@@ -1,0 +1,164 @@
+"""GPU parity of the plane sweep (psweep_depth through the C ABI) with the
+FP64 oracle on seeded synthetic scenes."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import scenes
+from tests.parity import assert_sweep_parity, sweep_stats
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1809_06132_gb300 as P  # noqa: E402
+
+
+def _gpu_levels(sw, imgs, boxes=None):
+    dev = [torch.from_numpy(np.ascontiguousarray(i)).cuda() for i in imgs]
+    outs = sw.alloc_level_outputs()
+    depth = sw.depth(dev, boxes=boxes, level_outs=outs)
+    torch.cuda.synchronize()
+    res = [{k: v.cpu().numpy() for k, v in o.items()} for o in outs]
+    return depth.cpu().numpy(), res
+
+
+@pytest.fixture(scope="module")
+def tiny_frame():
+    wl = scenes.tiny(0)
+    imgs, rng = scenes.FrameSource(wl).frame(0, with_range=True)
+    return wl, [i.numpy() for i in imgs]
+
+
+def test_tiny_full_frame_parity(tiny_frame):
+    wl, imgs = tiny_frame
+    o = oracle.sweep_level(wl.rig, wl.levels[0], imgs)
+    sw = P.Sweep(wl.rig, wl.levels)
+    depth, g = _gpu_levels(sw, imgs)
+    s = assert_sweep_parity(o, g[0], min_gated=2000)
+    print("tiny", s)
+    # no boxes, one level at factor 1: the merged map is the level map
+    assert np.array_equal(depth, g[0]["depth"])
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_tiny_more_seeds(seed):
+    wl = scenes.tiny(seed)
+    imgs, _ = scenes.FrameSource(wl).frame(0)
+    imgs = [i.numpy() for i in imgs]
+    o = oracle.sweep_level(wl.rig, wl.levels[0], imgs)
+    _, g = _gpu_levels(P.Sweep(wl.rig, wl.levels), imgs)
+    assert_sweep_parity(o, g[0], min_gated=2000)
+
+
+@pytest.fixture(scope="module")
+def street_small():
+    wl = scenes.street(0, n_frames=1, scale=0.25)
+    imgs, _ = scenes.FrameSource(wl).frame(0)
+    return wl, [i.numpy() for i in imgs]
+
+
+def test_street_small_levels_and_merge(street_small):
+    wl, imgs = street_small
+    boxes = wl.boxes[0]
+    sw = P.Sweep(wl.rig, wl.levels)
+    depth, g = _gpu_levels(sw, imgs, boxes)
+    o = oracle.depth_frame(wl, imgs, boxes)
+    for lv, ol, gl in zip(wl.levels, o["levels"], g):
+        s = assert_sweep_parity(ol, gl, min_gated=500)
+        print("street-small level", lv.kind, s)
+    # merged map: same source pixel rule and masks
+    od = o["depth"]
+    both = (od > 0) & (depth > 0)
+    assert ((od > 0) != (depth > 0)).mean() < 0.002
+    rel = np.abs(depth[both] - od[both]) / od[both]
+    assert (rel <= 1e-4).mean() >= 0.995
+    H, W = depth.shape
+    for (x0, y0, x1, y1) in boxes:
+        assert (depth[max(0, y0):min(H, y1), max(0, x0):min(W, x1)] == 0).all()
+
+
+def test_street_full_size_sampled(street_full):
+    wl, imgs, sw, depth, g = street_full
+    rng = np.random.default_rng(7)
+    for li, lv in enumerate(wl.levels):
+        H, W = g[li]["kstar"].shape
+        rho = lv.window // 2
+        pix = np.stack([rng.integers(rho, W - rho, 300), rng.integers(rho, H - rho, 300)], axis=1)
+        o = oracle.sweep_level(wl.rig, lv, imgs, pix=pix)
+        gs = {k: v[pix[:, 1], pix[:, 0]] for k, v in g[li].items()}
+        s = sweep_stats(o, gs)
+        print("street-full level", lv.kind, s)
+        assert s["n_gated"] >= 60, s
+        assert s["valid_mismatch"] <= 0.01, s
+        assert s["index_agree"] >= 0.99, s
+        assert s["depth_ok"] >= 0.99, s
+
+
+@pytest.fixture(scope="module")
+def street_full():
+    wl = scenes.street(0, n_frames=1, scale=1.0)
+    imgs, _ = scenes.FrameSource(wl, device="cuda").frame(0)
+    imgs = [i.numpy() for i in imgs]
+    sw = P.Sweep(wl.rig, wl.levels)
+    depth, g = _gpu_levels(sw, imgs, wl.boxes[0])
+    return wl, imgs, sw, depth, g
+
+
+def test_full_size_structure(street_full):
+    wl, imgs, sw, depth, g = street_full
+    assert depth.shape == (1024, 1280)
+    assert g[0]["kstar"].shape == (256, 320) and g[1]["kstar"].shape == (512, 640)
+    for gl, lv in zip(g, wl.levels):
+        v = gl["kstar"] >= 0
+        assert v.mean() > 0.3
+        assert ((gl["depth"] > 0) == v).all()
+        assert (gl["kstar"] < lv.n_planes).all()
+        assert (gl["c1"][v] <= gl["c2"][v]).all()
+        assert (gl["c1"][v] >= -1e-6).all() and (gl["c1"][v] <= 1 + 1e-6).all()
+
+
+def test_deterministic_and_optional_outputs(street_small):
+    wl, imgs = street_small
+    sw = P.Sweep(wl.rig, wl.levels)
+    dev = [torch.from_numpy(i).cuda() for i in imgs]
+    a = sw.depth(dev, boxes=wl.boxes[0]).clone()
+    b = sw.depth(dev, boxes=wl.boxes[0], level_outs=sw.alloc_level_outputs()).clone()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_boxes_edge_cases(street_small):
+    wl, imgs = street_small
+    sw = P.Sweep(wl.rig, wl.levels)
+    dev = [torch.from_numpy(i).cuda() for i in imgs]
+    H, W = imgs[0].shape
+    base = sw.depth(dev).clone()
+    allbox = sw.depth(dev, boxes=np.array([[0, 0, W, H]])).clone()
+    assert (allbox == 0).all()
+    # many boxes (more than fit in the kernel parameters), some empty or outside
+    rng = np.random.default_rng(3)
+    bx = np.concatenate([rng.integers(0, W, (40, 1)), rng.integers(0, H, (40, 1))], axis=1)
+    boxes = np.concatenate([bx, bx + rng.integers(0, 30, (40, 2))], axis=1).astype(np.int32)
+    boxes[5] = (10, 10, 10, 10)
+    boxes[6] = (W + 5, H + 5, W + 50, H + 50)
+    out = sw.depth(dev, boxes=boxes).cpu().numpy()
+    mask = np.zeros((H, W), bool)
+    for x0, y0, x1, y1 in boxes:
+        mask[max(0, y0):max(0, min(H, y1)), max(0, x0):max(0, min(W, x1))] = True
+    b = base.cpu().numpy()
+    assert (out[mask] == 0).all()
+    assert np.array_equal(out[~mask], b[~mask])
+
+
+def test_argument_errors_on_gpu(street_small):
+    wl, imgs = street_small
+    sw = P.Sweep(wl.rig, wl.levels)
+    dev = [torch.from_numpy(i).cuda() for i in imgs]
+    with pytest.raises(ValueError):
+        sw.depth(dev[:2])
+    with pytest.raises(P.PsError) as e:
+        sw.depth(dev, boxes=np.zeros((300, 4), np.int32))
+    assert e.value.status == P.PS_ERR_ARG

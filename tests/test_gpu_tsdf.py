@@ -1,0 +1,118 @@
+"""GPU parity of TSDF fusion (tsdf_integrate / tsdf_extract through the C ABI)
+with the FP64 oracle.  Both sides fuse the same float32 depth maps (the
+renderer's true range maps with the frame's boxes masked), so fusion parity
+does not depend on the sweep."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import scenes
+from scenes.configs import TsdfParams
+from tests.parity import TSDF_ABS, tsdf_compare
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1809_06132_gb300 as P  # noqa: E402
+
+
+def _masked(rng_map, boxes):
+    d = rng_map.numpy().astype(np.float32).copy()
+    H, W = d.shape
+    for x0, y0, x1, y1 in boxes:
+        d[max(0, y0):min(H, y1), max(0, x0):min(W, x1)] = 0
+    return d
+
+
+def _run(wl, frames, src, params=None):
+    p = params or wl.tsdf
+    T = P.Tsdf(p, wl.rig.ref)
+    O = oracle.Tsdf(p)
+    for f in frames:
+        _, rng = src.frame(f, with_range=True)
+        d = _masked(rng, wl.boxes[f])
+        T.integrate(torch.from_numpy(d).cuda(), wl.world_to_ref[f], wl.local_center(f))
+        O.integrate(d, wl.rig.ref, wl.world_to_ref[f], wl.local_center(f))
+    assert T.status() == P.PS_OK
+    k, D, W = T.extract()
+    return T, O, k.cpu().numpy(), D.cpu().numpy(), W.cpu().numpy()
+
+
+def test_tiny_dense_parity():
+    wl = scenes.tiny(0, n_frames=4)
+    src = scenes.FrameSource(wl)
+    T, O, gk, gD, gW = _run(wl, range(4), src)
+    ok, oD, oW, oamb = O.dump()
+    assert len(gk) == len(ok) == 512
+    s = tsdf_compare(ok, oD, oW, oamb, gk, gD, gW)
+    print("tiny dense", s)
+    assert s["n_common"] == 512
+    assert s["n_updated"] > 5000
+    assert s["n_amb"] < 0.01 * s["n_voxels"]
+    assert s["D_abs_max"] <= TSDF_ABS, s
+    assert s["W_mismatch"] == 0, s
+
+
+def test_street_small_hashed_parity():
+    wl = scenes.street(0, n_frames=6, scale=0.25)
+    src = scenes.FrameSource(wl)
+    T, O, gk, gD, gW = _run(wl, range(6), src)
+    ok, oD, oW, oamb = O.dump()
+    gset = set(map(tuple, gk.tolist()))
+    oset = set(map(tuple, ok.tolist()))
+    maybe = set(map(tuple, O.ever_maybe().tolist()))
+    amb_blocks = {tuple(k) for k, a in zip(ok.tolist(), oamb) if a.all()}
+    # every block the oracle allocates unambiguously exists on the GPU, and
+    # the GPU allocates nothing outside the oracle's set and ambiguity band
+    assert (oset - amb_blocks) <= gset
+    assert gset <= (oset | maybe)
+    s = tsdf_compare(ok, oD, oW, oamb, gk, gD, gW)
+    print("street-small hashed", s, "blocks", len(gset), len(oset))
+    assert s["n_updated"] > 10000
+    assert s["D_abs_max"] <= TSDF_ABS, s
+    assert s["W_mismatch"] == 0, s
+
+
+def test_min_weight_filter_and_count():
+    wl = scenes.tiny(1, n_frames=3)
+    src = scenes.FrameSource(wl)
+    T, O, gk, gD, gW = _run(wl, range(3), src)
+    k3, D3, W3 = T.extract(min_weight=3)
+    W3 = W3.cpu().numpy()
+    D3 = D3.cpu().numpy()
+    assert ((W3 == 0) | (W3 >= 3)).all()
+    keep = gW >= 3
+    assert np.array_equal(W3[keep], gW[keep]) and np.array_equal(D3[keep], gD[keep])
+    assert (D3[~keep] == 0).all()
+    assert T.count() == 512
+
+
+def test_pool_capacity_is_reported():
+    wl = scenes.street(0, n_frames=1, scale=0.25)
+    src = scenes.FrameSource(wl)
+    p = TsdfParams(voxel_size=0.1, mu=0.5, local_half=(30.0, 1.5, 30.0), local_offset=(0.0, 0.6, 0.0),
+                   hash_slots=1 << 12, pool_blocks=8)
+    T = P.Tsdf(p, wl.rig.ref)
+    _, rng = src.frame(0, with_range=True)
+    d = torch.from_numpy(_masked(rng, wl.boxes[0])).cuda()
+    T.integrate(d, wl.world_to_ref[0], wl.local_center(0))
+    assert T.status() == P.PS_ERR_CAPACITY
+    assert T.status() == P.PS_OK       # status is cleared once read
+    assert T.count() == 8
+    # the map stays usable: another frame runs and the overflow is reported again
+    T.integrate(d, wl.world_to_ref[0], wl.local_center(0))
+    assert T.status() == P.PS_ERR_CAPACITY
+
+
+def test_local_center_required():
+    wl = scenes.street(0, n_frames=1, scale=0.25)
+    T = P.Tsdf(wl.tsdf, wl.rig.ref)
+    d = torch.zeros((wl.rig.ref.height, wl.rig.ref.width), dtype=torch.float32, device="cuda")
+    with pytest.raises(P.PsError) as e:
+        T.integrate(d, wl.world_to_ref[0], None)
+    assert e.value.status == P.PS_ERR_ARG
+    T.integrate(d, wl.world_to_ref[0], wl.local_center(0))   # empty depth: nothing allocated
+    assert T.count() == 0
