@@ -262,7 +262,7 @@ def run_ours(args):
     sw = P.Sweep(wl.rig, wl.levels)
     T = P.Tsdf(wl.tsdf, wl.rig.ref)
     depth = torch.empty((H, W), dtype=torch.float32, device=dev)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     def step(i):
         f = i % nf
@@ -355,7 +355,7 @@ def run_ours(args):
         "config": {"workload": wl.name, "ref": f"{W}x{H}", "matching_cams": len(wl.rig.cams),
                    "levels": "320x256 (64 fronto + 32 ground, 7x7) + 640x512 crop (128 fronto, 9x9)",
                    "tsdf": "8^3 blocks, 0.1 m voxels, mu 0.5 m, 60x3x60 m local map", "frames": nf,
-                   "l2": "flushed between steps (512 MB write outside the step events)",
+                   "l2": "flushed between steps (256 MB write outside the step events)",
                    "parallelism": f"replicas x{world} (independent sequences)"},
         "sweep": {"value": pix_planes / (depth_ms * 1e-3) / 1e9, "unit": "Gpix·planes/s",
                   "kernel_only": pix_planes / (k_ms * 1e-3) / 1e9,

@@ -31,9 +31,12 @@ namespace ps {
 namespace {
 
 constexpr int TW = 64;   // output tile width (pixels)
-constexpr int TH = 16;   // output tile height
-constexpr int NT = 256;  // threads per CTA: one thread per 4-pixel run of a tile row
-static_assert(NT == (TW / 4) * TH, "one thread per 4-pixel output run");
+constexpr int TH = 24;   // output tile height
+constexpr int NT = 256;  // threads per CTA
+constexpr int RUN = 8;   // outputs per horizontal run (phase H)
+constexpr int SEG = 6;   // output rows per vertical segment (phase V)
+static_assert(NT == TW * (TH / SEG), "phase V: one thread per column and row segment");
+static_assert(NT / 32 == TW / RUN, "phase H: one warp per run, one lane per halo row");
 
 struct PlaneD {
     float nx, ny, nz, d;  // plane n . X = d (reference frame)
@@ -56,11 +59,12 @@ struct LevelD {
     int n_planes, n_sets;
     SetD sets[PS_MAX_SETS];
     const PlaneD* planes;
-    const float4* rays;  // (rx, ry, rz, 0), NaN where the pixel has no ray
-    const float* ref;    // centred intensities
+    const float4* rays;   // (rx, ry, rz, 0), NaN where the pixel has no ray
+    const float* ref;     // centred intensities
+    const float2* stats;  // reference window mean and sum of squared deviations
     int n_cams;
     CamJ cams[PS_MAX_CAMS];
-    int tiles_x, tiles_y, tile_begin;
+    int tiles_x, tiles_y, n_tiles;
     float* depth;
     float* c1;
     float* c2;
@@ -195,16 +199,50 @@ __global__ void quad_level_kernel(const uint8_t* img, int W, int s, int Wl, int 
     out[(size_t)y * Wl + x] = q;
 }
 
+// ------------------------------------------------------------- reference statistics
+
+// Mean and sum of squared deviations of the reference window around every
+// level pixel (two-pass, direct sums); var = -1 where the window leaves the
+// image.  Computed once per frame, read by the sweep for every plane.
+__global__ void ref_stats_kernel(const float* ref, int W, int H, int rho, float2* out) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y;
+    if (x >= W || y >= H) return;
+    float2 o = make_float2(0.f, -1.f);
+    if (x >= rho && y >= rho && x < W - rho && y < H - rho) {
+        float s = 0.f;
+        for (int dy = -rho; dy <= rho; ++dy)
+            for (int dx = -rho; dx <= rho; ++dx) s += ref[(size_t)(y + dy) * W + x + dx];
+        float m = s / (float)((2 * rho + 1) * (2 * rho + 1));
+        float v = 0.f;
+        for (int dy = -rho; dy <= rho; ++dy)
+            for (int dx = -rho; dx <= rho; ++dx) {
+                float e = ref[(size_t)(y + dy) * W + x + dx] - m;
+                v = fmaf(e, e, v);
+            }
+        o = make_float2(m, v);
+    }
+    out[(size_t)y * W + x] = o;
+}
+
 // ------------------------------------------------------------- sweep
 
-// Bilinear sample of matching camera j at the projection of X_j (camera
+// Matching camera as the sweep reads it (staged in shared memory per tile).
+struct CamS {
+    float R[9], t[3];
+    float xi, fx, fy, cx, cy, k1, k2, p1, p2, r2_max, lim, wm1, hm1;
+    int width;
+    const float4* quad;
+};
+
+// Bilinear sample of a matching camera at the projection of X_j (camera
 // frame); NaN when the point does not project (sphere side, distortion
-// range) or lands outside [0, W-1] x [0, H-1].
-__device__ __forceinline__ float warp_sample(const CamJ& C, float X, float Y, float Z) {
-    const CamF& c = C.cam;
-    float n = sqrtf(fmaf(X, X, fmaf(Y, Y, Z * Z)));
-    float den = fmaf(c.xi, n, Z);
-    float inv = 1.0f / den;
+// range) or lands outside [0, W-1] x [0, H-1].  The gather is clamped into
+// the image and always issued, so the warp does not diverge.
+__device__ __forceinline__ float warp_sample(const CamS& c, float X, float Y, float Z) {
+    float n2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
+    float n = n2 * rsqrtf(n2);
+    float inv = __fdividef(1.0f, fmaf(c.xi, n, Z));
     float mx = X * inv, my = Y * inv;
     float r2 = fmaf(mx, mx, my * my);
     float rad = fmaf(r2, fmaf(c.k2, r2, c.k1), 1.0f);
@@ -213,40 +251,54 @@ __device__ __forceinline__ float warp_sample(const CamJ& C, float X, float Y, fl
     float yd = fmaf(my, rad, fmaf(c.p1, fmaf(2.0f * my, my, r2), 2.0f * c.p2 * mxy));
     float u = fmaf(c.fx, xd, c.cx);
     float v = fmaf(c.fy, yd, c.cy);
-    bool ok = (Z > c.lim * n) && (r2 <= c.r2_max) && (u >= 0.0f) && (u <= (float)(c.width - 1)) &&
-              (v >= 0.0f) && (v <= (float)(c.height - 1));
-    if (!ok) return __int_as_float(0x7fc00000);
-    int x0 = (int)u, y0 = (int)v;
-    float ax = u - (float)x0, ay = v - (float)y0;
-    float4 q = __ldg(&C.quad[(size_t)y0 * c.width + x0]);
+    bool ok = (Z > c.lim * n) && (r2 <= c.r2_max) && (u >= 0.0f) && (u <= c.wm1) && (v >= 0.0f) && (v <= c.hm1);
+    float uc = fminf(fmaxf(u, 0.0f), c.wm1), vc = fminf(fmaxf(v, 0.0f), c.hm1);
+    int x0 = (int)uc, y0 = (int)vc;
+    float ax = uc - (float)x0, ay = vc - (float)y0;
+    float4 q = __ldg(&c.quad[y0 * c.width + x0]);
     float top = fmaf(ax, q.y - q.x, q.x);
     float bot = fmaf(ax, q.w - q.z, q.z);
-    return fmaf(ay, bot - top, top);
+    float w = fmaf(ay, bot - top, top);
+    return ok ? w : __int_as_float(0x7fc00000);
 }
 
+// Tile geometry.  A CTA owns TW x TH output pixels of one level plus a halo of
+// RHO on every side (HH rows x HWL columns of warped samples per plane and
+// camera).  Phase A: every thread warps PPT halo positions into W.  Phase
+// H: thread (row, run) slides a 2 RHO + 1 window along 8 outputs of one halo
+// row and stores (sum w, sum w^2, sum r w, invalid count) in H.  Phase V:
+// thread (column, segment) slides down SEG output rows, forms ZNCC and keeps
+// the minimum over cameras.  Strides are chosen so that each phase's
+// shared-memory accesses are free of bank conflicts.
 template <int RHO>
-struct Tile {
-    static constexpr int HWL = TW + 2 * RHO;          // logical halo width
-    static constexpr int HW = (HWL + 3) & ~3;         // padded row stride (float4 rows)
-    static constexpr int HH = TH + 2 * RHO;
+struct Geo {
+    static constexpr int HH = TH + 2 * RHO;           // halo rows (<= 32)
+    static constexpr int HWL = TW + 2 * RHO;          // halo columns
+    static constexpr int WS = 76;                     // W / R row stride (floats): 76 = 12 mod 32
+    static constexpr int HS = TW + 1;                 // H row stride (float4): odd
     static constexpr int NPOS = HH * HWL;
+    static constexpr int PPT = (NPOS + NT - 1) / NT;
+    static constexpr int NRUNPOS = RUN + 2 * RHO;     // positions one horizontal run reads
+    static constexpr int NV = (NRUNPOS + 3) / 4;      // float4 loads per run
     static constexpr int N = (2 * RHO + 1) * (2 * RHO + 1);
-    static constexpr int NV = (4 + 2 * RHO + 3) / 4;  // float4 loads per 4-output run
-    static constexpr size_t smem_bytes =
-        sizeof(float) * 2 * HH * HW + sizeof(float4) * (4 * HH * (TW / 4) + NPOS);
+    static constexpr size_t smem =
+        sizeof(float4) * (size_t)(NPOS + HH * HS) + sizeof(float) * 2 * HH * WS + sizeof(float2) * TH * TW;
+    static_assert(HH <= 32, "phase H maps one warp lane per halo row");
+    static_assert(HWL <= WS && 4 * NV + TW - RUN <= WS, "row stride covers the runs' loads");
 };
 
 template <int RHO>
-__device__ void sweep_tile(const LevelD& L, int tile, unsigned char* smem_raw) {
-    using T = Tile<RHO>;
-    constexpr int HW = T::HW, HH = T::HH, HWL = T::HWL, NPOS = T::NPOS, N = T::N;
-    float* Rs = reinterpret_cast<float*>(smem_raw);
-    float* Ws = Rs + HH * HW;
-    float4* Hs = reinterpret_cast<float4*>(Ws + HH * HW);  // [4][HH][TW/4]
-    float4* Ray = Hs + 4 * HH * (TW / 4);                  // [NPOS]
+__device__ void sweep_tile(const LevelD& L, const CamS* cams, int tile, unsigned char* smem_raw) {
+    using G = Geo<RHO>;
+    constexpr int HH = G::HH, HWL = G::HWL, WS = G::WS, HS = G::HS, NPOS = G::NPOS, N = G::N;
+    float4* Ray = reinterpret_cast<float4*>(smem_raw);  // [NPOS] (rx, ry, rz, 1 / n.r)
+    float4* Hs = Ray + NPOS;                             // [HH][HS]
+    float* Ws = reinterpret_cast<float*>(Hs + HH * HS);  // [HH][WS] warped samples (NaN = invalid)
+    float* Rs = Ws + HH * WS;                            // [HH][WS] reference intensities
+    float2* St = reinterpret_cast<float2*>(Rs + HH * WS); // [TH][TW] (mean, 1/sqrt(var)) of the reference window, NaN = none
     const int tid = threadIdx.x;
     const int tx = tile % L.tiles_x, ty = tile / L.tiles_x;
-    const int gx0 = tx * TW - RHO, gy0 = ty * TH - RHO;  // halo origin in level pixels
+    const int gx0 = tx * TW - RHO, gy0 = ty * TH - RHO;
     const float nan = __int_as_float(0x7fc00000);
     const float inf = __int_as_float(0x7f800000);
 
@@ -254,138 +306,127 @@ __device__ void sweep_tile(const LevelD& L, int tile, unsigned char* smem_raw) {
         int hy = p / HWL, hx = p - hy * HWL;
         int gx = gx0 + hx, gy = gy0 + hy;
         bool in = gx >= 0 && gy >= 0 && gx < L.W && gy < L.H;
-        Rs[hy * HW + hx] = in ? L.ref[(size_t)gy * L.W + gx] : 0.0f;
+        Rs[hy * WS + hx] = in ? L.ref[(size_t)gy * L.W + gx] : 0.0f;
         Ray[p] = in ? L.rays[(size_t)gy * L.W + gx] : make_float4(nan, nan, nan, 0.f);
     }
-    __syncthreads();
 
-    // this thread's outputs: run c (4 pixels) of tile row oy
-    const int c = tid % (TW / 4), oy = tid / (TW / 4);
-    float mu_r[4], var_r[4];
-    bool ovalid[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int gx = tx * TW + 4 * c + i, gy = ty * TH + oy;
-        float s = 0.f;
-        for (int dy = 0; dy <= 2 * RHO; ++dy)
-            for (int dx = 0; dx <= 2 * RHO; ++dx) s += Rs[(oy + dy) * HW + 4 * c + i + dx];
-        float m = s / (float)N;
-        float v = 0.f;
-        for (int dy = 0; dy <= 2 * RHO; ++dy)
-            for (int dx = 0; dx <= 2 * RHO; ++dx) {
-                float e = Rs[(oy + dy) * HW + 4 * c + i + dx] - m;
-                v = fmaf(e, e, v);
-            }
-        mu_r[i] = m;
-        var_r[i] = v;
-        ovalid[i] = gx >= RHO && gy >= RHO && gx < L.W - RHO && gy < L.H - RHO && v >= (float)N * 1e-8f;
+    for (int p = tid; p < TH * TW; p += NT) {
+        int y = p / TW, x = p - y * TW;
+        int gx = tx * TW + x, gy = ty * TH + y;
+        float2 st = make_float2(0.f, -1.f);
+        if (gx < L.W && gy < L.H) st = L.stats[(size_t)gy * L.W + gx];
+        St[p] = st.y >= (float)N * 1e-8f ? make_float2(st.x, rsqrtf(st.y)) : make_float2(nan, nan);
     }
-
-    // streaming winner-take-all state
-    float c1[4], c2[4], cprev[4], cminus[4], cplus[4];
-    int kb[4];
-    bool needp[4];
+    // outputs of this thread: column ox, rows oy0 .. oy0 + SEG - 1
+    const int ox = tid % TW, oy0 = (tid / TW) * SEG;
+    float c1[SEG], c2[SEG], cprev[SEG], cminus[SEG], cplus[SEG];
+    int kb[SEG];
+    bool needp[SEG];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < SEG; ++i) {
         c1[i] = c2[i] = cprev[i] = cminus[i] = cplus[i] = inf;
         kb[i] = -1;
         needp[i] = false;
     }
+    const int hrow = tid & 31, hrun = tid >> 5;  // phase H item
+    const int base_v = oy0 * HS + ox;            // phase V first H entry
+    __syncthreads();
 
     for (int s = 0; s < L.n_sets; ++s) {
-        const SetD S = L.sets[s];
+        const float snx = L.sets[s].nx, sny = L.sets[s].ny, snz = L.sets[s].nz;
         for (int p = tid; p < NPOS; p += NT) {
             float4 r = Ray[p];
-            float nr = S.nx * r.x + S.ny * r.y + S.nz * r.z;
+            float nr = snx * r.x + sny * r.y + snz * r.z;
             Ray[p].w = nr > 0.0f ? 1.0f / nr : nan;
         }
         __syncthreads();
-        for (int k = S.start; k < S.start + S.count; ++k) {
-            const float d = L.planes[k].d;
-            float cmin[4] = {inf, inf, inf, inf};
+        const int k_end = L.sets[s].start + L.sets[s].count;
+        for (int k = L.sets[s].start; k < k_end; ++k) {
+            const float d = __ldg(&L.planes[k].d);
+            float cmin[SEG];
+#pragma unroll
+            for (int i = 0; i < SEG; ++i) cmin[i] = inf;
             for (int j = 0; j < L.n_cams; ++j) {
-                const CamJ& C = L.cams[j];
+                const CamS& C = cams[j];
                 // phase A: warped samples of the tile + halo
-                for (int p = tid; p < NPOS; p += NT) {
-                    float4 r = Ray[p];
-                    float lam = d * r.w;
-                    float X = lam * r.x, Y = lam * r.y, Z = lam * r.z;
-                    float Xj = fmaf(C.R[0], X, fmaf(C.R[1], Y, fmaf(C.R[2], Z, C.t[0])));
-                    float Yj = fmaf(C.R[3], X, fmaf(C.R[4], Y, fmaf(C.R[5], Z, C.t[1])));
-                    float Zj = fmaf(C.R[6], X, fmaf(C.R[7], Y, fmaf(C.R[8], Z, C.t[2])));
-                    int hy = p / HWL, hx = p - hy * HWL;
-                    Ws[hy * HW + hx] = warp_sample(C, Xj, Yj, Zj);
+#pragma unroll 3
+                for (int i = 0; i < G::PPT; ++i) {
+                    int p = tid + i * NT;
+                    if (p < NPOS) {
+                        float4 r = Ray[p];
+                        float lam = d * r.w;
+                        float X = lam * r.x, Y = lam * r.y, Z = lam * r.z;
+                        float Xj = fmaf(C.R[0], X, fmaf(C.R[1], Y, fmaf(C.R[2], Z, C.t[0])));
+                        float Yj = fmaf(C.R[3], X, fmaf(C.R[4], Y, fmaf(C.R[5], Z, C.t[1])));
+                        float Zj = fmaf(C.R[6], X, fmaf(C.R[7], Y, fmaf(C.R[8], Z, C.t[2])));
+                        int hy = p / HWL, hx = p - hy * HWL;
+                        Ws[hy * WS + hx] = warp_sample(C, Xj, Yj, Zj);
+                    }
                 }
                 __syncthreads();
-                // phase H: horizontal window sums of w, w^2, r w, invalid count per 4-pixel run
-                for (int it = tid; it < HH * (TW / 4); it += NT) {
-                    int hy = it / (TW / 4), cc = it - hy * (TW / 4);
-                    float wv[4 * T::NV], rv[4 * T::NV];
+                // phase H: sliding horizontal sums along an 8-pixel run of one halo row
+                if (hrow < HH) {
+                    const float* wr = Ws + hrow * WS + RUN * hrun;
+                    const float* rr = Rs + hrow * WS + RUN * hrun;
+                    float w[4 * G::NV], r[4 * G::NV];
 #pragma unroll
-                    for (int q = 0; q < T::NV; ++q) {
-                        float4 a = *reinterpret_cast<const float4*>(&Ws[hy * HW + 4 * cc + 4 * q]);
-                        float4 b = *reinterpret_cast<const float4*>(&Rs[hy * HW + 4 * cc + 4 * q]);
-                        wv[4 * q] = a.x; wv[4 * q + 1] = a.y; wv[4 * q + 2] = a.z; wv[4 * q + 3] = a.w;
-                        rv[4 * q] = b.x; rv[4 * q + 1] = b.y; rv[4 * q + 2] = b.z; rv[4 * q + 3] = b.w;
+                    for (int q = 0; q < G::NV; ++q) {
+                        float4 a = *reinterpret_cast<const float4*>(wr + 4 * q);
+                        float4 b = *reinterpret_cast<const float4*>(rr + 4 * q);
+                        w[4 * q] = a.x; w[4 * q + 1] = a.y; w[4 * q + 2] = a.z; w[4 * q + 3] = a.w;
+                        r[4 * q] = b.x; r[4 * q + 1] = b.y; r[4 * q + 2] = b.z; r[4 * q + 3] = b.w;
                     }
-                    float m[4 + 2 * RHO];
+                    // invalid samples: excluded from the sums and counted
+                    float sw = 0.f, sww = 0.f, srw = 0.f, sm = 0.f;
 #pragma unroll
-                    for (int q = 0; q < 4 + 2 * RHO; ++q) {
-                        bool bad = isnan(wv[q]);
-                        m[q] = bad ? 1.0f : 0.0f;
-                        wv[q] = bad ? 0.0f : wv[q];
+                    for (int t = 0; t <= 2 * RHO; ++t) {
+                        bool bad = isnan(w[t]);
+                        float wt = bad ? 0.0f : w[t];
+                        sw += wt;
+                        sww = fmaf(wt, wt, sww);
+                        srw = fmaf(r[t], wt, srw);
+                        sm += bad ? 1.0f : 0.0f;
                     }
-                    float hw[4], hww[4], hrw[4], hm[4];
+                    float4* hrow_out = Hs + hrow * HS + RUN * hrun;
+                    hrow_out[0] = make_float4(sw, sww, srw, sm);
 #pragma unroll
-                    for (int o = 0; o < 4; ++o) {
-                        float a = 0.f, b = 0.f, e = 0.f, f = 0.f;
-#pragma unroll
-                        for (int q = 0; q <= 2 * RHO; ++q) {
-                            float w = wv[o + q];
-                            a += w;
-                            b = fmaf(w, w, b);
-                            e = fmaf(rv[o + q], w, e);
-                            f += m[o + q];
-                        }
-                        hw[o] = a;
-                        hww[o] = b;
-                        hrw[o] = e;
-                        hm[o] = f;
+                    for (int o = 1; o < RUN; ++o) {
+                        const int a = o + 2 * RHO, b = o - 1;
+                        bool ba = isnan(w[a]), bb = isnan(w[b]);
+                        float wa = ba ? 0.0f : w[a], wb = bb ? 0.0f : w[b];
+                        sw += wa - wb;
+                        sww += fmaf(wa, wa, -wb * wb);
+                        srw += fmaf(r[a], wa, -r[b] * wb);
+                        sm += (ba ? 1.0f : 0.0f) - (bb ? 1.0f : 0.0f);
+                        hrow_out[o] = make_float4(sw, sww, srw, sm);
                     }
-                    const int base = hy * (TW / 4) + cc;
-                    Hs[base] = make_float4(hw[0], hw[1], hw[2], hw[3]);
-                    Hs[HH * (TW / 4) + base] = make_float4(hww[0], hww[1], hww[2], hww[3]);
-                    Hs[2 * HH * (TW / 4) + base] = make_float4(hrw[0], hrw[1], hrw[2], hrw[3]);
-                    Hs[3 * HH * (TW / 4) + base] = make_float4(hm[0], hm[1], hm[2], hm[3]);
                 }
                 __syncthreads();
-                // phase V: vertical sums, ZNCC, cost, minimum over cameras
-                float4 sw = make_float4(0, 0, 0, 0), sww = sw, srw = sw, sm = sw;
+                // phase V: sliding vertical sums down SEG rows, ZNCC, minimum over cameras
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                 for (int dy = 0; dy <= 2 * RHO; ++dy) {
-                    const int base = (oy + dy) * (TW / 4) + c;
-                    float4 a = Hs[base], b = Hs[HH * (TW / 4) + base], e = Hs[2 * HH * (TW / 4) + base],
-                           f = Hs[3 * HH * (TW / 4) + base];
-                    sw.x += a.x; sw.y += a.y; sw.z += a.z; sw.w += a.w;
-                    sww.x += b.x; sww.y += b.y; sww.z += b.z; sww.w += b.w;
-                    srw.x += e.x; srw.y += e.y; srw.z += e.z; srw.w += e.w;
-                    sm.x += f.x; sm.y += f.y; sm.z += f.z; sm.w += f.w;
+                    float4 h = Hs[base_v + dy * HS];
+                    v.x += h.x; v.y += h.y; v.z += h.z; v.w += h.w;
                 }
-                const float vw[4] = {sw.x, sw.y, sw.z, sw.w}, vww[4] = {sww.x, sww.y, sww.z, sww.w},
-                            vrw[4] = {srw.x, srw.y, srw.z, srw.w}, vm[4] = {sm.x, sm.y, sm.z, sm.w};
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    float var_w = vww[i] - vw[i] * vw[i] * (1.0f / (float)N);
-                    float cov = vrw[i] - mu_r[i] * vw[i];
-                    bool ok = ovalid[i] && vm[i] == 0.0f && var_w >= (float)N * 1e-8f;
-                    float z = cov * rsqrtf(var_r[i] * var_w);
+                for (int i = 0; i < SEG; ++i) {
+                    if (i > 0) {
+                        float4 a = Hs[base_v + (i + 2 * RHO) * HS], b = Hs[base_v + (i - 1) * HS];
+                        v.x += a.x - b.x; v.y += a.y - b.y; v.z += a.z - b.z; v.w += a.w - b.w;
+                    }
+                    const float2 st = St[(oy0 + i) * TW + ox];   // NaN where the reference window is unusable
+                    float var_w = fmaf(-v.x * (1.0f / (float)N), v.x, v.y);
+                    float cov = fmaf(-st.x, v.x, v.z);
+                    bool ok = v.w == 0.0f && var_w >= (float)N * 1e-8f && !isnan(st.y);
+                    float z = fminf(1.0f, fmaxf(-1.0f, cov * st.y * rsqrtf(var_w)));  // |ZNCC| <= 1
                     float cost = fmaf(-0.5f, z, 0.5f);
-                    if (ok) cmin[i] = fminf(cmin[i], cost);
+                    cmin[i] = ok ? fminf(cmin[i], cost) : cmin[i];
                 }
             }
-            // winner-take-all update with the plane's aggregated cost
+            // streaming winner-take-all with the plane's aggregated cost
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < SEG; ++i) {
                 float cc = cmin[i];
                 if (needp[i]) {
                     cplus[i] = cc;
@@ -404,13 +445,12 @@ __device__ void sweep_tile(const LevelD& L, int tile, unsigned char* smem_raw) {
                 cprev[i] = cc;
             }
         }
-        __syncthreads();
     }
 
     // parabola through the winner and its neighbours in the same set; range
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int gx = tx * TW + 4 * c + i, gy = ty * TH + oy;
+    for (int i = 0; i < SEG; ++i) {
+        int gx = tx * TW + ox, gy = ty * TH + oy0 + i;
         if (gx >= L.W || gy >= L.H) continue;
         size_t o = (size_t)gy * L.W + gx;
         float depth = 0.f;
@@ -427,7 +467,7 @@ __device__ void sweep_tile(const LevelD& L, int tile, unsigned char* smem_raw) {
             float t = S.count > 1 ? ((float)li + delta) / (float)(S.count - 1) : 0.f;
             float param = S.family == PS_PLANES_FRONTO ? 1.0f / fmaf(t, 1.0f / S.a - 1.0f / S.b, 1.0f / S.b)
                                                        : fmaf(t, S.b - S.a, S.a);
-            float4 r = L.rays[o];
+            float4 r = Ray[(oy0 + i + RHO) * HWL + ox + RHO];
             float nr = S.nx * r.x + S.ny * r.y + S.nz * r.z;
             depth = param / nr;
         }
@@ -436,19 +476,50 @@ __device__ void sweep_tile(const LevelD& L, int tile, unsigned char* smem_raw) {
         if (L.c2) L.c2[o] = c2[i];
         if (L.kstar) L.kstar[o] = kb[i];
     }
+    __syncthreads();
 }
 
-__global__ void __launch_bounds__(NT) sweep_kernel(const __grid_constant__ SweepParams P) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    int b = blockIdx.x;
-    int l = 0;
-    while (l + 1 < P.n_levels && b >= P.lv[l + 1].tile_begin) ++l;
-    const LevelD& L = P.lv[l];
-    int tile = b - L.tile_begin;
+template <int LV>
+__device__ __forceinline__ void run_level(const SweepParams& P, int tile, CamS* cams, unsigned char* smem) {
+    const LevelD& L = P.lv[LV];
+    if (threadIdx.x < L.n_cams) {
+        const CamJ& J = L.cams[threadIdx.x];
+        CamS& c = cams[threadIdx.x];
+        for (int i = 0; i < 9; ++i) c.R[i] = J.R[i];
+        for (int i = 0; i < 3; ++i) c.t[i] = J.t[i];
+        c.xi = J.cam.xi; c.fx = J.cam.fx; c.fy = J.cam.fy; c.cx = J.cam.cx; c.cy = J.cam.cy;
+        c.k1 = J.cam.k1; c.k2 = J.cam.k2; c.p1 = J.cam.p1; c.p2 = J.cam.p2; c.r2_max = J.cam.r2_max;
+        c.lim = J.cam.lim;
+        c.wm1 = (float)(J.cam.width - 1);
+        c.hm1 = (float)(J.cam.height - 1);
+        c.width = J.cam.width;
+        c.quad = J.quad;
+    }
+    __syncthreads();
     switch (L.rho) {
-        case 2: sweep_tile<2>(L, tile, smem); break;
-        case 3: sweep_tile<3>(L, tile, smem); break;
-        default: sweep_tile<4>(L, tile, smem); break;
+        case 2: sweep_tile<2>(L, cams, tile, smem); break;
+        case 3: sweep_tile<3>(L, cams, tile, smem); break;
+        default: sweep_tile<4>(L, cams, tile, smem); break;
+    }
+}
+
+// Persistent CTAs take tiles from a counter; levels are ordered so the
+// heavier tiles start first.
+__global__ void __launch_bounds__(NT, 2) sweep_kernel(const __grid_constant__ SweepParams P, int* tile_counter) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ CamS cams[PS_MAX_CAMS];
+    __shared__ int s_tile;
+    const int total = P.lv[0].n_tiles + (P.n_levels > 1 ? P.lv[1].n_tiles : 0);
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1);
+        __syncthreads();
+        const int t = s_tile;
+        __syncthreads();
+        if (t >= total) break;
+        if (t < P.lv[0].n_tiles)
+            run_level<0>(P, t, cams, smem);
+        else
+            run_level<1>(P, t - P.lv[0].n_tiles, cams, smem);
     }
 }
 
@@ -545,7 +616,10 @@ struct psweep_s {
     float4* rays[PS_MAX_LEVELS] = {};
     PlaneD* planes[PS_MAX_LEVELS] = {};
     float* ref_img[PS_MAX_LEVELS] = {};
+    float2* stats[PS_MAX_LEVELS] = {};
     float4* quad[PS_MAX_LEVELS][PS_MAX_CAMS] = {};
+    int* tile_counter = nullptr;
+    int grid = 0;
     float* out_depth[PS_MAX_LEVELS] = {};
     float* out_c1[PS_MAX_LEVELS] = {};
     float* out_c2[PS_MAX_LEVELS] = {};
@@ -569,6 +643,7 @@ void free_sweep(psweep_t* h) {
         cudaFree(h->rays[l]);
         cudaFree(h->planes[l]);
         cudaFree(h->ref_img[l]);
+        cudaFree(h->stats[l]);
         for (int j = 0; j < PS_MAX_CAMS; ++j) cudaFree(h->quad[l][j]);
         cudaFree(h->out_depth[l]);
         cudaFree(h->out_c1[l]);
@@ -576,6 +651,7 @@ void free_sweep(psweep_t* h) {
         cudaFree(h->out_k[l]);
     }
     cudaFree(h->boxes_dev);
+    cudaFree(h->tile_counter);
     for (int i = 0; i <= PS_MAX_CAMS; ++i) cudaFree(h->stage_img[i]);
     cudaFree(h->stage_depth);
     delete h;
@@ -728,6 +804,7 @@ extern "C" int psweep_create(const ps_sweep_desc* d, psweep_t** out) {
             return PS_ERR_CUDA;
         }
         PS_TRY(cudaMalloc(&h->ref_img[l], sizeof(float) * (size_t)W * H));
+        PS_TRY(cudaMalloc(&h->stats[l], sizeof(float2) * (size_t)W * H));
         for (int j = 0; j < d->n_cams; ++j) {
             const ps_camera& cj = h->lcam[l][j];
             PS_TRY(cudaMalloc(&h->quad[l][j], sizeof(float4) * (size_t)cj.width * cj.height));
@@ -743,8 +820,15 @@ extern "C" int psweep_create(const ps_sweep_desc* d, psweep_t** out) {
     for (int j = 0; j < d->n_cams; ++j)
         PS_TRY(cudaMalloc(&h->stage_img[1 + j], (size_t)d->cams[j].width * d->cams[j].height));
     PS_TRY(cudaMalloc(&h->stage_depth, sizeof(float) * (size_t)d->ref.width * d->ref.height));
-    PS_TRY(cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Tile<4>::smem_bytes));
+    PS_TRY(cudaMalloc(&h->tile_counter, sizeof(int)));
+    PS_TRY(cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<4>::smem));
+    {
+        int dev = 0, sms = 0, per_sm = 0;
+        PS_TRY(cudaGetDevice(&dev));
+        PS_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        PS_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel, NT, Geo<4>::smem));
+        h->grid = sms * std::max(1, per_sm);
+    }
     PS_TRY(cudaDeviceSynchronize());
 #undef PS_TRY
     *out = h;
@@ -767,10 +851,18 @@ extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_
     SweepParams P;
     std::memset(&P, 0, sizeof(P));
     P.n_levels = h->n_levels;
-    int tiles = 0;
     h->prof.mark(0, s);
-    // larger windows first so the heavier tiles start early
-    for (int l = 0; l < h->n_levels; ++l) {
+    // heavier level first in the tile order (planes x halo samples per tile)
+    int order[PS_MAX_LEVELS] = {0, 1};
+    if (h->n_levels == 2) {
+        auto cost = [&](int l) {
+            int r = h->levels[l].window / 2;
+            return (double)h->n_planes[l] * (TW + 2 * r) * (TH + 2 * r);
+        };
+        if (cost(1) > cost(0)) std::swap(order[0], order[1]);
+    }
+    for (int oi = 0; oi < h->n_levels; ++oi) {
+        const int l = order[oi];
         const ps_level& L = h->levels[l];
         const int W = h->lW[l], H = h->lH[l];
         if (L.kind == PS_LEVEL_DOWNSAMPLE) {
@@ -791,7 +883,8 @@ extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_
                     images[1 + j], h->cams[j].width, 1, cj.width, cj.height, h->quad[l][j]);
             }
         }
-        LevelD& D = P.lv[l];
+        ref_stats_kernel<<<dim3((W + 127) / 128, H), 128, 0, s>>>(h->ref_img[l], W, H, L.window / 2, h->stats[l]);
+        LevelD& D = P.lv[oi];
         D.W = W;
         D.H = H;
         D.rho = L.window / 2;
@@ -801,6 +894,7 @@ extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_
         D.planes = h->planes[l];
         D.rays = h->rays[l];
         D.ref = h->ref_img[l];
+        D.stats = h->stats[l];
         D.n_cams = h->n_cams;
         for (int j = 0; j < h->n_cams; ++j) {
             for (int i = 0; i < 9; ++i) D.cams[j].R[i] = (float)h->poses[j].R[i];
@@ -810,8 +904,7 @@ extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_
         }
         D.tiles_x = (W + TW - 1) / TW;
         D.tiles_y = (H + TH - 1) / TH;
-        D.tile_begin = tiles;
-        tiles += D.tiles_x * D.tiles_y;
+        D.n_tiles = D.tiles_x * D.tiles_y;
         const ps_level_out* lo = level_out ? &level_out[l] : nullptr;
         D.depth = lo && lo->depth ? lo->depth : h->out_depth[l];
         D.c1 = lo && lo->best_cost ? lo->best_cost : h->out_c1[l];
@@ -820,13 +913,16 @@ extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_
     }
     PS_CUDA(cudaGetLastError());
     size_t smem = 0;
+    int tiles = 0;
     for (int l = 0; l < h->n_levels; ++l) {
         int r = P.lv[l].rho;
-        size_t b = r == 2 ? Tile<2>::smem_bytes : r == 3 ? Tile<3>::smem_bytes : Tile<4>::smem_bytes;
+        size_t b = r == 2 ? Geo<2>::smem : r == 3 ? Geo<3>::smem : Geo<4>::smem;
         smem = std::max(smem, b);
+        tiles += P.lv[l].n_tiles;
     }
+    PS_CUDA(cudaMemsetAsync(h->tile_counter, 0, sizeof(int), s));
     h->prof.mark(1, s);
-    sweep_kernel<<<tiles, NT, smem, s>>>(P);
+    sweep_kernel<<<std::min(tiles, h->grid), NT, smem, s>>>(P, h->tile_counter);
     PS_CUDA(cudaGetLastError());
     h->prof.mark(2, s);
 
@@ -836,15 +932,16 @@ extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_
     M.H = h->ref.height;
     M.s = 1;
     M.Wl = M.Hl = 1;
-    for (int l = 0; l < h->n_levels; ++l) {
+    for (int oi = 0; oi < h->n_levels; ++oi) {
+        const int l = order[oi];
         const ps_level& L = h->levels[l];
         if (L.kind == PS_LEVEL_DOWNSAMPLE) {
-            M.low = P.lv[l].depth;
+            M.low = P.lv[oi].depth;
             M.s = L.factor;
             M.Wl = h->lW[l];
             M.Hl = h->lH[l];
         } else {
-            M.crop = P.lv[l].depth;
+            M.crop = P.lv[oi].depth;
             M.cx0 = h->cx0[l];
             M.cy0 = h->cy0[l];
             M.cw = L.crop_w;

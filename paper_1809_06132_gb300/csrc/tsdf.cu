@@ -94,7 +94,11 @@ __device__ int hash_insert(const TsdfDev& T, int bx, int by, int bz) {
     long long h = (long long)(hash64(key) & (unsigned long long)T.slot_mask);
     for (int probe = 0; probe < MAX_PROBE; ++probe) {
         unsigned long long k = *((volatile unsigned long long*)&T.hkeys[h]);
-        if (k == key) return 0;
+        if (k == key) {
+            // a block that found no room in the pool stays unstored; say so on every frame that needs it
+            if (*((volatile int*)&T.hvals[h]) == -2) atomicOr(T.status, DEV_CAPACITY);
+            return 0;
+        }
         if (k == EMPTY) {
             unsigned long long prev = atomicCAS(&T.hkeys[h], EMPTY, key);
             if (prev == EMPTY) {
@@ -108,7 +112,10 @@ __device__ int hash_insert(const TsdfDev& T, int bx, int by, int bz) {
                 T.hvals[h] = idx;
                 return 0;
             }
-            if (prev == key) return 0;
+            if (prev == key) {
+                if (*((volatile int*)&T.hvals[h]) == -2) atomicOr(T.status, DEV_CAPACITY);
+                return 0;
+            }
         }
         h = (h + 1) & T.slot_mask;
     }

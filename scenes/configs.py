@@ -85,7 +85,7 @@ class TsdfParams:
     local_half: Optional[Tuple[float, float, float]] = None  # None = no local-map gate
     local_offset: Tuple[float, float, float] = (0.0, 0.0, 0.0)  # local-map centre - camera centre
     hash_slots: int = 1 << 20
-    pool_blocks: int = 1 << 17
+    pool_blocks: int = 1 << 16
 
 
 @dataclass

@@ -117,7 +117,8 @@ def test_full_size_structure(street_full):
         assert ((gl["depth"] > 0) == v).all()
         assert (gl["kstar"] < lv.n_planes).all()
         assert (gl["c1"][v] <= gl["c2"][v]).all()
-        assert (gl["c1"][v] >= -1e-6).all() and (gl["c1"][v] <= 1 + 1e-6).all()
+        # float32 ZNCC of a near-perfect match can exceed 1 by rounding (cost slightly below 0)
+        assert (gl["c1"][v] >= -1e-4).all() and (gl["c1"][v] <= 1 + 1e-4).all()
 
 
 def test_deterministic_and_optional_outputs(street_small):
