@@ -237,6 +237,38 @@ int psweep_profile_read(psweep_t* h, double* stage_ms, int32_t* n_calls);
 int tsdf_profile(tsdf_t* t, int32_t capacity);
 int tsdf_profile_read(tsdf_t* t, double* stage_ms, int32_t* n_calls);
 
+/* Allocation-free fusion into a caller-owned dense grid (the paper has no
+ * counterpart; this is a convenience of the library).  Some callers cannot
+ * allocate GPU memory while they run: code recording a CUDA graph (an
+ * allocation breaks the capture), real-time loops whose memory is planned
+ * once up front, and hosts whose device memory belongs to another
+ * allocator.  This call fuses one depth map exactly like tsdf_integrate on
+ * a dense grid, but the voxels are the caller's and the library's working
+ * memory (block list, counters, depth maximum) is one fixed static device
+ * array of PS_STATIC_SCRATCH_BYTES (about 1.3 MB), which every GPU that
+ * loads the library keeps until the process exits.  No memory is allocated.
+ *   voxels        device float32: n_blocks x 512 {D, w} pairs; block
+ *                 b = bx + nbx (by + nby bz) of the grid, voxel x + 8 y + 64 z
+ *                 inside a block (the order tsdf_extract reports for a dense
+ *                 map).  Zero it to start an empty map.
+ *   dims          host int32[3]: voxels per axis, multiples of 8, at most
+ *                 PS_STATIC_MAX_BLOCKS blocks in all (larger grids get
+ *                 PS_ERR_ARG and a message naming the limit).
+ *   origin        host double[3]; voxel_size, mu, w_max as in ps_tsdf_desc.
+ *   depth         device float32 H x W range map of cam (0 = no depth).
+ *   cam           host, the depth map's camera; world_to_cam host pose.
+ * Asynchronous on `stream`.  The first call on each device looks up the
+ * static array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call
+ * reuses the same array (it keeps the last call's contents; the call clears
+ * what must start at zero), so calls that overlap on the GPU, from other
+ * streams or host threads, race on it: serialise them. */
+#define PS_STATIC_MAX_BLOCKS 65536
+#define PS_STATIC_SCRATCH_BYTES (256 + PS_STATIC_MAX_BLOCKS * 20)
+int tsdf_integrate_dense_static(float* voxels, const int32_t* dims, const double* origin, double voxel_size,
+                                double mu, double w_max, const float* depth, const ps_camera* cam,
+                                const ps_pose* world_to_cam, void* stream);
+
 /* Message for the calling thread's last non-zero status ("" if none). */
 const char* ps_last_error(void);
 

@@ -563,3 +563,121 @@ extern "C" int tsdf_status(tsdf_t* t, void* stream) {
     PS_ARG(t != nullptr, "tsdf_status: NULL handle");
     return read_status(t, (cudaStream_t)stream);
 }
+
+// ===================================================================== allocation-free dense fusion
+//
+// For callers that cannot allocate device memory while they run (graph
+// capture, pre-planned real-time memory, foreign allocators): the working
+// memory lives in this fixed static device array instead of a handle.
+// Layout: [0] status, [4] block count, [8] listed-block count, [12] depth
+// maximum bits, [256 ..) block keys (int4 x PS_STATIC_MAX_BLOCKS), then the
+// visible-block list (int x PS_STATIC_MAX_BLOCKS).
+
+#include <mutex>
+
+namespace ps {
+namespace {
+
+static __device__ __align__(256) unsigned char g_static_scratch[PS_STATIC_SCRATCH_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_static_mu;
+unsigned char* g_static_ptr[MAX_DEVICES] = {};
+
+// Device address of the static array on the current device (looked up once per device).
+int static_scratch(unsigned char** out) {
+    int dev = 0;
+    PS_CUDA(cudaGetDevice(&dev));
+    PS_ARG(dev >= 0 && dev < MAX_DEVICES, "tsdf_integrate_dense_static: device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+        g_static_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_static_ptr[dev];
+    return PS_OK;
+}
+
+__global__ void static_dense_keys_kernel(int4* keys, int* n_alloc, int nx, int ny, int nz) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int n = nx * ny * nz;
+    if (i == 0) *n_alloc = n;
+    if (i < n) keys[i] = make_int4(i % nx, (i / nx) % ny, i / (nx * ny), 0);
+}
+
+}  // namespace
+}  // namespace ps
+
+extern "C" int tsdf_integrate_dense_static(float* voxels, const int32_t* dims, const double* origin,
+                                           double voxel_size, double mu, double w_max, const float* depth,
+                                           const ps_camera* cam, const ps_pose* w2c, void* stream) {
+    clear_error();
+    PS_ARG(voxels && dims && origin && depth && cam && w2c, "tsdf_integrate_dense_static: NULL argument");
+    PS_ARG(voxel_size > 0 && mu > 0 && w_max >= 1, "tsdf_integrate_dense_static: need voxel_size > 0, mu > 0, w_max >= 1");
+    PS_ARG(cam->width > 0 && cam->height > 0 && cam->fx > 0 && cam->fy > 0 && cam->xi >= 0,
+           "tsdf_integrate_dense_static: bad camera");
+    for (int i = 0; i < 3; ++i)
+        PS_ARG(dims[i] > 0 && dims[i] % 8 == 0, "tsdf_integrate_dense_static: dims must be positive multiples of 8");
+    const long long nx = dims[0] / 8, ny = dims[1] / 8, nz = dims[2] / 8;
+    const long long n_blocks = nx * ny * nz;
+    PS_ARG(n_blocks <= PS_STATIC_MAX_BLOCKS,
+           "tsdf_integrate_dense_static: %lld blocks exceed the static limit of %d blocks (%d voxels)", n_blocks,
+           PS_STATIC_MAX_BLOCKS, PS_STATIC_MAX_BLOCKS * B3);
+    for (int i = 0; i < 12; ++i)
+        PS_ARG(std::isfinite(i < 9 ? w2c->R[i] : w2c->t[i - 9]), "tsdf_integrate_dense_static: pose not finite");
+    unsigned char* base = nullptr;
+    int st = static_scratch(&base);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    TsdfDev T{};
+    T.status = reinterpret_cast<unsigned*>(base);
+    T.n_alloc = reinterpret_cast<int*>(base + 4);
+    T.n_vis = reinterpret_cast<int*>(base + 8);
+    T.dmax_bits = reinterpret_cast<unsigned*>(base + 12);
+    T.pool_keys = reinterpret_cast<int4*>(base + 256);
+    T.vis = reinterpret_cast<int*>(base + 256 + sizeof(int4) * PS_STATIC_MAX_BLOCKS);
+    T.vox = reinterpret_cast<float2*>(voxels);
+    T.pool_cap = (int)n_blocks;
+
+    FrameP F;
+    std::memset(&F, 0, sizeof(F));
+    F.cam = to_camf(*cam);
+    for (int i = 0; i < 3; ++i) {
+        double Cw = -(w2c->R[i] * w2c->t[0] + w2c->R[3 + i] * w2c->t[1] + w2c->R[6 + i] * w2c->t[2]);
+        for (int k = 0; k < 3; ++k) {
+            F.R[3 * i + k] = (float)w2c->R[3 * i + k];
+            F.Rt[3 * i + k] = (float)w2c->R[3 * k + i];
+        }
+        double rel = Cw - origin[i];
+        F.C[i] = (float)rel;
+        double cv = rel / voxel_size;
+        double ic = std::floor(cv + 0.5);
+        PS_ARG(std::fabs(ic) < 1e8, "tsdf_integrate_dense_static: camera too far from the grid origin");
+        F.ic[i] = (int)ic;
+        F.fb[i] = (float)(0.5 - (cv - ic));
+    }
+    F.vox = (float)voxel_size;
+    F.vox_lo = (float)(voxel_size - (double)F.vox);
+    F.mu = (float)mu;
+    F.inv_mu = (float)(1.0 / mu);
+    F.w_max = (float)w_max;
+    F.block = (float)(8.0 * voxel_size);
+    F.view_angle = 4.0f;  // no view-cone culling: the range test alone keeps the list a superset
+    int dev = 0, sms = 0;
+    PS_CUDA(cudaGetDevice(&dev));
+    PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int W = cam->width, H = cam->height;
+    PS_CUDA(cudaMemsetAsync(base, 0, 256, s));  // status, counters, depth maximum start at zero
+    static_dense_keys_kernel<<<(int)((n_blocks + 255) / 256), 256, 0, s>>>(T.pool_keys, T.n_alloc, (int)nx, (int)ny,
+                                                                           (int)nz);
+    PS_CUDA(cudaGetLastError());
+    depth_max_kernel<<<sms * 2, 256, 0, s>>>(depth, W * H, T.dmax_bits);
+    PS_CUDA(cudaGetLastError());
+    visible_kernel<<<sms * 4, 256, 0, s>>>(F, T);
+    PS_CUDA(cudaGetLastError());
+    integrate_kernel<<<sms * 8, IT, 0, s>>>(F, T, depth);
+    PS_CUDA(cudaGetLastError());
+    return PS_OK;
+}

@@ -25,7 +25,8 @@ MAX_SETS, MAX_CAMS, MAX_LEVELS = 4, 4, 2
 # every symbol include/psweep.h declares
 EXPORTS = ["psweep_create", "psweep_depth", "psweep_destroy", "tsdf_create", "tsdf_integrate", "tsdf_count",
            "tsdf_extract", "tsdf_status", "tsdf_destroy", "psweep_frame_host", "psweep_profile",
-           "psweep_profile_read", "tsdf_profile", "tsdf_profile_read", "ps_last_error", "ps_version"]
+           "psweep_profile_read", "tsdf_profile", "tsdf_profile_read", "tsdf_integrate_dense_static",
+           "ps_last_error", "ps_version"]
 
 
 class PsError(RuntimeError):
@@ -108,6 +109,8 @@ def load(build_if_missing: bool = True):
     L.psweep_profile_read.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int32)]
     L.tsdf_profile.argtypes = [P, C.c_int32]
     L.tsdf_profile_read.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int32)]
+    L.tsdf_integrate_dense_static.argtypes = [P, P, P, C.c_double, C.c_double, C.c_double, P,
+                                              C.POINTER(ps_camera), C.POINTER(ps_pose), P]
     L.ps_last_error.restype = C.c_char_p
     L.ps_version.restype = C.c_char_p
     _lib = L
@@ -323,6 +326,24 @@ class Tsdf:
         _check(load().tsdf_extract(self.h, float(min_weight), keys.data_ptr(), D.data_ptr(), W.data_ptr(), n,
                                    C.byref(m), _stream_ptr(stream)))
         return keys[:m.value], D[:m.value], W[:m.value]
+
+
+STATIC_MAX_BLOCKS = 65536
+
+
+def tsdf_integrate_dense_static(voxels: torch.Tensor, dims, origin, voxel_size: float, mu: float, w_max: float,
+                                depth: torch.Tensor, cam, world_to_cam, stream=None):
+    """Fuse one depth map into a caller-owned dense grid without any
+    allocation by the library (for callers that cannot allocate while they
+    run; the working memory is a fixed static device array).  voxels:
+    contiguous CUDA float32 tensor of n_blocks x 512 x 2 ({D, w} pairs)."""
+    d = (C.c_int32 * 3)(*[int(v) for v in dims])
+    o = (C.c_double * 3)(*[float(v) for v in origin])
+    cz = camera(cam)
+    pz = pose(world_to_cam)
+    _check(load().tsdf_integrate_dense_static(_dev(voxels, torch.float32, "voxels"), d, o, float(voxel_size),
+                                              float(mu), float(w_max), _dev(depth, torch.float32, "depth"),
+                                              C.byref(cz), C.byref(pz), _stream_ptr(stream)))
 
 
 def version() -> str:
