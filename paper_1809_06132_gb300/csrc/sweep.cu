@@ -32,11 +32,13 @@ namespace {
 
 constexpr int TW = 64;   // output tile width (pixels)
 constexpr int TH = 24;   // output tile height
-constexpr int NT = 256;  // threads per CTA
-constexpr int RUN = 8;   // outputs per horizontal run (phase H)
-constexpr int SEG = 6;   // output rows per vertical segment (phase V)
+constexpr int NT = 512;  // threads per CTA (one CTA per SM)
+constexpr int RUN = 4;   // outputs per horizontal run (phase H)
+constexpr int SEG = 3;   // output rows per vertical segment (phase V)
+constexpr int KP = 2;    // planes swept per camera before moving to the next camera
+constexpr int PLANE_CHUNK = 32;  // most planes one work item sweeps
 static_assert(NT == TW * (TH / SEG), "phase V: one thread per column and row segment");
-static_assert(NT / 32 == TW / RUN, "phase H: one warp per run, one lane per halo row");
+static_assert(NT / 32 >= TW / RUN, "phase H: one warp per run, one lane per halo row");
 
 struct PlaneD {
     float nx, ny, nz, d;  // plane n . X = d (reference frame)
@@ -65,6 +67,9 @@ struct LevelD {
     int n_cams;
     CamJ cams[PS_MAX_CAMS];
     int tiles_x, tiles_y, n_tiles;
+    int chunk, n_chunks, n_items;  // planes per work item, items per tile, tiles x items
+    float* partial;                // [n_items][7][TH * TW] chunk results (when n_chunks > 1)
+    int* done;                     // [n_tiles] finished chunks per tile (zeroed per launch)
     float* depth;
     float* c1;
     float* c2;
@@ -187,6 +192,9 @@ __global__ void ref_level_kernel(const uint8_t* img, int W, int s, int x0, int y
     out[(size_t)y * Wl + x] = v;
 }
 
+// Matching image of a level in "quad" layout: entry (x, y) holds the
+// centred intensities at (x, y), (x+1, y), (x, y+1), (x+1, y+1), so one
+// bilinear sample is one 16-byte gather.
 __global__ void quad_level_kernel(const uint8_t* img, int W, int s, int Wl, int Hl, float4* out) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y;
@@ -236,9 +244,11 @@ struct CamS {
 };
 
 // Bilinear sample of a matching camera at the projection of X_j (camera
-// frame); NaN when the point does not project (sphere side, distortion
-// range) or lands outside [0, W-1] x [0, H-1].  The gather is clamped into
-// the image and always issued, so the warp does not diverge.
+// frame), as a centred intensity; NaN when the point does not project
+// (sphere side, distortion range) or lands outside [0, W-1] x [0, H-1].
+// The gather is clamped into the image and always issued, so the warp does
+// not diverge; a clamp that moved the point marks it outside (NaN compares
+// unequal, so a NaN position is rejected too).
 __device__ __forceinline__ float warp_sample(const CamS& c, float X, float Y, float Z) {
     float n2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
     float n = n2 * rsqrtf(n2);
@@ -251,11 +261,11 @@ __device__ __forceinline__ float warp_sample(const CamS& c, float X, float Y, fl
     float yd = fmaf(my, rad, fmaf(c.p1, fmaf(2.0f * my, my, r2), 2.0f * c.p2 * mxy));
     float u = fmaf(c.fx, xd, c.cx);
     float v = fmaf(c.fy, yd, c.cy);
-    bool ok = (Z > c.lim * n) && (r2 <= c.r2_max) && (u >= 0.0f) && (u <= c.wm1) && (v >= 0.0f) && (v <= c.hm1);
     float uc = fminf(fmaxf(u, 0.0f), c.wm1), vc = fminf(fmaxf(v, 0.0f), c.hm1);
+    bool ok = (Z > c.lim * n) && (r2 <= c.r2_max) && (uc == u) && (vc == v);
     int x0 = (int)uc, y0 = (int)vc;
     float ax = uc - (float)x0, ay = vc - (float)y0;
-    float4 q = __ldg(&c.quad[y0 * c.width + x0]);
+    float4 q = __ldg(c.quad + y0 * c.width + x0);
     float top = fmaf(ax, q.y - q.x, q.x);
     float bot = fmaf(ax, q.w - q.z, q.z);
     float w = fmaf(ay, bot - top, top);
@@ -264,12 +274,14 @@ __device__ __forceinline__ float warp_sample(const CamS& c, float X, float Y, fl
 
 // Tile geometry.  A CTA owns TW x TH output pixels of one level plus a halo of
 // RHO on every side (HH rows x HWL columns of warped samples per plane and
-// camera).  Phase A: every thread warps PPT halo positions into W.  Phase
-// H: thread (row, run) slides a 2 RHO + 1 window along 8 outputs of one halo
-// row and stores (sum w, sum w^2, sum r w, invalid count) in H.  Phase V:
-// thread (column, segment) slides down SEG output rows, forms ZNCC and keeps
-// the minimum over cameras.  Strides are chosen so that each phase's
-// shared-memory accesses are free of bank conflicts.
+// camera).  Per plane set, every halo position keeps, per matching camera,
+// a = R_j r / (n . r), so that the plane at offset d maps it to d a + t_j.
+// Phase A: every thread warps PPT halo positions into W.  Phase H: thread
+// (row, run) slides a 2 RHO + 1 window along RUN outputs of one halo row and
+// stores (sum w, sum w^2, sum r w, invalid count) in H.  Phase V: thread
+// (column, segment) slides down SEG output rows, forms ZNCC and keeps the
+// minimum over cameras.  Strides make every phase's shared-memory accesses
+// free of bank conflicts.
 template <int RHO>
 struct Geo {
     static constexpr int HH = TH + 2 * RHO;           // halo rows (<= 32)
@@ -281,21 +293,53 @@ struct Geo {
     static constexpr int NRUNPOS = RUN + 2 * RHO;     // positions one horizontal run reads
     static constexpr int NV = (NRUNPOS + 3) / 4;      // float4 loads per run
     static constexpr int N = (2 * RHO + 1) * (2 * RHO + 1);
-    static constexpr size_t smem =
-        sizeof(float4) * (size_t)(NPOS + HH * HS) + sizeof(float) * 2 * HH * WS + sizeof(float2) * TH * TW;
+    // n_cams direction tables, H, two W (one per plane of a pair) and R
+    static constexpr size_t smem(int n_cams) {
+        return sizeof(float4) * ((size_t)n_cams * NPOS + HH * HS) + sizeof(float) * 3 * HH * WS;
+    }
     static_assert(HH <= 32, "phase H maps one warp lane per halo row");
     static_assert(HWL <= WS && 4 * NV + TW - RUN <= WS, "row stride covers the runs' loads");
 };
 
+// Parabola through the winner and its neighbours in the same plane set, and
+// the range along the pixel's ray; writes the level outputs of one pixel.
+__device__ void finish_pixel(const LevelD& L, int gx, int gy, float c1, float c2, int kb, float cminus, float cplus) {
+    const float inf = __int_as_float(0x7f800000);
+    size_t o = (size_t)gy * L.W + gx;
+    float depth = 0.f;
+    if (kb >= 0) {
+        int s = 0;
+        while (s + 1 < L.n_sets && L.sets[s + 1].start <= kb) ++s;
+        const SetD S = L.sets[s];
+        int li = kb - S.start;
+        float delta = 0.f;
+        if (li > 0 && li < S.count - 1 && cminus < inf && cplus < inf) {
+            float den = cminus - 2.0f * c1 + cplus;
+            if (den > 0.f) delta = fminf(0.5f, fmaxf(-0.5f, (cminus - cplus) / (2.0f * den)));
+        }
+        float t = S.count > 1 ? ((float)li + delta) / (float)(S.count - 1) : 0.f;
+        float param = S.family == PS_PLANES_FRONTO ? 1.0f / fmaf(t, 1.0f / S.a - 1.0f / S.b, 1.0f / S.b)
+                                                   : fmaf(t, S.b - S.a, S.a);
+        float4 r = L.rays[o];
+        float nr = S.nx * r.x + S.ny * r.y + S.nz * r.z;
+        depth = param / nr;
+    }
+    if (L.depth) L.depth[o] = depth;
+    if (L.c1) L.c1[o] = c1;
+    if (L.c2) L.c2[o] = c2;
+    if (L.kstar) L.kstar[o] = kb;
+}
+
 template <int RHO>
-__device__ void sweep_tile(const LevelD& L, const CamS* cams, int tile, unsigned char* smem_raw) {
+__device__ void sweep_tile(const LevelD& L, const CamS* cams, int item, unsigned char* smem_raw, int* s_flag) {
     using G = Geo<RHO>;
+    const int tile = item / L.n_chunks, chunk = item - tile * L.n_chunks;
+    const int k_lo = chunk * L.chunk, k_hi = min(L.n_planes, k_lo + L.chunk);
     constexpr int HH = G::HH, HWL = G::HWL, WS = G::WS, HS = G::HS, NPOS = G::NPOS, N = G::N;
-    float4* Ray = reinterpret_cast<float4*>(smem_raw);  // [NPOS] (rx, ry, rz, 1 / n.r)
-    float4* Hs = Ray + NPOS;                             // [HH][HS]
-    float* Ws = reinterpret_cast<float*>(Hs + HH * HS);  // [HH][WS] warped samples (NaN = invalid)
-    float* Rs = Ws + HH * WS;                            // [HH][WS] reference intensities
-    float2* St = reinterpret_cast<float2*>(Rs + HH * WS); // [TH][TW] (mean, 1/sqrt(var)) of the reference window, NaN = none
+    float4* Hs = reinterpret_cast<float4*>(smem_raw);            // [HH][HS] window sums
+    float4* A = Hs + HH * HS;                                     // [n_cams][NPOS] (R_j r / n.r); NaN = none
+    float* Ws = reinterpret_cast<float*>(A + L.n_cams * NPOS);    // [2][HH][WS] warped samples of the pair (NaN = invalid)
+    float* Rs = Ws + 2 * HH * WS;                                 // [HH][WS] reference intensities
     const int tid = threadIdx.x;
     const int tx = tile % L.tiles_x, ty = tile / L.tiles_x;
     const int gx0 = tx * TW - RHO, gy0 = ty * TH - RHO;
@@ -307,180 +351,259 @@ __device__ void sweep_tile(const LevelD& L, const CamS* cams, int tile, unsigned
         int gx = gx0 + hx, gy = gy0 + hy;
         bool in = gx >= 0 && gy >= 0 && gx < L.W && gy < L.H;
         Rs[hy * WS + hx] = in ? L.ref[(size_t)gy * L.W + gx] : 0.0f;
-        Ray[p] = in ? L.rays[(size_t)gy * L.W + gx] : make_float4(nan, nan, nan, 0.f);
     }
-
-    for (int p = tid; p < TH * TW; p += NT) {
-        int y = p / TW, x = p - y * TW;
-        int gx = tx * TW + x, gy = ty * TH + y;
-        float2 st = make_float2(0.f, -1.f);
-        if (gx < L.W && gy < L.H) st = L.stats[(size_t)gy * L.W + gx];
-        St[p] = st.y >= (float)N * 1e-8f ? make_float2(st.x, rsqrtf(st.y)) : make_float2(nan, nan);
-    }
-    // outputs of this thread: column ox, rows oy0 .. oy0 + SEG - 1
+    // outputs of this thread: column ox, rows oy0 .. oy0 + SEG - 1; their
+    // reference window mean and 1/sqrt(sum of squared deviations), NaN = unusable
     const int ox = tid % TW, oy0 = (tid / TW) * SEG;
-    float c1[SEG], c2[SEG], cprev[SEG], cminus[SEG], cplus[SEG];
+    float2 st[SEG];
+#pragma unroll
+    for (int i = 0; i < SEG; ++i) {
+        int gx = tx * TW + ox, gy = ty * TH + oy0 + i;
+        float2 v = make_float2(0.f, -1.f);
+        if (gx < L.W && gy < L.H) v = L.stats[(size_t)gy * L.W + gx];
+        st[i] = v.y >= (float)N * 1e-8f ? make_float2(v.x, rsqrtf(v.y)) : make_float2(nan, nan);
+    }
+    float c1[SEG], c2[SEG], cprev[SEG], cminus[SEG], cplus[SEG], cfirst[SEG];
     int kb[SEG];
     bool needp[SEG];
 #pragma unroll
     for (int i = 0; i < SEG; ++i) {
-        c1[i] = c2[i] = cprev[i] = cminus[i] = cplus[i] = inf;
+        c1[i] = c2[i] = cprev[i] = cminus[i] = cplus[i] = cfirst[i] = inf;
         kb[i] = -1;
         needp[i] = false;
     }
     const int hrow = tid & 31, hrun = tid >> 5;  // phase H item
     const int base_v = oy0 * HS + ox;            // phase V first H entry
-    __syncthreads();
 
     for (int s = 0; s < L.n_sets; ++s) {
+        const int s_lo = max(L.sets[s].start, k_lo), k_end = min(L.sets[s].start + L.sets[s].count, k_hi);
+        if (s_lo >= k_end) continue;  // the set lies outside this work item's planes
         const float snx = L.sets[s].nx, sny = L.sets[s].ny, snz = L.sets[s].nz;
+        __syncthreads();  // previous users of A are done
         for (int p = tid; p < NPOS; p += NT) {
-            float4 r = Ray[p];
+            int hy = p / HWL, hx = p - hy * HWL;
+            int gx = gx0 + hx, gy = gy0 + hy;
+            float4 r = make_float4(nan, nan, nan, 0.f);
+            if (gx >= 0 && gy >= 0 && gx < L.W && gy < L.H) r = L.rays[(size_t)gy * L.W + gx];
             float nr = snx * r.x + sny * r.y + snz * r.z;
-            Ray[p].w = nr > 0.0f ? 1.0f / nr : nan;
-        }
-        __syncthreads();
-        const int k_end = L.sets[s].start + L.sets[s].count;
-        for (int k = L.sets[s].start; k < k_end; ++k) {
-            const float d = __ldg(&L.planes[k].d);
-            float cmin[SEG];
-#pragma unroll
-            for (int i = 0; i < SEG; ++i) cmin[i] = inf;
+            float inv = nr > 0.0f ? 1.0f / nr : nan;
             for (int j = 0; j < L.n_cams; ++j) {
                 const CamS& C = cams[j];
-                // phase A: warped samples of the tile + halo
+                A[j * NPOS + p] = make_float4(inv * fmaf(C.R[0], r.x, fmaf(C.R[1], r.y, C.R[2] * r.z)),
+                                              inv * fmaf(C.R[3], r.x, fmaf(C.R[4], r.y, C.R[5] * r.z)),
+                                              inv * fmaf(C.R[6], r.x, fmaf(C.R[7], r.y, C.R[8] * r.z)), 0.f);
+            }
+        }
+        __syncthreads();
+        // planes go in pairs: both planes of a pair are swept with one camera
+        // before the next camera, so consecutive gathers hit overlapping
+        // footprints of the same image
+        for (int k0 = s_lo; k0 < k_end; k0 += KP) {
+            const int np = min(KP, k_end - k0);
+            float cmin[KP][SEG];
+#pragma unroll
+            for (int q = 0; q < KP; ++q)
+#pragma unroll
+                for (int i = 0; i < SEG; ++i) cmin[q][i] = inf;
+            for (int j = 0; j < L.n_cams; ++j) {
+                const CamS& C = cams[j];
+                const float4* Aj = A + j * NPOS;
+                // phase A: warped samples of the tile + halo for both planes of the pair
+                const float d0 = __ldg(&L.planes[k0].d);
+                const float d1 = __ldg(&L.planes[k0 + np - 1].d);
+                int bad = 0;
 #pragma unroll 3
                 for (int i = 0; i < G::PPT; ++i) {
                     int p = tid + i * NT;
                     if (p < NPOS) {
-                        float4 r = Ray[p];
-                        float lam = d * r.w;
-                        float X = lam * r.x, Y = lam * r.y, Z = lam * r.z;
-                        float Xj = fmaf(C.R[0], X, fmaf(C.R[1], Y, fmaf(C.R[2], Z, C.t[0])));
-                        float Yj = fmaf(C.R[3], X, fmaf(C.R[4], Y, fmaf(C.R[5], Z, C.t[1])));
-                        float Zj = fmaf(C.R[6], X, fmaf(C.R[7], Y, fmaf(C.R[8], Z, C.t[2])));
+                        float4 a = Aj[p];
+                        float w0 = warp_sample(C, fmaf(d0, a.x, C.t[0]), fmaf(d0, a.y, C.t[1]), fmaf(d0, a.z, C.t[2]));
+                        float w1 = warp_sample(C, fmaf(d1, a.x, C.t[0]), fmaf(d1, a.y, C.t[1]), fmaf(d1, a.z, C.t[2]));
+                        bad |= isnan(w0) | isnan(w1);
                         int hy = p / HWL, hx = p - hy * HWL;
-                        Ws[hy * WS + hx] = warp_sample(C, Xj, Yj, Zj);
+                        Ws[hy * WS + hx] = w0;
+                        Ws[HH * WS + hy * WS + hx] = w1;
                     }
                 }
-                __syncthreads();
-                // phase H: sliding horizontal sums along an 8-pixel run of one halo row
-                if (hrow < HH) {
-                    const float* wr = Ws + hrow * WS + RUN * hrun;
-                    const float* rr = Rs + hrow * WS + RUN * hrun;
-                    float w[4 * G::NV], r[4 * G::NV];
+                bad = __syncthreads_or(bad);
 #pragma unroll
-                    for (int q = 0; q < G::NV; ++q) {
-                        float4 a = *reinterpret_cast<const float4*>(wr + 4 * q);
-                        float4 b = *reinterpret_cast<const float4*>(rr + 4 * q);
-                        w[4 * q] = a.x; w[4 * q + 1] = a.y; w[4 * q + 2] = a.z; w[4 * q + 3] = a.w;
-                        r[4 * q] = b.x; r[4 * q + 1] = b.y; r[4 * q + 2] = b.z; r[4 * q + 3] = b.w;
+                for (int q = 0; q < KP; ++q) {
+                    if (q >= np) break;
+                    if (q > 0) __syncthreads();  // the previous plane's vertical pass is done with H
+                    // phase H: sliding horizontal sums along a run of one halo row
+                    if (hrow < HH && hrun < TW / RUN) {
+                        const float* wr = Ws + q * HH * WS + hrow * WS + RUN * hrun;
+                        const float* rr = Rs + hrow * WS + RUN * hrun;
+                        float w[4 * G::NV], r[4 * G::NV];
+#pragma unroll
+                        for (int qq = 0; qq < G::NV; ++qq) {
+                            float4 a = *reinterpret_cast<const float4*>(wr + 4 * qq);
+                            float4 b = *reinterpret_cast<const float4*>(rr + 4 * qq);
+                            w[4 * qq] = a.x; w[4 * qq + 1] = a.y; w[4 * qq + 2] = a.z; w[4 * qq + 3] = a.w;
+                            r[4 * qq] = b.x; r[4 * qq + 1] = b.y; r[4 * qq + 2] = b.z; r[4 * qq + 3] = b.w;
+                        }
+                        float4* hrow_out = Hs + hrow * HS + RUN * hrun;
+                        float sw = 0.f, sww = 0.f, srw = 0.f, sm = 0.f;
+                        if (!bad) {  // every sample of the tile is valid (the common case)
+#pragma unroll
+                            for (int t = 0; t <= 2 * RHO; ++t) {
+                                sw += w[t];
+                                sww = fmaf(w[t], w[t], sww);
+                                srw = fmaf(r[t], w[t], srw);
+                            }
+                            hrow_out[0] = make_float4(sw, sww, srw, 0.f);
+#pragma unroll
+                            for (int o = 1; o < RUN; ++o) {
+                                const int a = o + 2 * RHO, b = o - 1;
+                                sw += w[a] - w[b];
+                                sww += fmaf(w[a], w[a], -w[b] * w[b]);
+                                srw += fmaf(r[a], w[a], -r[b] * w[b]);
+                                hrow_out[o] = make_float4(sw, sww, srw, 0.f);
+                            }
+                        } else {  // invalid samples: excluded from the sums and counted
+#pragma unroll
+                            for (int t = 0; t <= 2 * RHO; ++t) {
+                                bool bt = isnan(w[t]);
+                                float wt = bt ? 0.0f : w[t];
+                                sw += wt;
+                                sww = fmaf(wt, wt, sww);
+                                srw = fmaf(r[t], wt, srw);
+                                sm += bt ? 1.0f : 0.0f;
+                            }
+                            hrow_out[0] = make_float4(sw, sww, srw, sm);
+#pragma unroll
+                            for (int o = 1; o < RUN; ++o) {
+                                const int a = o + 2 * RHO, b = o - 1;
+                                bool ba = isnan(w[a]), bb = isnan(w[b]);
+                                float wa = ba ? 0.0f : w[a], wb = bb ? 0.0f : w[b];
+                                sw += wa - wb;
+                                sww += fmaf(wa, wa, -wb * wb);
+                                srw += fmaf(r[a], wa, -r[b] * wb);
+                                sm += (ba ? 1.0f : 0.0f) - (bb ? 1.0f : 0.0f);
+                                hrow_out[o] = make_float4(sw, sww, srw, sm);
+                            }
+                        }
                     }
-                    // invalid samples: excluded from the sums and counted
-                    float sw = 0.f, sww = 0.f, srw = 0.f, sm = 0.f;
+                    __syncthreads();
+                    // phase V: sliding vertical sums down SEG rows, ZNCC, minimum over cameras
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                    for (int t = 0; t <= 2 * RHO; ++t) {
-                        bool bad = isnan(w[t]);
-                        float wt = bad ? 0.0f : w[t];
-                        sw += wt;
-                        sww = fmaf(wt, wt, sww);
-                        srw = fmaf(r[t], wt, srw);
-                        sm += bad ? 1.0f : 0.0f;
+                    for (int dy = 0; dy <= 2 * RHO; ++dy) {
+                        float4 h = Hs[base_v + dy * HS];
+                        v.x += h.x; v.y += h.y; v.z += h.z; v.w += h.w;
                     }
-                    float4* hrow_out = Hs + hrow * HS + RUN * hrun;
-                    hrow_out[0] = make_float4(sw, sww, srw, sm);
 #pragma unroll
-                    for (int o = 1; o < RUN; ++o) {
-                        const int a = o + 2 * RHO, b = o - 1;
-                        bool ba = isnan(w[a]), bb = isnan(w[b]);
-                        float wa = ba ? 0.0f : w[a], wb = bb ? 0.0f : w[b];
-                        sw += wa - wb;
-                        sww += fmaf(wa, wa, -wb * wb);
-                        srw += fmaf(r[a], wa, -r[b] * wb);
-                        sm += (ba ? 1.0f : 0.0f) - (bb ? 1.0f : 0.0f);
-                        hrow_out[o] = make_float4(sw, sww, srw, sm);
+                    for (int i = 0; i < SEG; ++i) {
+                        if (i > 0) {
+                            float4 a = Hs[base_v + (i + 2 * RHO) * HS], b = Hs[base_v + (i - 1) * HS];
+                            v.x += a.x - b.x; v.y += a.y - b.y; v.z += a.z - b.z; v.w += a.w - b.w;
+                        }
+                        float var_w = fmaf(-v.x * (1.0f / (float)N), v.x, v.y);
+                        float cov = fmaf(-st[i].x, v.x, v.z);
+                        bool ok = v.w == 0.0f && var_w >= (float)N * 1e-8f && !isnan(st[i].y);
+                        float z = fminf(1.0f, fmaxf(-1.0f, cov * st[i].y * rsqrtf(var_w)));  // |ZNCC| <= 1
+                        float cost = fmaf(-0.5f, z, 0.5f);
+                        cmin[q][i] = ok ? fminf(cmin[q][i], cost) : cmin[q][i];
                     }
-                }
-                __syncthreads();
-                // phase V: sliding vertical sums down SEG rows, ZNCC, minimum over cameras
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int dy = 0; dy <= 2 * RHO; ++dy) {
-                    float4 h = Hs[base_v + dy * HS];
-                    v.x += h.x; v.y += h.y; v.z += h.z; v.w += h.w;
-                }
-#pragma unroll
-                for (int i = 0; i < SEG; ++i) {
-                    if (i > 0) {
-                        float4 a = Hs[base_v + (i + 2 * RHO) * HS], b = Hs[base_v + (i - 1) * HS];
-                        v.x += a.x - b.x; v.y += a.y - b.y; v.z += a.z - b.z; v.w += a.w - b.w;
-                    }
-                    const float2 st = St[(oy0 + i) * TW + ox];   // NaN where the reference window is unusable
-                    float var_w = fmaf(-v.x * (1.0f / (float)N), v.x, v.y);
-                    float cov = fmaf(-st.x, v.x, v.z);
-                    bool ok = v.w == 0.0f && var_w >= (float)N * 1e-8f && !isnan(st.y);
-                    float z = fminf(1.0f, fmaxf(-1.0f, cov * st.y * rsqrtf(var_w)));  // |ZNCC| <= 1
-                    float cost = fmaf(-0.5f, z, 0.5f);
-                    cmin[i] = ok ? fminf(cmin[i], cost) : cmin[i];
                 }
             }
-            // streaming winner-take-all with the plane's aggregated cost
+            // streaming winner-take-all with each plane's aggregated cost, in plane order
 #pragma unroll
-            for (int i = 0; i < SEG; ++i) {
-                float cc = cmin[i];
-                if (needp[i]) {
-                    cplus[i] = cc;
-                    needp[i] = false;
+            for (int q = 0; q < KP; ++q) {
+                if (q >= np) break;
+                const int k = k0 + q;
+#pragma unroll
+                for (int i = 0; i < SEG; ++i) {
+                    float cc = cmin[q][i];
+                    if (k == k_lo) cfirst[i] = cc;
+                    if (needp[i]) {
+                        cplus[i] = cc;
+                        needp[i] = false;
+                    }
+                    if (cc < c1[i]) {
+                        c2[i] = c1[i];
+                        c1[i] = cc;
+                        kb[i] = k;
+                        cminus[i] = cprev[i];
+                        cplus[i] = inf;
+                        needp[i] = true;
+                    } else if (cc < c2[i]) {
+                        c2[i] = cc;
+                    }
+                    cprev[i] = cc;
                 }
-                if (cc < c1[i]) {
-                    c2[i] = c1[i];
-                    c1[i] = cc;
-                    kb[i] = k;
-                    cminus[i] = cprev[i];
-                    cplus[i] = inf;
-                    needp[i] = true;
-                } else if (cc < c2[i]) {
-                    c2[i] = cc;
-                }
-                cprev[i] = cc;
             }
         }
     }
 
-    // parabola through the winner and its neighbours in the same set; range
+    if (L.n_chunks == 1) {
+#pragma unroll
+        for (int i = 0; i < SEG; ++i) {
+            int gx = tx * TW + ox, gy = ty * TH + oy0 + i;
+            if (gx < L.W && gy < L.H) finish_pixel(L, gx, gy, c1[i], c2[i], kb[i], cminus[i], cplus[i]);
+        }
+        __syncthreads();
+        return;
+    }
+    // several work items share this tile: publish this item's result; the
+    // item that completes the tile merges all of them in plane order
+    float* part = L.partial + (size_t)item * 7 * (TH * TW);
 #pragma unroll
     for (int i = 0; i < SEG; ++i) {
-        int gx = tx * TW + ox, gy = ty * TH + oy0 + i;
-        if (gx >= L.W || gy >= L.H) continue;
-        size_t o = (size_t)gy * L.W + gx;
-        float depth = 0.f;
-        if (kb[i] >= 0) {
-            int s = 0;
-            while (s + 1 < L.n_sets && L.sets[s + 1].start <= kb[i]) ++s;
-            const SetD S = L.sets[s];
-            int li = kb[i] - S.start;
-            float delta = 0.f;
-            if (li > 0 && li < S.count - 1 && cminus[i] < inf && cplus[i] < inf) {
-                float den = cminus[i] - 2.0f * c1[i] + cplus[i];
-                if (den > 0.f) delta = fminf(0.5f, fmaxf(-0.5f, (cminus[i] - cplus[i]) / (2.0f * den)));
+        const int px = (oy0 + i) * TW + ox;
+        part[0 * TH * TW + px] = c1[i];
+        part[1 * TH * TW + px] = c2[i];
+        part[2 * TH * TW + px] = cminus[i];
+        part[3 * TH * TW + px] = cplus[i];
+        part[4 * TH * TW + px] = cfirst[i];
+        part[5 * TH * TW + px] = cprev[i];  // cost of the item's last plane
+        part[6 * TH * TW + px] = __int_as_float(kb[i]);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) *s_flag = atomicAdd(&L.done[tile], 1) == L.n_chunks - 1;
+    __syncthreads();
+    if (*s_flag) {
+        __threadfence();
+        const float* base = L.partial + (size_t)tile * L.n_chunks * 7 * (TH * TW);
+#pragma unroll 1
+        for (int i = 0; i < SEG; ++i) {
+            const int gx = tx * TW + ox, gy = ty * TH + oy0 + i;
+            const int px = (oy0 + i) * TW + ox;
+            // global winner (first chunk holding the lowest cost: ties keep the lowest plane)
+            int wc = -1;
+            float b1 = inf;
+            for (int c = 0; c < L.n_chunks; ++c) {
+                float v = __ldcg(base + ((size_t)c * 7 + 0) * (TH * TW) + px);
+                if (v < b1) {
+                    b1 = v;
+                    wc = c;
+                }
             }
-            float t = S.count > 1 ? ((float)li + delta) / (float)(S.count - 1) : 0.f;
-            float param = S.family == PS_PLANES_FRONTO ? 1.0f / fmaf(t, 1.0f / S.a - 1.0f / S.b, 1.0f / S.b)
-                                                       : fmaf(t, S.b - S.a, S.a);
-            float4 r = Ray[(oy0 + i + RHO) * HWL + ox + RHO];
-            float nr = S.nx * r.x + S.ny * r.y + S.nz * r.z;
-            depth = param / nr;
+            float b2 = inf, cm = inf, cp = inf;
+            int k = -1;
+            if (wc >= 0) {
+                const float* P = base + (size_t)wc * 7 * (TH * TW) + px;
+                b2 = __ldcg(P + 1 * (TH * TW));
+                for (int c = 0; c < L.n_chunks; ++c)
+                    if (c != wc) b2 = fminf(b2, __ldcg(base + ((size_t)c * 7 + 0) * (TH * TW) + px));
+                k = __float_as_int(__ldcg(P + 6 * (TH * TW)));
+                const int lo = wc * L.chunk, hi = min(L.n_planes, lo + L.chunk);
+                cm = k > lo ? __ldcg(P + 2 * (TH * TW))
+                            : (wc > 0 ? __ldcg(base + ((size_t)(wc - 1) * 7 + 5) * (TH * TW) + px) : inf);
+                cp = k < hi - 1 ? __ldcg(P + 3 * (TH * TW))
+                                : (wc + 1 < L.n_chunks ? __ldcg(base + ((size_t)(wc + 1) * 7 + 4) * (TH * TW) + px)
+                                                       : inf);
+            }
+            if (gx < L.W && gy < L.H) finish_pixel(L, gx, gy, b1, b2, k, cm, cp);
         }
-        if (L.depth) L.depth[o] = depth;
-        if (L.c1) L.c1[o] = c1[i];
-        if (L.c2) L.c2[o] = c2[i];
-        if (L.kstar) L.kstar[o] = kb[i];
     }
     __syncthreads();
 }
 
 template <int LV>
-__device__ __forceinline__ void run_level(const SweepParams& P, int tile, CamS* cams, unsigned char* smem) {
+__device__ __forceinline__ void run_level(const SweepParams& P, int item, CamS* cams, unsigned char* smem,
+                                          int* s_flag) {
     const LevelD& L = P.lv[LV];
     if (threadIdx.x < L.n_cams) {
         const CamJ& J = L.cams[threadIdx.x];
@@ -497,29 +620,29 @@ __device__ __forceinline__ void run_level(const SweepParams& P, int tile, CamS* 
     }
     __syncthreads();
     switch (L.rho) {
-        case 2: sweep_tile<2>(L, cams, tile, smem); break;
-        case 3: sweep_tile<3>(L, cams, tile, smem); break;
-        default: sweep_tile<4>(L, cams, tile, smem); break;
+        case 2: sweep_tile<2>(L, cams, item, smem, s_flag); break;
+        case 3: sweep_tile<3>(L, cams, item, smem, s_flag); break;
+        default: sweep_tile<4>(L, cams, item, smem, s_flag); break;
     }
 }
 
-// Persistent CTAs take tiles from a counter; levels are ordered so the
-// heavier tiles start first.
-__global__ void __launch_bounds__(NT, 2) sweep_kernel(const __grid_constant__ SweepParams P, int* tile_counter) {
+// Persistent CTAs take work items (a tile and a chunk of its planes) from a
+// counter; levels are ordered so the heavier items start first.
+__global__ void __launch_bounds__(NT, 1) sweep_kernel(const __grid_constant__ SweepParams P, int* tile_counter) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ CamS cams[PS_MAX_CAMS];
-    __shared__ int s_tile;
-    const int total = P.lv[0].n_tiles + (P.n_levels > 1 ? P.lv[1].n_tiles : 0);
+    __shared__ int s_tile, s_flag;
+    const int total = P.lv[0].n_items + (P.n_levels > 1 ? P.lv[1].n_items : 0);
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1);
         __syncthreads();
         const int t = s_tile;
         __syncthreads();
         if (t >= total) break;
-        if (t < P.lv[0].n_tiles)
-            run_level<0>(P, t, cams, smem);
+        if (t < P.lv[0].n_items)
+            run_level<0>(P, t, cams, smem, &s_flag);
         else
-            run_level<1>(P, t - P.lv[0].n_tiles, cams, smem);
+            run_level<1>(P, t - P.lv[0].n_items, cams, smem, &s_flag);
     }
 }
 
@@ -617,9 +740,13 @@ struct psweep_s {
     PlaneD* planes[PS_MAX_LEVELS] = {};
     float* ref_img[PS_MAX_LEVELS] = {};
     float2* stats[PS_MAX_LEVELS] = {};
+    float* partial[PS_MAX_LEVELS] = {};
+    int* done[PS_MAX_LEVELS] = {};
+    int chunk[PS_MAX_LEVELS] = {};
     float4* quad[PS_MAX_LEVELS][PS_MAX_CAMS] = {};
     int* tile_counter = nullptr;
     int grid = 0;
+    int smem_optin = 0;
     float* out_depth[PS_MAX_LEVELS] = {};
     float* out_c1[PS_MAX_LEVELS] = {};
     float* out_c2[PS_MAX_LEVELS] = {};
@@ -644,6 +771,8 @@ void free_sweep(psweep_t* h) {
         cudaFree(h->planes[l]);
         cudaFree(h->ref_img[l]);
         cudaFree(h->stats[l]);
+        cudaFree(h->partial[l]);
+        cudaFree(h->done[l]);
         for (int j = 0; j < PS_MAX_CAMS; ++j) cudaFree(h->quad[l][j]);
         cudaFree(h->out_depth[l]);
         cudaFree(h->out_c1[l]);
@@ -805,6 +934,16 @@ extern "C" int psweep_create(const ps_sweep_desc* d, psweep_t** out) {
         }
         PS_TRY(cudaMalloc(&h->ref_img[l], sizeof(float) * (size_t)W * H));
         PS_TRY(cudaMalloc(&h->stats[l], sizeof(float2) * (size_t)W * H));
+        {
+            // work items: tiles x chunks of at most PLANE_CHUNK planes, so that
+            // items of both levels cost about the same and balance across SMs
+            const int n_tiles = ((W + TW - 1) / TW) * ((H + TH - 1) / TH);
+            const int n_chunks = (h->n_planes[l] + PLANE_CHUNK - 1) / PLANE_CHUNK;
+            h->chunk[l] = (h->n_planes[l] + n_chunks - 1) / n_chunks;
+            if (n_chunks > 1)
+                PS_TRY(cudaMalloc(&h->partial[l], sizeof(float) * 7 * TH * TW * (size_t)n_tiles * n_chunks));
+            PS_TRY(cudaMalloc(&h->done[l], sizeof(int) * (size_t)n_tiles));
+        }
         for (int j = 0; j < d->n_cams; ++j) {
             const ps_camera& cj = h->lcam[l][j];
             PS_TRY(cudaMalloc(&h->quad[l][j], sizeof(float4) * (size_t)cj.width * cj.height));
@@ -821,12 +960,18 @@ extern "C" int psweep_create(const ps_sweep_desc* d, psweep_t** out) {
         PS_TRY(cudaMalloc(&h->stage_img[1 + j], (size_t)d->cams[j].width * d->cams[j].height));
     PS_TRY(cudaMalloc(&h->stage_depth, sizeof(float) * (size_t)d->ref.width * d->ref.height));
     PS_TRY(cudaMalloc(&h->tile_counter, sizeof(int)));
-    PS_TRY(cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<4>::smem));
+    {
+        int dev = 0, optin = 0;
+        PS_TRY(cudaGetDevice(&dev));
+        PS_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        h->smem_optin = optin;
+        PS_TRY(cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024));
+    }
     {
         int dev = 0, sms = 0, per_sm = 0;
         PS_TRY(cudaGetDevice(&dev));
         PS_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        PS_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel, NT, Geo<4>::smem));
+        PS_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel, NT, Geo<4>::smem(d->n_cams)));
         h->grid = sms * std::max(1, per_sm);
     }
     PS_TRY(cudaDeviceSynchronize());
@@ -855,9 +1000,9 @@ extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_
     // heavier level first in the tile order (planes x halo samples per tile)
     int order[PS_MAX_LEVELS] = {0, 1};
     if (h->n_levels == 2) {
-        auto cost = [&](int l) {
+        auto cost = [&](int l) {  // one work item: planes x halo samples
             int r = h->levels[l].window / 2;
-            return (double)h->n_planes[l] * (TW + 2 * r) * (TH + 2 * r);
+            return (double)h->chunk[l] * (TW + 2 * r) * (TH + 2 * r);
         };
         if (cost(1) > cost(0)) std::swap(order[0], order[1]);
     }
@@ -905,6 +1050,12 @@ extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_
         D.tiles_x = (W + TW - 1) / TW;
         D.tiles_y = (H + TH - 1) / TH;
         D.n_tiles = D.tiles_x * D.tiles_y;
+        D.chunk = h->chunk[l];
+        D.n_chunks = (D.n_planes + D.chunk - 1) / D.chunk;
+        D.n_items = D.n_tiles * D.n_chunks;
+        D.partial = h->partial[l];
+        D.done = h->done[l];
+        PS_CUDA(cudaMemsetAsync(D.done, 0, sizeof(int) * D.n_tiles, s));
         const ps_level_out* lo = level_out ? &level_out[l] : nullptr;
         D.depth = lo && lo->depth ? lo->depth : h->out_depth[l];
         D.c1 = lo && lo->best_cost ? lo->best_cost : h->out_c1[l];
@@ -916,9 +1067,9 @@ extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_
     int tiles = 0;
     for (int l = 0; l < h->n_levels; ++l) {
         int r = P.lv[l].rho;
-        size_t b = r == 2 ? Geo<2>::smem : r == 3 ? Geo<3>::smem : Geo<4>::smem;
-        smem = std::max(smem, b);
-        tiles += P.lv[l].n_tiles;
+        const int nc = h->n_cams;
+        smem = std::max(smem, r == 2 ? Geo<2>::smem(nc) : r == 3 ? Geo<3>::smem(nc) : Geo<4>::smem(nc));
+        tiles += P.lv[l].n_items;
     }
     PS_CUDA(cudaMemsetAsync(h->tile_counter, 0, sizeof(int), s));
     h->prof.mark(1, s);
