@@ -96,6 +96,25 @@ typedef struct {
     ps_plane_set sets[PS_MAX_SETS];
 } ps_level;
 
+/* Depth map filtering (Sec. III-A, "Depth map filtering"), all zero = off.
+ * Per level, a pixel is an outlier when its best cost exceeds alpha of its
+ * image part (alpha_upper for pixels whose centre lies above the
+ * full-resolution row split_row, alpha_lower below; split_row < 0 means half
+ * the height; the paper uses 0.05 and 0.3) or when its second-best cost is
+ * below ratio_min times the best (the paper's uniqueness ratio; it gives no
+ * value).  After merging, a pixel keeps its depth only if at least a
+ * fraction delta of the other pixels of its window x window neighbourhood
+ * inside the image have a depth within gamma of it (the paper: gamma 0.5 m,
+ * delta 0.3).  The boxes are applied last. */
+typedef struct {
+    int32_t enable;
+    int32_t window;         /* odd, 1 .. 15 */
+    double alpha_upper, alpha_lower;
+    double split_row;
+    double ratio_min;
+    double gamma, delta;
+} ps_filter;
+
 typedef struct {
     ps_camera ref;                 /* reference camera at full resolution */
     int32_t n_cams;                /* matching cameras, 1 .. PS_MAX_CAMS */
@@ -103,6 +122,7 @@ typedef struct {
     const ps_pose* ref_to_cam;     /* host, n_cams entries: X_cam = R X_ref + t */
     int32_t n_levels;              /* 1 .. PS_MAX_LEVELS: at most one DOWNSAMPLE and one CROP */
     const ps_level* levels;        /* host */
+    ps_filter filter;              /* depth map filtering; zero-initialised = off */
 } ps_sweep_desc;
 
 /* Half-open pixel rectangle [x0, x1) x [y0, y1) in full-resolution
@@ -135,9 +155,10 @@ int psweep_create(const ps_sweep_desc* desc, psweep_t** out);
 /* Depth map of the reference camera for one synchronised frame (Sec. III-A):
  * per level, warp each matching image through every plane, ZNCC cost over
  * the window, minimum over matching cameras, winner-take-all with parabolic
- * sub-plane refinement; then merge the levels at full resolution (crop depth
- * where valid, else the downsampled level's depth at (u/factor, v/factor))
- * and zero the pixels inside the boxes.
+ * sub-plane refinement; then, when the descriptor enables it, the per-level
+ * cost filters; merge the levels at full resolution (crop depth where valid,
+ * else the downsampled level's depth at (u/factor, v/factor)); the
+ * continuity filter; and zero the pixels inside the boxes.
  *   images    host array of 1 + n_cams device pointers: [0] reference, then
  *             the matching cameras, each a contiguous uint8 H x W image of
  *             its camera's full-resolution size.

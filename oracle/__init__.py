@@ -57,6 +57,11 @@ class OrLevel(C.Structure):
                 ("window", C.c_int32), ("n_sets", C.c_int32), ("sets", OrPlaneSet * 4)]
 
 
+class OrFilter(C.Structure):
+    _fields_ = [("alpha_upper", C.c_double), ("alpha_lower", C.c_double), ("split_row", C.c_double),
+                ("ratio_min", C.c_double), ("gamma", C.c_double), ("delta", C.c_double), ("window", C.c_int32)]
+
+
 class OrTsdfDesc(C.Structure):
     _fields_ = [("voxel_size", C.c_double), ("mu", C.c_double), ("w_max", C.c_double),
                 ("block_dim", C.c_int32), ("dense_dim", C.c_int32 * 3), ("origin", C.c_double * 3),
@@ -89,6 +94,8 @@ def lib():
             L.orc_wta.argtypes = [_D, C.c_int32, C.c_int32, _P, _P, _D]
             L.orc_merge.argtypes = [C.c_int32, C.c_int32, _D, C.c_int32, _D, C.c_int32, C.c_int32, _P,
                                     C.c_int32, _D]
+            L.orc_filter_frame.argtypes = [C.c_int32, C.c_int32, _D, _D, _D, C.c_int32, _D, _D, _D, C.c_int32,
+                                           C.c_int32, C.POINTER(OrFilter), _P, C.c_int32, _D, _P]
             L.orc_tsdf_new.argtypes = [C.POINTER(OrTsdfDesc)]
             L.orc_tsdf_new.restype = C.c_void_p
             L.orc_tsdf_free.argtypes = [_P]
@@ -270,6 +277,32 @@ def merge(W: int, H: int, low: Optional[np.ndarray], s: int, crop: Optional[np.n
     return out
 
 
+def filter_params(f) -> OrFilter:
+    return OrFilter(alpha_upper=f.alpha_upper, alpha_lower=f.alpha_lower, split_row=f.split_row,
+                    ratio_min=f.ratio_min, gamma=f.gamma, delta=f.delta, window=f.window)
+
+
+def filter_frame(W, H, low=None, s=1, crop=None, crop_w=0, crop_h=0, params=None, boxes=None):
+    """Depth filtering, merge and masks at full resolution.  low / crop: dicts
+    with depth, c1, c2 arrays of their level.  Returns (depth, ambiguous)."""
+    out = np.zeros((H, W))
+    amb = np.zeros((H, W), dtype=np.uint8)
+    f = filter_params(params)
+
+    def arrs(d):
+        if d is None:
+            return None, None, None
+        return tuple(np.ascontiguousarray(d[k], dtype=np.float64) for k in ("depth", "c1", "c2"))
+
+    ld, l1, l2 = arrs(low)
+    cd, k1, k2 = arrs(crop)
+    bx = np.ascontiguousarray(boxes if boxes is not None else np.zeros((0, 4)), dtype=np.int32)
+    p = lambda a: _dptr(a) if a is not None else None  # noqa: E731
+    lib().orc_filter_frame(W, H, p(ld), p(l1), p(l2), s, p(cd), p(k1), p(k2), crop_w, crop_h, C.byref(f),
+                           bx.ctypes.data, len(bx), _dptr(out), amb.ctypes.data)
+    return out, amb.astype(bool)
+
+
 def depth_frame(wl, imgs, boxes=None):
     """Whole-frame depth of a workload (every level swept at every pixel,
     then merged and masked): dict(depth (H, W), levels [per-level dicts])."""
@@ -284,7 +317,18 @@ def depth_frame(wl, imgs, boxes=None):
         else:
             crop, cw, ch = res["depth"], lv.crop_w, lv.crop_h
     D = merge(rig.ref.width, rig.ref.height, low, s, crop, cw, ch, boxes)
-    return dict(depth=D, levels=levels)
+    out = dict(depth=D, levels=levels)
+    flt = getattr(wl, "filters", None)
+    if flt is not None and flt.enable:
+        lo = cr = None
+        for lv, res in zip(wl.levels, levels):
+            if lv.kind == 0:
+                lo = res
+            else:
+                cr = res
+        out["filtered"], out["filtered_amb"] = filter_frame(rig.ref.width, rig.ref.height, lo, s, cr, cw, ch, flt,
+                                                             boxes)
+    return out
 
 
 # ----------------------------------------------------------------- TSDF

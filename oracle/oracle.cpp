@@ -743,6 +743,88 @@ void orc_merge(int32_t W, int32_t H, const double* low, int32_t s, const double*
         }
 }
 
+// Depth map filtering (Sec. III-A, "Depth map filtering"), then merging and
+// masking.  Per level: a pixel is an outlier when its best cost exceeds
+// alpha of its image part (alpha_upper above the full-resolution row
+// split_row, alpha_lower below), or when its second-best cost is below
+// ratio_min times its best cost (the ratio of second to first best measures
+// uniqueness).  The surviving level depths are merged as in orc_merge.  On the
+// merged map, a pixel keeps its depth only if at least a fraction delta of
+// the other pixels of its (2w+1)^2 window inside the image have a depth
+// within gamma of it.  Finally the boxes are zeroed.  amb (optional, W x H)
+// marks pixels whose outcome a float rounding of a cost (1e-4) or a depth
+// (1e-5 relative) could flip.
+struct FilterParams {
+    double alpha_upper, alpha_lower, split_row, ratio_min, gamma, delta;
+    int32_t window;
+};
+
+static bool keep_level(double c1, double c2, double alpha, double ratio, bool* amb) {
+    const double tol = 1e-4;
+    if (std::isfinite(c1) && std::fabs(c1 - alpha) < tol) *amb = true;
+    if (std::isfinite(c1) && std::isfinite(c2) && std::fabs(c2 - ratio * c1) < tol * (1.0 + c1)) *amb = true;
+    return c1 <= alpha && c2 >= ratio * c1;
+}
+
+void orc_filter_frame(int32_t W, int32_t H, const double* low_d, const double* low_c1, const double* low_c2,
+                      int32_t s, const double* crop_d, const double* crop_c1, const double* crop_c2, int32_t crop_w,
+                      int32_t crop_h, const FilterParams* f, const int32_t* boxes, int32_t n_boxes, double* out,
+                      uint8_t* amb) {
+    const double split = f->split_row >= 0 ? f->split_row : H / 2.0;
+    int x0 = (W - crop_w) / 2, y0 = (H - crop_h) / 2;
+    int Wl = s > 0 ? W / s : 0, Hl = s > 0 ? H / s : 0;
+    std::vector<double> merged((size_t)W * H, 0.0);
+    std::vector<uint8_t> am((size_t)W * H, 0);
+    for (int v = 0; v < H; ++v)
+        for (int u = 0; u < W; ++u) {
+            double val = 0.0;
+            bool a = false;
+            if (low_d) {
+                int lu = std::min(u / s, Wl - 1), lv = std::min(v / s, Hl - 1);
+                size_t i = (size_t)lv * Wl + lu;
+                double row = s * lv + (s - 1) / 2.0;  // full-resolution row of the level pixel's centre
+                double alpha = row < split ? f->alpha_upper : f->alpha_lower;
+                if (low_d[i] > 0.0 && keep_level(low_c1[i], low_c2[i], alpha, f->ratio_min, &a)) val = low_d[i];
+            }
+            if (crop_d && u >= x0 && u < x0 + crop_w && v >= y0 && v < y0 + crop_h) {
+                size_t i = (size_t)(v - y0) * crop_w + (u - x0);
+                double alpha = v < split ? f->alpha_upper : f->alpha_lower;
+                if (crop_d[i] > 0.0 && keep_level(crop_c1[i], crop_c2[i], alpha, f->ratio_min, &a)) val = crop_d[i];
+            }
+            merged[(size_t)v * W + u] = val;
+            am[(size_t)v * W + u] = a;
+        }
+    const int w = f->window / 2;
+    for (int v = 0; v < H; ++v)
+        for (int u = 0; u < W; ++u) {
+            double d = merged[(size_t)v * W + u];
+            double res = 0.0;
+            bool a = am[(size_t)v * W + u];
+            if (d > 0.0) {
+                int cons = 0, tot = 0;
+                for (int dy = -w; dy <= w; ++dy)
+                    for (int dx = -w; dx <= w; ++dx) {
+                        if (dx == 0 && dy == 0) continue;
+                        int uu = u + dx, vv = v + dy;
+                        if (uu < 0 || vv < 0 || uu >= W || vv >= H) continue;
+                        ++tot;
+                        double dn = merged[(size_t)vv * W + uu];
+                        if (am[(size_t)vv * W + uu]) a = true;  // a neighbour's own depth may flip
+                        if (dn > 0.0 && std::fabs(std::fabs(dn - d) - f->gamma) < 1e-5 * (d + dn)) a = true;
+                        if (dn > 0.0 && std::fabs(dn - d) < f->gamma) ++cons;
+                    }
+                if (tot > 0 && cons >= f->delta * tot) res = d;
+            }
+            for (int b = 0; b < n_boxes; ++b)
+                if (u >= boxes[4 * b] && u < boxes[4 * b + 2] && v >= boxes[4 * b + 1] && v < boxes[4 * b + 3]) {
+                    res = 0.0;
+                    a = false;
+                }
+            out[(size_t)v * W + u] = res;
+            if (amb) amb[(size_t)v * W + u] = a;
+        }
+}
+
 void* orc_tsdf_new(const TsdfDesc* d) {
     Tsdf* T = new Tsdf();
     T->d = *d;

@@ -651,29 +651,79 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const __grid_constant__ Sw
 struct MergeP {
     int W, H;
     const float* low;
+    const float *low_c1, *low_c2;
     int s, Wl, Hl;
     const float* crop;
+    const float *crop_c1, *crop_c2;
     int cx0, cy0, cw, ch;
+    int filter;                     // apply the per-level cost filters
+    float alpha_upper, alpha_lower, split_row, ratio_min;
     int n_boxes;
     ps_box boxes[16];
-    const ps_box* boxes_dev;  // when n_boxes > 16
 };
+
+// A level pixel survives the cost filters: best cost at most alpha of its
+// image part, second best at least ratio_min times the best.
+__device__ __forceinline__ bool keep_level(const MergeP& P, float c1, float c2, float row) {
+    float alpha = row < P.split_row ? P.alpha_upper : P.alpha_lower;
+    return c1 <= alpha && c2 >= P.ratio_min * c1;
+}
 
 __global__ void merge_kernel(const __grid_constant__ MergeP P, const ps_box* boxes, float* out) {
     int u = blockIdx.x * blockDim.x + threadIdx.x;
     int v = blockIdx.y;
     if (u >= P.W || v >= P.H) return;
     float val = 0.f;
-    if (P.low) val = P.low[(size_t)min(v / P.s, P.Hl - 1) * P.Wl + min(u / P.s, P.Wl - 1)];
+    if (P.low) {
+        int lu = min(u / P.s, P.Wl - 1), lv = min(v / P.s, P.Hl - 1);
+        size_t i = (size_t)lv * P.Wl + lu;
+        val = P.low[i];
+        if (P.filter && val > 0.f &&
+            !keep_level(P, P.low_c1[i], P.low_c2[i], (float)(P.s * lv) + 0.5f * (float)(P.s - 1)))
+            val = 0.f;
+    }
     if (P.crop && u >= P.cx0 && u < P.cx0 + P.cw && v >= P.cy0 && v < P.cy0 + P.ch) {
-        float c = P.crop[(size_t)(v - P.cy0) * P.cw + (u - P.cx0)];
-        if (c > 0.f) val = c;
+        size_t i = (size_t)(v - P.cy0) * P.cw + (u - P.cx0);
+        float c = P.crop[i];
+        if (c > 0.f && (!P.filter || keep_level(P, P.crop_c1[i], P.crop_c2[i], (float)v))) val = c;
     }
     for (int b = 0; b < P.n_boxes; ++b) {
         ps_box bx = b < 16 ? P.boxes[b] : boxes[b];
         if (u >= bx.x0 && u < bx.x1 && v >= bx.y0 && v < bx.y1) val = 0.f;
     }
     out[(size_t)v * P.W + u] = val;
+}
+
+// Local depth continuity on the merged map, then the boxes: a pixel keeps its
+// depth when at least a fraction delta of the other in-image pixels of its
+// window have a depth within gamma of it.
+__global__ void continuity_kernel(const float* in, int W, int H, int half, float gamma, float delta,
+                                  const __grid_constant__ MergeP P, const ps_box* boxes, float* out) {
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    int v = blockIdx.y;
+    if (u >= W || v >= H) return;
+    float d = in[(size_t)v * W + u];
+    float res = 0.f;
+    if (d > 0.f) {
+        int cons = 0, tot = 0;
+        for (int dy = -half; dy <= half; ++dy) {
+            int vv = v + dy;
+            if (vv < 0 || vv >= H) continue;
+            for (int dx = -half; dx <= half; ++dx) {
+                int uu = u + dx;
+                if (uu < 0 || uu >= W || (dx == 0 && dy == 0)) continue;
+                ++tot;
+                float dn = in[(size_t)vv * W + uu];
+                cons += (dn > 0.f && fabsf(dn - d) < gamma) ? 1 : 0;
+            }
+        }
+        if (tot > 0 && (float)cons >= delta * (float)tot) res = d;
+    }
+    for (int b = 0; b < P.n_boxes; ++b) {
+        ps_box bx = b < 16 ? P.boxes[b] : boxes[b];
+        if (u >= bx.x0 && u < bx.x1 && v >= bx.y0 && v < bx.y1) res = 0.f;
+    }
+    out[(size_t)v * W + u] = res;
 }
 
 }  // namespace
@@ -758,6 +808,8 @@ struct psweep_s {
     // host-frame staging (psweep_frame_host)
     uint8_t* stage_img[1 + PS_MAX_CAMS] = {};
     float* stage_depth = nullptr;
+    ps_filter filter{};
+    float* merged = nullptr;  // merged map before the continuity filter
     StageProfiler prof;
 };
 
@@ -783,6 +835,7 @@ void free_sweep(psweep_t* h) {
     cudaFree(h->tile_counter);
     for (int i = 0; i <= PS_MAX_CAMS; ++i) cudaFree(h->stage_img[i]);
     cudaFree(h->stage_depth);
+    cudaFree(h->merged);
     delete h;
 }
 
@@ -855,6 +908,13 @@ extern "C" int psweep_create(const ps_sweep_desc* d, psweep_t** out) {
         }
     }
     PS_ARG(n_down <= 1 && n_crop <= 1, "at most one downsample level and one crop level");
+    if (d->filter.enable) {
+        const ps_filter& f = d->filter;
+        PS_ARG(f.window >= 1 && f.window <= 15 && f.window % 2 == 1, "filter: window must be odd, 1 .. 15");
+        PS_ARG(f.delta >= 0 && f.delta <= 1 && f.gamma > 0 && f.ratio_min >= 0,
+               "filter: need 0 <= delta <= 1, gamma > 0, ratio_min >= 0");
+        PS_ARG(std::isfinite(f.alpha_upper) && std::isfinite(f.alpha_lower), "filter: alpha not finite");
+    }
     for (int j = 0; j < d->n_cams; ++j) {
         st = check_camera(d->cams[j], "matching camera");
         if (st) return st;
@@ -864,6 +924,7 @@ extern "C" int psweep_create(const ps_sweep_desc* d, psweep_t** out) {
     h->ref = d->ref;
     h->n_cams = d->n_cams;
     h->n_levels = d->n_levels;
+    h->filter = d->filter;
     for (int j = 0; j < d->n_cams; ++j) {
         h->cams[j] = d->cams[j];
         h->poses[j] = d->ref_to_cam[j];
@@ -959,6 +1020,7 @@ extern "C" int psweep_create(const ps_sweep_desc* d, psweep_t** out) {
     for (int j = 0; j < d->n_cams; ++j)
         PS_TRY(cudaMalloc(&h->stage_img[1 + j], (size_t)d->cams[j].width * d->cams[j].height));
     PS_TRY(cudaMalloc(&h->stage_depth, sizeof(float) * (size_t)d->ref.width * d->ref.height));
+    if (d->filter.enable) PS_TRY(cudaMalloc(&h->merged, sizeof(float) * (size_t)d->ref.width * d->ref.height));
     PS_TRY(cudaMalloc(&h->tile_counter, sizeof(int)));
     {
         int dev = 0, optin = 0;
@@ -1088,22 +1150,45 @@ extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_
         const ps_level& L = h->levels[l];
         if (L.kind == PS_LEVEL_DOWNSAMPLE) {
             M.low = P.lv[oi].depth;
+            M.low_c1 = P.lv[oi].c1;
+            M.low_c2 = P.lv[oi].c2;
             M.s = L.factor;
             M.Wl = h->lW[l];
             M.Hl = h->lH[l];
         } else {
             M.crop = P.lv[oi].depth;
+            M.crop_c1 = P.lv[oi].c1;
+            M.crop_c2 = P.lv[oi].c2;
             M.cx0 = h->cx0[l];
             M.cy0 = h->cy0[l];
             M.cw = L.crop_w;
             M.ch = L.crop_h;
         }
     }
+    const ps_filter& F = h->filter;
+    if (F.enable) {
+        M.filter = 1;
+        M.alpha_upper = (float)F.alpha_upper;
+        M.alpha_lower = (float)F.alpha_lower;
+        M.split_row = (float)(F.split_row >= 0 ? F.split_row : h->ref.height / 2.0);
+        M.ratio_min = (float)F.ratio_min;
+    }
     M.n_boxes = n_boxes;
     for (int b = 0; b < n_boxes && b < 16; ++b) M.boxes[b] = boxes[b];
     if (n_boxes > 16)
         PS_CUDA(cudaMemcpyAsync(h->boxes_dev, boxes, sizeof(ps_box) * n_boxes, cudaMemcpyHostToDevice, s));
-    merge_kernel<<<dim3((M.W + 127) / 128, M.H), 128, 0, s>>>(M, h->boxes_dev, depth_out);
+    if (F.enable) {
+        // cost filters and merge into the scratch map; continuity and boxes into the output
+        MergeP M0 = M;
+        M0.n_boxes = 0;
+        merge_kernel<<<dim3((M.W + 127) / 128, M.H), 128, 0, s>>>(M0, h->boxes_dev, h->merged);
+        PS_CUDA(cudaGetLastError());
+        continuity_kernel<<<dim3((M.W + 127) / 128, M.H), 128, 0, s>>>(h->merged, M.W, M.H, F.window / 2,
+                                                                       (float)F.gamma, (float)F.delta, M,
+                                                                       h->boxes_dev, depth_out);
+    } else {
+        merge_kernel<<<dim3((M.W + 127) / 128, M.H), 128, 0, s>>>(M, h->boxes_dev, depth_out);
+    }
     PS_CUDA(cudaGetLastError());
     h->prof.mark(3, s);
     h->prof.end_call();

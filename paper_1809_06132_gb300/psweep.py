@@ -54,9 +54,16 @@ class ps_level(C.Structure):
                 ("window", C.c_int32), ("n_sets", C.c_int32), ("sets", ps_plane_set * MAX_SETS)]
 
 
+class ps_filter(C.Structure):
+    _fields_ = [("enable", C.c_int32), ("window", C.c_int32), ("alpha_upper", C.c_double),
+                ("alpha_lower", C.c_double), ("split_row", C.c_double), ("ratio_min", C.c_double),
+                ("gamma", C.c_double), ("delta", C.c_double)]
+
+
 class ps_sweep_desc(C.Structure):
     _fields_ = [("ref", ps_camera), ("n_cams", C.c_int32), ("cams", C.POINTER(ps_camera)),
-                ("ref_to_cam", C.POINTER(ps_pose)), ("n_levels", C.c_int32), ("levels", C.POINTER(ps_level))]
+                ("ref_to_cam", C.POINTER(ps_pose)), ("n_levels", C.c_int32), ("levels", C.POINTER(ps_level)),
+                ("filter", ps_filter)]
 
 
 class ps_box(C.Structure):
@@ -182,7 +189,7 @@ def level_shape(ref, lv):
 class Sweep:
     """Multi-scale fisheye plane sweep of one rig (psweep_create / psweep_depth)."""
 
-    def __init__(self, rig, levels):
+    def __init__(self, rig, levels, filters=None):
         L = load()
         self.rig = rig
         self.levels = list(levels)
@@ -191,6 +198,10 @@ class Sweep:
         self._levels = (ps_level * len(self.levels))(*[level(lv) for lv in self.levels])
         d = ps_sweep_desc(ref=camera(rig.ref), n_cams=len(rig.cams), cams=self._cams, ref_to_cam=self._poses,
                           n_levels=len(self.levels), levels=self._levels)
+        if filters is not None and filters.enable:
+            d.filter = ps_filter(enable=1, window=filters.window, alpha_upper=filters.alpha_upper,
+                                 alpha_lower=filters.alpha_lower, split_row=filters.split_row,
+                                 ratio_min=filters.ratio_min, gamma=filters.gamma, delta=filters.delta)
         h = C.c_void_p()
         _check(L.psweep_create(C.byref(d), C.byref(h)))
         self.h = h

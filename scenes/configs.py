@@ -68,6 +68,21 @@ class Level:
 
 
 @dataclass
+class Filters:
+    """Depth map filtering (best cost, uniqueness, local continuity).  The
+    paper gives alpha 0.05 / 0.3 for the upper / lower image part, gamma
+    0.5 m and delta 0.3; the ratio threshold and the window are not given."""
+    enable: bool = True
+    alpha_upper: float = 0.05
+    alpha_lower: float = 0.3
+    split_row: float = -1.0      # < 0: half the image height
+    ratio_min: float = 1.1
+    gamma: float = 0.5
+    delta: float = 0.3
+    window: int = 5
+
+
+@dataclass
 class Rig:
     ref: Camera
     cams: List[Camera]
@@ -98,6 +113,7 @@ class Workload:
     world_to_ref: List[Pose]          # trajectory, one pose per frame
     boxes: List[np.ndarray]           # per frame (n, 4) int32 half-open pixel rects
     ss: int = 2                       # supersampling used when rendering
+    filters: Optional[Filters] = None  # depth map filtering (None = off)
 
     @property
     def n_frames(self) -> int:

@@ -163,3 +163,31 @@ def test_argument_errors_on_gpu(street_small):
     with pytest.raises(P.PsError) as e:
         sw.depth(dev, boxes=np.zeros((300, 4), np.int32))
     assert e.value.status == P.PS_ERR_ARG
+
+
+def test_street_small_filters_parity(street_small):
+    # depth map filtering (best cost, uniqueness, continuity) with the paper's
+    # alpha / gamma / delta; outcomes within float rounding of a threshold are
+    # excluded (the oracle marks them)
+    import copy
+    wl, imgs = street_small
+    flt = scenes.Filters()
+    sw = P.Sweep(wl.rig, wl.levels, filters=flt)
+    depth, g = _gpu_levels(sw, imgs, wl.boxes[0])
+    wf = copy.copy(wl)
+    wf.filters = flt
+    o = oracle.depth_frame(wf, imgs, wl.boxes[0])
+    od, amb = o["filtered"], o["filtered_amb"]
+    ok = ~amb
+    assert ok.mean() > 0.9
+    agree = ((od > 0) == (depth > 0))[ok].mean()
+    both = ok & (od > 0) & (depth > 0)
+    rel = np.abs(depth[both] - od[both]) / od[both]
+    print("filters", dict(kept=float((od > 0).mean()), unfiltered=float((o["depth"] > 0).mean()),
+                          agree=float(agree), depth_ok=float((rel <= 1e-4).mean())))
+    assert (od > 0).mean() < (o["depth"] > 0).mean()       # the filters remove depths
+    assert agree >= 0.995
+    assert (rel <= 1e-4).mean() >= 0.995
+    H, W = depth.shape
+    for (x0, y0, x1, y1) in wl.boxes[0]:
+        assert (depth[max(0, y0):min(H, y1), max(0, x0):min(W, x1)] == 0).all()
