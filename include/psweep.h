@@ -216,8 +216,8 @@ int tsdf_integrate(tsdf_t* t, const float* depth, const ps_pose* world_to_cam, c
  * the latched device status (then clears it). */
 int tsdf_count(tsdf_t* t, int64_t* n_blocks, void* stream);
 
-/* Synchronises `stream` and copies out every allocated block, in pool
- * order: keys (device int32, capacity x 3 block indices), D and W (device
+/* Synchronises `stream` and copies out every allocated block, in pool-slot
+ * order (for a dense grid: block bx + nbx (by + nby bz)): keys (device int32, capacity x 3 block indices), D and W (device
  * float32, capacity x 512 voxels each, voxel index x + 8 y + 64 z).
  * Voxels with w < min_weight are reported with W = 0 and D = 0 (Sec. III-C:
  * only voxels with at least 3 observations are kept; pass 0 for all).
@@ -228,6 +228,24 @@ int tsdf_extract(tsdf_t* t, float min_weight, int32_t* keys, float* D, float* W,
 
 /* Synchronises `stream`, returns and clears the latched device status. */
 int tsdf_status(tsdf_t* t, void* stream);
+
+/* Local-map swap-out (Sec. III-C: blocks that are no longer in the local map
+ * are swapped out of GPU memory).  Every allocated block whose centre lies
+ * outside the local-map box around local_center (half extents local_half of
+ * the descriptor) is copied to the caller's buffers (device; keys capacity x 3,
+ * D and W capacity x 512, in an unspecified order), removed from the hash
+ * table, and its pool slot freed for reuse by later allocations.  At most
+ * `capacity` blocks leave per call; if more lie outside, the rest stay and the
+ * call returns PS_ERR_CAPACITY.  *n_out = blocks written.  Hashed maps with a
+ * local map only.  Synchronises `stream`. */
+int tsdf_swap_out(tsdf_t* t, const double* local_center, int32_t* keys, float* D, float* W, int64_t capacity,
+                  int64_t* n_out, void* stream);
+
+/* Insert or overwrite n blocks (device keys n x 3, D and W n x 512, the layout
+ * tsdf_extract and tsdf_swap_out produce): checkpoint resume and swap-in.
+ * Hashed maps only.  Asynchronous on `stream`; a full pool is latched
+ * (PS_ERR_CAPACITY) and the blocks that found no slot are skipped. */
+int tsdf_load(tsdf_t* t, const int32_t* keys, const float* D, const float* W, int64_t n, void* stream);
 
 void tsdf_destroy(tsdf_t* t);
 

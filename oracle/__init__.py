@@ -106,6 +106,9 @@ def lib():
             L.orc_tsdf_dump.argtypes = [_P, _P, _D, _D, _P]
             L.orc_tsdf_alloc_counts.argtypes = [_P, _P, _P]
             L.orc_tsdf_alloc_sets.argtypes = [_P, _P, _P]
+            L.orc_tsdf_swap_out.argtypes = [_P, _D, _P, _D, _D, _P, _P]
+            L.orc_tsdf_swap_out.restype = C.c_int64
+            L.orc_tsdf_load.argtypes = [_P, C.c_int64, _P, _D, _D]
             L.orc_tsdf_ever_maybe.argtypes = [_P, _P]
             L.orc_tsdf_ever_maybe.restype = C.c_int64
             _lib = L
@@ -380,6 +383,26 @@ class Tsdf:
         m = np.zeros((int(nm[0]), 3), dtype=np.int64)
         lib().orc_tsdf_alloc_sets(self.h, s.ctypes.data, m.ctypes.data)
         return s, m
+
+    def swap_out(self, local_center):
+        """Remove the blocks outside the local map: (keys, D, W, ambiguous keys)."""
+        lc = np.ascontiguousarray(local_center, dtype=np.float64)
+        n = lib().orc_tsdf_count(self.h)
+        B3 = self.params.block_dim ** 3
+        keys = np.zeros((n, 3), dtype=np.int64)
+        D = np.zeros((n, B3))
+        W = np.zeros((n, B3))
+        na = np.zeros(1, dtype=np.int64)
+        amb = np.zeros((n, 3), dtype=np.int64)
+        m = lib().orc_tsdf_swap_out(self.h, _dptr(lc), keys.ctypes.data, _dptr(D), _dptr(W), na.ctypes.data,
+                                    amb.ctypes.data)
+        return keys[:m], D[:m], W[:m], amb[:int(na[0])]
+
+    def load(self, keys, D, W):
+        keys = np.ascontiguousarray(keys, dtype=np.int64)
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        W = np.ascontiguousarray(W, dtype=np.float64)
+        lib().orc_tsdf_load(self.h, len(keys), keys.ctypes.data, _dptr(D), _dptr(W))
 
     def ever_maybe(self):
         n = lib().orc_tsdf_ever_maybe(self.h, None)

@@ -898,6 +898,66 @@ void orc_tsdf_alloc_sets(void* h, int64_t* strict, int64_t* maybe) {
     }
 }
 
+// Local-map swap-out (Sec. III-C: blocks that are no longer in the local map
+// are swapped out of GPU memory): remove every block whose centre lies
+// outside the box of half extents local_half around lc, returning the removed
+// blocks in key order.  n_amb counts removed or kept blocks whose centre lies
+// within tau_len of the box (a float rounding may decide them either way);
+// their keys come first in amb_keys when given.
+int64_t orc_tsdf_swap_out(void* h, const double* lc, int64_t* keys, double* D, double* W, int64_t* n_amb,
+                          int64_t* amb_keys) {
+    Tsdf* T = static_cast<Tsdf*>(h);
+    const TsdfDesc& d = T->d;
+    const int B = d.block_dim;
+    const int B3 = B * B * B;
+    const double L = B * d.voxel_size;
+    int64_t n = 0, na = 0;
+    for (auto it = T->blocks.begin(); it != T->blocks.end();) {
+        double margin = INF;
+        for (int i = 0; i < 3; ++i) {
+            double c = d.origin[i] + (it->first[i] + 0.5) * L;
+            margin = std::min(margin, d.local_half[i] - std::fabs(c - lc[i]));
+        }
+        if (std::fabs(margin) < T->tau_len) {
+            if (amb_keys)
+                for (int k = 0; k < 3; ++k) amb_keys[3 * na + k] = it->first[k];
+            ++na;
+        }
+        if (margin < 0.0) {
+            if (keys) {
+                for (int k = 0; k < 3; ++k) keys[3 * n + k] = it->first[k];
+                for (int v = 0; v < B3; ++v) {
+                    D[n * B3 + v] = it->second.D[v];
+                    W[n * B3 + v] = it->second.W[v];
+                }
+            }
+            ++n;
+            it = T->blocks.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    if (n_amb) *n_amb = na;
+    return n;
+}
+
+// Load blocks (checkpoint resume, swap-in): insert or overwrite each block's voxels.
+void orc_tsdf_load(void* h, int64_t n, const int64_t* keys, const double* D, const double* W) {
+    Tsdf* T = static_cast<Tsdf*>(h);
+    const int B3 = T->d.block_dim * T->d.block_dim * T->d.block_dim;
+    for (int64_t i = 0; i < n; ++i) {
+        Key k = {keys[3 * i], keys[3 * i + 1], keys[3 * i + 2]};
+        auto it = T->blocks.find(k);
+        if (it == T->blocks.end()) it = T->blocks.emplace(k, new_block(B3)).first;
+        for (int v = 0; v < B3; ++v) {
+            it->second.D[v] = D[i * B3 + v];
+            it->second.W[v] = W[i * B3 + v];
+            it->second.amb[v] = 0;
+        }
+        it->second.block_amb = 0;
+    }
+}
+
 // Blocks ever in an ambiguous allocation band (for set comparisons).
 int64_t orc_tsdf_ever_maybe(void* h, int64_t* keys) {
     Tsdf* T = static_cast<Tsdf*>(h);

@@ -76,8 +76,10 @@ struct TsdfDev {
     int* hvals;
     long long slot_mask;
     float2* vox;
-    int4* pool_keys;
-    int* n_alloc;
+    int4* pool_keys;     // (bx, by, bz, 0); w = -1 marks a freed slot
+    int* n_alloc;        // slots handed out so far (freed ones included)
+    int* free_stack;     // freed slots, reused before the pool grows
+    int* free_top;       // entries on the free stack (may run below zero while allocating)
     int pool_cap;
     int* vis;
     int* n_vis;
@@ -102,7 +104,12 @@ __device__ int hash_insert(const TsdfDev& T, int bx, int by, int bz) {
         if (k == EMPTY) {
             unsigned long long prev = atomicCAS(&T.hkeys[h], EMPTY, key);
             if (prev == EMPTY) {
-                int idx = atomicAdd(T.n_alloc, 1);
+                int idx = -1;
+                if (T.free_top) {
+                    int top = atomicSub(T.free_top, 1);
+                    if (top > 0) idx = T.free_stack[top - 1];
+                }
+                if (idx < 0) idx = atomicAdd(T.n_alloc, 1);
                 if (idx >= T.pool_cap) {
                     atomicOr(T.status, DEV_CAPACITY);
                     T.hvals[h] = -2;
@@ -174,6 +181,14 @@ __global__ void alloc_kernel(const __grid_constant__ FrameP F, TsdfDev T, const 
         float Bp = fmaf(s1, dw[i], F.C[i]);
         Dv[i] = Bp - A[i];
         float flo = floorf(fminf(A[i], Bp) / F.block), fhi = floorf(fmaxf(A[i], Bp) / F.block);
+        if (F.gate) {
+            // only blocks whose centre lies in the local map can be allocated:
+            // clip the candidates to the gate's index range (one block of slack;
+            // the exact centre test below decides)
+            flo = fmaxf(flo, floorf((F.lc[i] - F.lh[i]) / F.block - 0.5f) - 1.0f);
+            fhi = fminf(fhi, floorf((F.lc[i] + F.lh[i]) / F.block - 0.5f) + 1.0f);
+            if (flo > fhi) return;
+        }
         // block keys hold 21-bit signed indices; a segment outside that range cannot be stored
         if (!(flo >= -1048575.f && fhi <= 1048575.f)) {
             atomicOr(T.status, DEV_CAPACITY);
@@ -212,6 +227,7 @@ __global__ void visible_kernel(const __grid_constant__ FrameP F, TsdfDev T) {
     float rb = F.block * 0.8660254f * 1.001f + 1e-4f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int4 k = T.pool_keys[i];
+        if (k.w < 0) continue;  // freed slot
         float c[3] = {(k.x + 0.5f) * F.block - F.C[0], (k.y + 0.5f) * F.block - F.C[1],
                       (k.z + 0.5f) * F.block - F.C[2]};
         float Xc[3];
@@ -292,20 +308,132 @@ __global__ void __launch_bounds__(IT) integrate_kernel(const __grid_constant__ F
     }
 }
 
-__global__ void extract_kernel(TsdfDev T, int n, float min_w, int* keys, float* D, float* W) {
-    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+// Output o <- live slot live[o] (or slot o when live is NULL).
+__global__ void extract_kernel(TsdfDev T, const int* live, int n, float min_w, int* keys, float* D, float* W) {
+    for (int o = blockIdx.x; o < n; o += gridDim.x) {
+        const int i = live ? live[o] : o;
         if (threadIdx.x == 0) {
             int4 k = T.pool_keys[i];
-            keys[3 * i] = k.x;
-            keys[3 * i + 1] = k.y;
-            keys[3 * i + 2] = k.z;
+            keys[3 * o] = k.x;
+            keys[3 * o + 1] = k.y;
+            keys[3 * o + 2] = k.z;
         }
         for (int v = threadIdx.x; v < B3; v += blockDim.x) {
             float2 dw = T.vox[(size_t)i * B3 + v];
             bool keep = dw.y >= min_w && dw.y > 0.f;
-            D[(size_t)i * B3 + v] = keep ? dw.x : 0.f;
-            W[(size_t)i * B3 + v] = keep ? dw.y : 0.f;
+            D[(size_t)o * B3 + v] = keep ? dw.x : 0.f;
+            W[(size_t)o * B3 + v] = keep ? dw.y : 0.f;
         }
+    }
+}
+
+// Live slots of the pool in slot order (one CTA of 1024 threads: each thread
+// counts a contiguous range, a CTA-wide scan places the ranges).  live[]
+// receives the slot indices, *n_live their number.
+__global__ void __launch_bounds__(1024) compact_live_kernel(TsdfDev T, int* live, int* n_live) {
+    __shared__ int part[1024];
+    const int n = min(*T.n_alloc, T.pool_cap);
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int lo = min(n, (int)threadIdx.x * per), hi = min(n, lo + per);
+    int c = 0;
+    for (int i = lo; i < hi; ++i) c += T.pool_keys[i].w >= 0;
+    part[threadIdx.x] = c;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {  // inclusive scan
+        int v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int o = part[threadIdx.x] - c;
+    for (int i = lo; i < hi; ++i)
+        if (T.pool_keys[i].w >= 0) live[o++] = i;
+    if (threadIdx.x == blockDim.x - 1) *n_live = part[threadIdx.x];
+}
+
+// Swap-out: live blocks whose centre lies outside the local map are copied
+// to the caller's buffers (up to cap of them), their slots freed and zeroed.
+__global__ void evict_kernel(TsdfDev T, const int* live, const int* n_live, float block, float3 lc, float3 lh,
+                             int cap, int* n_out, int* keys, float* D, float* W) {
+    __shared__ int s_o;
+    const int n = *n_live;
+    for (int e = blockIdx.x; e < n; e += gridDim.x) {
+        const int i = live[e];
+        const int4 k = T.pool_keys[i];
+        const bool out = fabsf((k.x + 0.5f) * block - lc.x) > lh.x || fabsf((k.y + 0.5f) * block - lc.y) > lh.y ||
+                         fabsf((k.z + 0.5f) * block - lc.z) > lh.z;
+        if (!out) continue;  // uniform over the CTA
+        if (threadIdx.x == 0) s_o = atomicAdd(n_out, 1);
+        __syncthreads();
+        const int o = s_o;
+        __syncthreads();
+        if (o >= cap) continue;  // no room: the block stays in the map
+        if (threadIdx.x == 0) {
+            keys[3 * o] = k.x;
+            keys[3 * o + 1] = k.y;
+            keys[3 * o + 2] = k.z;
+            T.pool_keys[i].w = -1;
+        }
+        for (int v = threadIdx.x; v < B3; v += blockDim.x) {
+            float2 dw = T.vox[(size_t)i * B3 + v];
+            D[(size_t)o * B3 + v] = dw.x;
+            W[(size_t)o * B3 + v] = dw.y;
+            T.vox[(size_t)i * B3 + v] = make_float2(0.f, 0.f);
+        }
+    }
+}
+
+// Free stack <- every freed slot below the high-water mark.
+__global__ void free_list_kernel(TsdfDev T) {
+    const int n = min(*T.n_alloc, T.pool_cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (T.pool_keys[i].w < 0) T.free_stack[atomicAdd(T.free_top, 1)] = i;
+}
+
+// Hash table rebuilt from the live slots (after a swap-out).
+__global__ void rehash_kernel(TsdfDev T) {
+    const int n = min(*T.n_alloc, T.pool_cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int4 k = T.pool_keys[i];
+        if (k.w < 0) continue;
+        unsigned long long key = pack_key(k.x, k.y, k.z);
+        long long h = (long long)(hash64(key) & (unsigned long long)T.slot_mask);
+        for (int probe = 0; probe < MAX_PROBE; ++probe) {
+            if (atomicCAS(&T.hkeys[h], EMPTY, key) == EMPTY) {
+                T.hvals[h] = i;
+                break;
+            }
+            h = (h + 1) & T.slot_mask;
+            if (probe == MAX_PROBE - 1) atomicOr(T.status, DEV_TIMEOUT | DEV_CAPACITY);
+        }
+    }
+}
+
+// Pool slot of a key, -1 when absent (bounded probing).
+__device__ int hash_find(const TsdfDev& T, int bx, int by, int bz) {
+    unsigned long long key = pack_key(bx, by, bz);
+    long long h = (long long)(hash64(key) & (unsigned long long)T.slot_mask);
+    for (int probe = 0; probe < MAX_PROBE; ++probe) {
+        unsigned long long k = T.hkeys[h];
+        if (k == key) return T.hvals[h];
+        if (k == EMPTY) return -1;
+        h = (h + 1) & T.slot_mask;
+    }
+    return -1;
+}
+
+// Load: (1) insert the keys, (2) copy each block's voxels into its slot.
+__global__ void load_keys_kernel(TsdfDev T, const int* keys, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        hash_insert(T, keys[3 * i], keys[3 * i + 1], keys[3 * i + 2]);
+}
+
+__global__ void load_voxels_kernel(TsdfDev T, const int* keys, const float* D, const float* W, int n) {
+    for (int e = blockIdx.x; e < n; e += gridDim.x) {
+        const int i = hash_find(T, keys[3 * e], keys[3 * e + 1], keys[3 * e + 2]);
+        if (i < 0) continue;  // no room (capacity already latched)
+        for (int v = threadIdx.x; v < B3; v += blockDim.x)
+            T.vox[(size_t)i * B3 + v] = make_float2(D[(size_t)e * B3 + v], W[(size_t)e * B3 + v]);
     }
 }
 
@@ -331,6 +459,7 @@ struct tsdf_s {
     int sms = 0;
     float4* rays = nullptr;
     double view_angle = 0;
+    int* n_tmp = nullptr;  // [0] live blocks, [1] swapped-out blocks
     StageProfiler prof;
 };
 
@@ -348,6 +477,9 @@ void free_tsdf(tsdf_t* t) {
     cudaFree(t->T.n_vis);
     cudaFree(t->T.status);
     cudaFree(t->T.dmax_bits);
+    cudaFree(t->T.free_stack);
+    cudaFree(t->T.free_top);
+    cudaFree(t->n_tmp);
     cudaFree(t->rays);
     delete t;
 }
@@ -418,6 +550,7 @@ extern "C" int tsdf_create(const ps_tsdf_desc* d, tsdf_t** out) {
     PS_TRY(cudaMalloc(&t->T.status, sizeof(unsigned)));
     PS_TRY(cudaMemset(t->T.status, 0, sizeof(unsigned)));
     PS_TRY(cudaMalloc(&t->T.dmax_bits, sizeof(unsigned)));
+    PS_TRY(cudaMalloc(&t->n_tmp, 2 * sizeof(int)));
     if (dense) {
         int nx = d->dense_dim[0] / 8, ny = d->dense_dim[1] / 8, nz = d->dense_dim[2] / 8;
         dense_keys_kernel<<<(int)((pool + 255) / 256), 256>>>(t->T.pool_keys, nx, ny, nz);
@@ -431,6 +564,9 @@ extern "C" int tsdf_create(const ps_tsdf_desc* d, tsdf_t** out) {
         PS_TRY(cudaMemset(t->T.hvals, 0xFF, sizeof(int) * (size_t)d->hash_slots));
         PS_TRY(cudaMemset(t->T.n_alloc, 0, sizeof(int)));
         t->T.slot_mask = d->hash_slots - 1;
+        PS_TRY(cudaMalloc(&t->T.free_stack, sizeof(int) * (size_t)pool));
+        PS_TRY(cudaMalloc(&t->T.free_top, sizeof(int)));
+        PS_TRY(cudaMemset(t->T.free_top, 0, sizeof(int)));
     }
     PS_TRY(cudaMalloc(&t->rays, sizeof(float4) * (size_t)d->cam.width * d->cam.height));
     t->T.rays = t->rays;
@@ -527,11 +663,23 @@ extern "C" int tsdf_count(tsdf_t* t, int64_t* n_blocks, void* stream) {
     clear_error();
     PS_ARG(t != nullptr && n_blocks != nullptr, "tsdf_count: NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
-    int n = 0;
-    PS_CUDA(cudaMemcpyAsync(&n, t->T.n_alloc, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int n[2] = {0, 0};
+    PS_CUDA(cudaMemcpyAsync(&n[0], t->T.n_alloc, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (t->T.free_top) PS_CUDA(cudaMemcpyAsync(&n[1], t->T.free_top, sizeof(int), cudaMemcpyDeviceToHost, s));
     PS_CUDA(cudaStreamSynchronize(s));
-    *n_blocks = std::min<int64_t>(n, t->T.pool_cap);
+    *n_blocks = std::min<int64_t>(n[0], t->T.pool_cap) - std::max(0, n[1]);
     return read_status(t, s);
+}
+
+// Live slots in slot order into t->T.vis (scratch outside integrate calls); returns their number.
+int live_slots(tsdf_t* t, cudaStream_t s, int64_t* n_live) {
+    compact_live_kernel<<<1, 1024, 0, s>>>(t->T, t->T.vis, t->n_tmp);
+    PS_CUDA(cudaGetLastError());
+    int n = 0;
+    PS_CUDA(cudaMemcpyAsync(&n, t->n_tmp, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PS_CUDA(cudaStreamSynchronize(s));
+    *n_live = n;
+    return PS_OK;
 }
 
 extern "C" int tsdf_extract(tsdf_t* t, float min_weight, int32_t* keys, float* D, float* W, int64_t capacity,
@@ -543,9 +691,18 @@ extern "C" int tsdf_extract(tsdf_t* t, float min_weight, int32_t* keys, float* D
     cudaStream_t s = (cudaStream_t)stream;
     int64_t n = 0;
     int st = tsdf_count(t, &n, stream);
+    int64_t hw = 0;
+    PS_CUDA(cudaMemcpyAsync(&hw, t->T.n_alloc, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PS_CUDA(cudaStreamSynchronize(s));
+    const bool holes = std::min<int64_t>((int)hw, t->T.pool_cap) != n;  // freed slots below the high-water mark
+    if (holes) {
+        int e = live_slots(t, s, &n);
+        if (e) return e;
+    }
     int64_t m = std::min(n, capacity);
     if (m > 0) {
-        extract_kernel<<<(int)std::min<int64_t>(m, 65535), 256, 0, s>>>(t->T, (int)m, min_weight, keys, D, W);
+        extract_kernel<<<(int)std::min<int64_t>(m, 65535), 256, 0, s>>>(t->T, holes ? t->T.vis : nullptr, (int)m,
+                                                                       min_weight, keys, D, W);
         PS_CUDA(cudaGetLastError());
         PS_CUDA(cudaStreamSynchronize(s));
     }
@@ -555,6 +712,65 @@ extern "C" int tsdf_extract(tsdf_t* t, float min_weight, int32_t* keys, float* D
         set_error("tsdf_extract: capacity %lld < %lld blocks", (long long)capacity, (long long)n);
         return PS_ERR_CAPACITY;
     }
+    return PS_OK;
+}
+
+extern "C" int tsdf_swap_out(tsdf_t* t, const double* lc, int32_t* keys, float* D, float* W, int64_t capacity,
+                             int64_t* n_out, void* stream) {
+    clear_error();
+    PS_ARG(t != nullptr && lc != nullptr && n_out != nullptr, "tsdf_swap_out: NULL argument");
+    PS_ARG(!t->dense, "tsdf_swap_out: a dense grid has no local map to leave");
+    const ps_tsdf_desc& d = t->d;
+    PS_ARG(d.local_half[0] > 0 || d.local_half[1] > 0 || d.local_half[2] > 0,
+           "tsdf_swap_out: the map has no local-map extent");
+    PS_ARG(capacity >= 0 && (capacity == 0 || (keys && D && W)), "tsdf_swap_out: bad output buffers");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t n_live = 0;
+    int e = live_slots(t, s, &n_live);
+    if (e) return e;
+    PS_CUDA(cudaMemsetAsync(t->n_tmp + 1, 0, sizeof(int), s));
+    const float block = (float)(8.0 * d.voxel_size);
+    float3 c = make_float3((float)(lc[0] - d.origin[0]), (float)(lc[1] - d.origin[1]), (float)(lc[2] - d.origin[2]));
+    float3 h = make_float3((float)d.local_half[0], (float)d.local_half[1], (float)d.local_half[2]);
+    if (n_live > 0) {
+        evict_kernel<<<(int)std::min<int64_t>(n_live, 65535), 256, 0, s>>>(t->T, t->T.vis, t->n_tmp, block, c, h,
+                                                                          (int)std::min<int64_t>(capacity, 1 << 30),
+                                                                          t->n_tmp + 1, keys, D, W);
+        PS_CUDA(cudaGetLastError());
+    }
+    // free list and hash rebuilt from the surviving blocks
+    PS_CUDA(cudaMemsetAsync(t->T.free_top, 0, sizeof(int), s));
+    free_list_kernel<<<t->sms * 4, 256, 0, s>>>(t->T);
+    PS_CUDA(cudaGetLastError());
+    PS_CUDA(cudaMemsetAsync(t->T.hkeys, 0xFF, sizeof(unsigned long long) * (size_t)d.hash_slots, s));
+    PS_CUDA(cudaMemsetAsync(t->T.hvals, 0xFF, sizeof(int) * (size_t)d.hash_slots, s));
+    rehash_kernel<<<t->sms * 4, 256, 0, s>>>(t->T);
+    PS_CUDA(cudaGetLastError());
+    int n_ev = 0;
+    PS_CUDA(cudaMemcpyAsync(&n_ev, t->n_tmp + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PS_CUDA(cudaStreamSynchronize(s));
+    *n_out = std::min<int64_t>(n_ev, capacity);
+    int st = read_status(t, s);
+    if (st) return st;
+    if (n_ev > capacity) {
+        set_error("tsdf_swap_out: %d blocks left the local map, capacity %lld; the rest stay in the map", n_ev,
+                  (long long)capacity);
+        return PS_ERR_CAPACITY;
+    }
+    return PS_OK;
+}
+
+extern "C" int tsdf_load(tsdf_t* t, const int32_t* keys, const float* D, const float* W, int64_t n, void* stream) {
+    clear_error();
+    PS_ARG(t != nullptr && n >= 0 && (n == 0 || (keys && D && W)), "tsdf_load: bad arguments");
+    PS_ARG(!t->dense, "tsdf_load: a dense grid keeps its blocks; write its voxels instead");
+    PS_ARG(n <= (1ll << 30), "tsdf_load: too many blocks");
+    if (n == 0) return PS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    load_keys_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 65535), 256, 0, s>>>(t->T, keys, (int)n);
+    PS_CUDA(cudaGetLastError());
+    load_voxels_kernel<<<(int)std::min<int64_t>(n, 65535), 256, 0, s>>>(t->T, keys, D, W, (int)n);
+    PS_CUDA(cudaGetLastError());
     return PS_OK;
 }
 

@@ -26,6 +26,7 @@ MAX_SETS, MAX_CAMS, MAX_LEVELS = 4, 4, 2
 EXPORTS = ["psweep_create", "psweep_depth", "psweep_destroy", "tsdf_create", "tsdf_integrate", "tsdf_count",
            "tsdf_extract", "tsdf_status", "tsdf_destroy", "psweep_frame_host", "psweep_profile",
            "psweep_profile_read", "tsdf_profile", "tsdf_profile_read", "tsdf_integrate_dense_static",
+           "tsdf_swap_out", "tsdf_load",
            "ps_last_error", "ps_version"]
 
 
@@ -116,6 +117,8 @@ def load(build_if_missing: bool = True):
     L.psweep_profile_read.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int32)]
     L.tsdf_profile.argtypes = [P, C.c_int32]
     L.tsdf_profile_read.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int32)]
+    L.tsdf_swap_out.argtypes = [P, P, P, P, P, C.c_int64, C.POINTER(C.c_int64), P]
+    L.tsdf_load.argtypes = [P, P, P, P, C.c_int64, P]
     L.tsdf_integrate_dense_static.argtypes = [P, P, P, C.c_double, C.c_double, C.c_double, P,
                                               C.POINTER(ps_camera), C.POINTER(ps_pose), P]
     L.ps_last_error.restype = C.c_char_p
@@ -326,6 +329,25 @@ class Tsdf:
 
     def status(self, stream=None) -> int:
         return load().tsdf_status(self.h, _stream_ptr(stream))
+
+    def swap_out(self, local_center, capacity: int = None, device="cuda", stream=None):
+        """Move the blocks outside the local map out of the map: (keys, D, W) CUDA tensors."""
+        cap = self.count(stream) if capacity is None else int(capacity)
+        keys = torch.empty((max(cap, 1), 3), dtype=torch.int32, device=device)
+        D = torch.empty((max(cap, 1), 512), dtype=torch.float32, device=device)
+        W = torch.empty((max(cap, 1), 512), dtype=torch.float32, device=device)
+        m = C.c_int64()
+        lc = (C.c_double * 3)(*local_center)
+        _check(load().tsdf_swap_out(self.h, lc, keys.data_ptr(), D.data_ptr(), W.data_ptr(), cap, C.byref(m),
+                                    _stream_ptr(stream)))
+        return keys[:m.value], D[:m.value], W[:m.value]
+
+    def load_blocks(self, keys: torch.Tensor, D: torch.Tensor, W: torch.Tensor, stream=None):
+        """Insert or overwrite blocks (checkpoint resume, swap-in)."""
+        n = keys.shape[0]
+        _check(load().tsdf_load(self.h, _dev(keys.contiguous(), torch.int32, "keys"),
+                                _dev(D.contiguous(), torch.float32, "D"), _dev(W.contiguous(), torch.float32, "W"),
+                                n, _stream_ptr(stream)))
 
     def extract(self, min_weight: float = 0.0, device="cuda", stream=None):
         """(keys (n, 3) int32, D (n, 512), W (n, 512)) as CUDA tensors, in pool order."""

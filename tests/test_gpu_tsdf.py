@@ -116,3 +116,74 @@ def test_local_center_required():
     assert e.value.status == P.PS_ERR_ARG
     T.integrate(d, wl.world_to_ref[0], wl.local_center(0))   # empty depth: nothing allocated
     assert T.count() == 0
+
+
+def _sorted(k, D, W):
+    k = k.cpu().numpy() if torch.is_tensor(k) else k
+    D = D.cpu().numpy() if torch.is_tensor(D) else D
+    W = W.cpu().numpy() if torch.is_tensor(W) else W
+    o = np.lexsort((k[:, 2], k[:, 1], k[:, 0]))
+    return k[o], D[o], W[o]
+
+
+def test_swap_out_parity_and_slot_reuse():
+    # a small local map (12 x 3 x 8 m) so that blocks fall behind it within a
+    # few frames; swap-outs on both sides after frames 6 and 10, fusion continues
+    import dataclasses
+    wl = scenes.street(0, n_frames=12, scale=0.25)
+    p = dataclasses.replace(wl.tsdf, local_half=(6.0, 1.5, 4.0), pool_blocks=4096)
+    src = scenes.FrameSource(wl)
+    T = P.Tsdf(p, wl.rig.ref)
+    O = oracle.Tsdf(p)
+    n_swapped = 0
+    for f in range(12):
+        _, rng = src.frame(f, with_range=True)
+        d = _masked(rng, wl.boxes[f])
+        # off the block grid, so that no block centre ties with the box boundary
+        lc = tuple(np.array(wl.local_center(f)) + np.array([0.13, 0.0, 0.27]))
+        T.integrate(torch.from_numpy(d).cuda(), wl.world_to_ref[f], lc)
+        O.integrate(d, wl.rig.ref, wl.world_to_ref[f], lc)
+        if f in (6, 10):
+            gk, gD, gW = _sorted(*T.swap_out(lc))
+            ok, oD, oW, amb = O.swap_out(np.array(lc))
+            amb = set(map(tuple, amb.tolist()))
+            gs, os_ = set(map(tuple, gk.tolist())), set(map(tuple, ok.tolist()))
+            assert len(os_) > 20
+            assert (gs ^ os_) <= amb
+            s = tsdf_compare(ok, oD, oW, np.zeros_like(oD, dtype=bool), gk, gD, gW)
+            assert s["D_abs_max"] <= TSDF_ABS and s["W_mismatch"] == 0, s
+            n_swapped += len(gs)
+    assert T.status() == P.PS_OK
+    k, D, W = T.extract()
+    ok, oD, oW, oamb = O.dump()
+    gset, oset = set(map(tuple, k.cpu().numpy().tolist())), set(map(tuple, ok.tolist()))
+    maybe = set(map(tuple, O.ever_maybe().tolist()))
+    assert gset <= (oset | maybe)
+    s = tsdf_compare(ok, oD, oW, oamb, k.cpu().numpy(), D.cpu().numpy(), W.cpu().numpy())
+    print("swap-out", s, "swapped", n_swapped, "live", len(gset))
+    assert s["n_updated"] > 5000
+    assert s["D_abs_max"] <= TSDF_ABS and s["W_mismatch"] == 0, s
+
+
+def test_checkpoint_and_resume():
+    wl = scenes.street(1, n_frames=4, scale=0.25)
+    src = scenes.FrameSource(wl)
+    frames = []
+    for f in range(4):
+        _, rng = src.frame(f, with_range=True)
+        frames.append(torch.from_numpy(_masked(rng, wl.boxes[f])).cuda())
+    A = P.Tsdf(wl.tsdf, wl.rig.ref)
+    for f in range(3):
+        A.integrate(frames[f], wl.world_to_ref[f], wl.local_center(f))
+    k, D, W = A.extract()
+    B = P.Tsdf(wl.tsdf, wl.rig.ref)                   # resume from the checkpoint
+    B.load_blocks(k, D, W)
+    assert B.status() == P.PS_OK and B.count() == A.count()
+    a = _sorted(*A.extract())
+    b = _sorted(*B.extract())
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    for M in (A, B):                                    # both continue identically
+        M.integrate(frames[3], wl.world_to_ref[3], wl.local_center(3))
+    a = _sorted(*A.extract())
+    b = _sorted(*B.extract())
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))

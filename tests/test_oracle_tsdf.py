@@ -233,3 +233,34 @@ def test_nearest_pixel_lookup():
             assert W[i, v] == 1 and abs(D[i, v] - min(1.0, eta / p.mu)) < 1e-12
             n += 1
     assert n > 1000
+
+
+def test_swap_out_and_load():
+    # blocks whose centre leaves the local map are removed and returned;
+    # loading them back restores the map exactly
+    rng = np.random.default_rng(13)
+    cam = Camera(xi=1.0, fx=20, fy=20, cx=20, cy=20, width=41, height=41)
+    depth = rng.uniform(1.0, 12.0, size=(41, 41)).astype(np.float32)
+    p = _hashed(voxel=0.1, mu=0.5)
+    T = oracle.Tsdf(p)
+    T.integrate(depth, cam, Pose.identity())
+    k0, D0, W0, _ = T.dump()
+    pg = TsdfParams(voxel_size=0.1, mu=0.5, local_half=(2.0, 1.0, 3.0))
+    Tg = oracle.Tsdf(pg)
+    Tg.load(k0, D0, W0)
+    centre = np.array([0.31, -0.17, 5.13])
+    ks, Ds, Ws, amb = Tg.swap_out(centre)
+    kk, DD, WW, _ = Tg.dump()
+    L = 0.8
+    cen = (k0 + 0.5) * L
+    outside = np.any(np.abs(cen - centre) > np.array(pg.local_half), axis=1)
+    assert 0 < outside.sum() < len(k0)
+    assert set(map(tuple, ks)) == set(map(tuple, k0[outside]))
+    assert set(map(tuple, kk)) == set(map(tuple, k0[~outside]))
+    idx = {tuple(k): i for i, k in enumerate(k0)}
+    for i, k in enumerate(ks):
+        assert np.array_equal(Ds[i], D0[idx[tuple(k)]]) and np.array_equal(Ws[i], W0[idx[tuple(k)]])
+    assert len(amb) == 0
+    Tg.load(ks, Ds, Ws)
+    k2, D2, W2, _ = Tg.dump()
+    assert np.array_equal(k2, k0) and np.array_equal(D2, D0) and np.array_equal(W2, W0)
