@@ -55,7 +55,18 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", choices=["street", "ring"], default="street",
+                    help="street: the paper-shaped frame (default); ring: 4 cameras, 256 full-resolution planes, "
+                         "2 cm voxels on a 500 m loop")
+    ap.add_argument("--half", action="store_true", help="FP16 storage of the matching images")
     return ap.parse_args()
+
+
+def workload(args, seed):
+    import scenes
+    if args.config == "ring":
+        return scenes.ring(seed, n_frames=1000)
+    return scenes.street(seed, n_frames=100)
 
 
 def dist_env():
@@ -248,9 +259,9 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     peaks, peaks_src = load_peaks()
 
-    wl = scenes.street(args.seed + rank, n_frames=100)
+    wl = workload(args, args.seed + rank)
     n_total = args.warmup + args.steps
-    nf = min(n_total, 100)
+    nf = min(n_total, 100 if args.config == "street" else 40)
     t_r = time.time()
     frames = render_frames(wl, nf, f"cuda:{local}")
     render_s = time.time() - t_r
@@ -259,7 +270,7 @@ def run_ours(args):
     H, W = wl.rig.ref.height, wl.rig.ref.width
     stream = torch.cuda.current_stream()
 
-    sw = P.Sweep(wl.rig, wl.levels)
+    sw = P.Sweep(wl.rig, wl.levels, image_half=args.half)
     T = P.Tsdf(wl.tsdf, wl.rig.ref)
     depth = torch.empty((H, W), dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
@@ -353,8 +364,11 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl.name, "ref": f"{W}x{H}", "matching_cams": len(wl.rig.cams),
-                   "levels": "320x256 (64 fronto + 32 ground, 7x7) + 640x512 crop (128 fronto, 9x9)",
-                   "tsdf": "8^3 blocks, 0.1 m voxels, mu 0.5 m, 60x3x60 m local map", "frames": nf,
+                   "levels": ("320x256 (64 fronto + 32 ground, 7x7) + 640x512 crop (128 fronto, 9x9)"
+                              if args.config == "street" else "1280x1024 (256 fronto, 9x9)"),
+                   "tsdf": ("8^3 blocks, 0.1 m voxels, mu 0.5 m, 60x3x60 m local map" if args.config == "street"
+                            else "8^3 blocks, 0.02 m voxels, mu 0.1 m, 60x3x60 m local map, 2^23-block pool"),
+                   "image_storage": "fp16" if args.half else "fp32", "frames": nf,
                    "l2": "flushed between steps (256 MB write outside the step events)",
                    "parallelism": f"replicas x{world} (independent sequences)"},
         "sweep": {"value": pix_planes / (depth_ms * 1e-3) / 1e9, "unit": "Gpix·planes/s",
@@ -376,7 +390,7 @@ def run_ours(args):
         "clocks": clk,
         "render_s": render_s,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.config == "street":
         line["cpu_baseline"] = cpu_baseline(wl, frames)
     if rank == 0:
         print(json.dumps(line))

@@ -123,6 +123,7 @@ typedef struct {
     int32_t n_levels;              /* 1 .. PS_MAX_LEVELS: at most one DOWNSAMPLE and one CROP */
     const ps_level* levels;        /* host */
     ps_filter filter;              /* depth map filtering; zero-initialised = off */
+    int32_t image_half;            /* 1: matching images stored as FP16 (arithmetic stays FP32) */
 } ps_sweep_desc;
 
 /* Half-open pixel rectangle [x0, x1) x [y0, y1) in full-resolution

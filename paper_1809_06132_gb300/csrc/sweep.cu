@@ -24,6 +24,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "internal.cuh"
 
 namespace ps {
@@ -53,7 +55,7 @@ struct SetD {
 struct CamJ {
     float R[9], t[3];  // reference -> matching camera
     CamF cam;          // intrinsics at this level
-    const float4* quad;
+    const void* quad;  // float4 quads, or four halves per quad with FP16 storage
 };
 
 struct LevelD {
@@ -78,6 +80,7 @@ struct LevelD {
 
 struct SweepParams {
     int n_levels;
+    int image_half;  // matching quads stored as FP16
     LevelD lv[PS_MAX_LEVELS];
 };
 
@@ -195,7 +198,7 @@ __global__ void ref_level_kernel(const uint8_t* img, int W, int s, int x0, int y
 // Matching image of a level in "quad" layout: entry (x, y) holds the
 // centred intensities at (x, y), (x+1, y), (x, y+1), (x+1, y+1), so one
 // bilinear sample is one 16-byte gather.
-__global__ void quad_level_kernel(const uint8_t* img, int W, int s, int Wl, int Hl, float4* out) {
+__global__ void quad_level_kernel(const uint8_t* img, int W, int s, int Wl, int Hl, void* out, int half) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y;
     if (x >= Wl || y >= Hl) return;
@@ -204,7 +207,13 @@ __global__ void quad_level_kernel(const uint8_t* img, int W, int s, int Wl, int 
     q.y = level_px(img, W, Wl, Hl, s, x + 1, y);
     q.z = level_px(img, W, Wl, Hl, s, x, y + 1);
     q.w = level_px(img, W, Wl, Hl, s, x + 1, y + 1);
-    out[(size_t)y * Wl + x] = q;
+    if (half) {  // FP16 storage: four halves in 8 bytes
+        __half2 a = __floats2half2_rn(q.x, q.y), b = __floats2half2_rn(q.z, q.w);
+        static_cast<uint2*>(out)[(size_t)y * Wl + x] =
+            make_uint2(*reinterpret_cast<unsigned*>(&a), *reinterpret_cast<unsigned*>(&b));
+    } else {
+        static_cast<float4*>(out)[(size_t)y * Wl + x] = q;
+    }
 }
 
 // ------------------------------------------------------------- reference statistics
@@ -240,7 +249,7 @@ struct CamS {
     float R[9], t[3];
     float xi, fx, fy, cx, cy, k1, k2, p1, p2, r2_max, lim, wm1, hm1;
     int width;
-    const float4* quad;
+    const void* quad;
 };
 
 // Bilinear sample of a matching camera at the projection of X_j (camera
@@ -248,7 +257,8 @@ struct CamS {
 // (sphere side, distortion range) or lands outside [0, W-1] x [0, H-1].
 // The gather is clamped into the image and always issued, so the warp does
 // not diverge; a clamp that moved the point marks it outside (NaN compares
-// unequal, so a NaN position is rejected too).
+// unequal, so a NaN position is rejected too).  HALF: quads stored as FP16.
+template <bool HALF>
 __device__ __forceinline__ float warp_sample(const CamS& c, float X, float Y, float Z) {
     float n2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
     float n = n2 * rsqrtf(n2);
@@ -265,7 +275,15 @@ __device__ __forceinline__ float warp_sample(const CamS& c, float X, float Y, fl
     bool ok = (Z > c.lim * n) && (r2 <= c.r2_max) && (uc == u) && (vc == v);
     int x0 = (int)uc, y0 = (int)vc;
     float ax = uc - (float)x0, ay = vc - (float)y0;
-    float4 q = __ldg(c.quad + y0 * c.width + x0);
+    float4 q;
+    if (HALF) {
+        uint2 h = __ldg(static_cast<const uint2*>(c.quad) + y0 * c.width + x0);
+        float2 a = __half22float2(*reinterpret_cast<const __half2*>(&h.x));
+        float2 b = __half22float2(*reinterpret_cast<const __half2*>(&h.y));
+        q = make_float4(a.x, a.y, b.x, b.y);
+    } else {
+        q = __ldg(static_cast<const float4*>(c.quad) + y0 * c.width + x0);
+    }
     float top = fmaf(ax, q.y - q.x, q.x);
     float bot = fmaf(ax, q.w - q.z, q.z);
     float w = fmaf(ay, bot - top, top);
@@ -330,7 +348,7 @@ __device__ void finish_pixel(const LevelD& L, int gx, int gy, float c1, float c2
     if (L.kstar) L.kstar[o] = kb;
 }
 
-template <int RHO>
+template <int RHO, bool HALF>
 __device__ void sweep_tile(const LevelD& L, const CamS* cams, int item, unsigned char* smem_raw, int* s_flag) {
     using G = Geo<RHO>;
     const int tile = item / L.n_chunks, chunk = item - tile * L.n_chunks;
@@ -417,8 +435,8 @@ __device__ void sweep_tile(const LevelD& L, const CamS* cams, int item, unsigned
                     int p = tid + i * NT;
                     if (p < NPOS) {
                         float4 a = Aj[p];
-                        float w0 = warp_sample(C, fmaf(d0, a.x, C.t[0]), fmaf(d0, a.y, C.t[1]), fmaf(d0, a.z, C.t[2]));
-                        float w1 = warp_sample(C, fmaf(d1, a.x, C.t[0]), fmaf(d1, a.y, C.t[1]), fmaf(d1, a.z, C.t[2]));
+                        float w0 = warp_sample<HALF>(C, fmaf(d0, a.x, C.t[0]), fmaf(d0, a.y, C.t[1]), fmaf(d0, a.z, C.t[2]));
+                        float w1 = warp_sample<HALF>(C, fmaf(d1, a.x, C.t[0]), fmaf(d1, a.y, C.t[1]), fmaf(d1, a.z, C.t[2]));
                         bad |= isnan(w0) | isnan(w1);
                         int hy = p / HWL, hx = p - hy * HWL;
                         Ws[hy * WS + hx] = w0;
@@ -619,10 +637,18 @@ __device__ __forceinline__ void run_level(const SweepParams& P, int item, CamS* 
         c.quad = J.quad;
     }
     __syncthreads();
-    switch (L.rho) {
-        case 2: sweep_tile<2>(L, cams, item, smem, s_flag); break;
-        case 3: sweep_tile<3>(L, cams, item, smem, s_flag); break;
-        default: sweep_tile<4>(L, cams, item, smem, s_flag); break;
+    if (P.image_half) {
+        switch (L.rho) {
+            case 2: sweep_tile<2, true>(L, cams, item, smem, s_flag); break;
+            case 3: sweep_tile<3, true>(L, cams, item, smem, s_flag); break;
+            default: sweep_tile<4, true>(L, cams, item, smem, s_flag); break;
+        }
+    } else {
+        switch (L.rho) {
+            case 2: sweep_tile<2, false>(L, cams, item, smem, s_flag); break;
+            case 3: sweep_tile<3, false>(L, cams, item, smem, s_flag); break;
+            default: sweep_tile<4, false>(L, cams, item, smem, s_flag); break;
+        }
     }
 }
 
@@ -793,7 +819,8 @@ struct psweep_s {
     float* partial[PS_MAX_LEVELS] = {};
     int* done[PS_MAX_LEVELS] = {};
     int chunk[PS_MAX_LEVELS] = {};
-    float4* quad[PS_MAX_LEVELS][PS_MAX_CAMS] = {};
+    void* quad[PS_MAX_LEVELS][PS_MAX_CAMS] = {};
+    int image_half = 0;
     int* tile_counter = nullptr;
     int grid = 0;
     int smem_optin = 0;
@@ -925,6 +952,7 @@ extern "C" int psweep_create(const ps_sweep_desc* d, psweep_t** out) {
     h->n_cams = d->n_cams;
     h->n_levels = d->n_levels;
     h->filter = d->filter;
+    h->image_half = d->image_half ? 1 : 0;
     for (int j = 0; j < d->n_cams; ++j) {
         h->cams[j] = d->cams[j];
         h->poses[j] = d->ref_to_cam[j];
@@ -1007,7 +1035,7 @@ extern "C" int psweep_create(const ps_sweep_desc* d, psweep_t** out) {
         }
         for (int j = 0; j < d->n_cams; ++j) {
             const ps_camera& cj = h->lcam[l][j];
-            PS_TRY(cudaMalloc(&h->quad[l][j], sizeof(float4) * (size_t)cj.width * cj.height));
+            PS_TRY(cudaMalloc(&h->quad[l][j], (d->image_half ? sizeof(uint2) : sizeof(float4)) * (size_t)cj.width * cj.height));
         }
         PS_TRY(cudaMalloc(&h->out_depth[l], sizeof(float) * (size_t)W * H));
         PS_TRY(cudaMalloc(&h->out_c1[l], sizeof(float) * (size_t)W * H));
@@ -1058,6 +1086,7 @@ extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_
     SweepParams P;
     std::memset(&P, 0, sizeof(P));
     P.n_levels = h->n_levels;
+    P.image_half = h->image_half;
     h->prof.mark(0, s);
     // heavier level first in the tile order (planes x halo samples per tile)
     int order[PS_MAX_LEVELS] = {0, 1};
@@ -1079,7 +1108,7 @@ extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_
             for (int j = 0; j < h->n_cams; ++j) {
                 const ps_camera& cj = h->lcam[l][j];
                 quad_level_kernel<<<dim3((cj.width + 127) / 128, cj.height), 128, 0, s>>>(
-                    images[1 + j], h->cams[j].width, sf, cj.width, cj.height, h->quad[l][j]);
+                    images[1 + j], h->cams[j].width, sf, cj.width, cj.height, h->quad[l][j], h->image_half);
             }
         } else {
             ref_level_kernel<<<dim3((W + 127) / 128, H), 128, 0, s>>>(images[0], h->ref.width, 0, h->cx0[l],
@@ -1087,7 +1116,7 @@ extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_
             for (int j = 0; j < h->n_cams; ++j) {
                 const ps_camera& cj = h->lcam[l][j];
                 quad_level_kernel<<<dim3((cj.width + 127) / 128, cj.height), 128, 0, s>>>(
-                    images[1 + j], h->cams[j].width, 1, cj.width, cj.height, h->quad[l][j]);
+                    images[1 + j], h->cams[j].width, 1, cj.width, cj.height, h->quad[l][j], h->image_half);
             }
         }
         ref_stats_kernel<<<dim3((W + 127) / 128, H), 128, 0, s>>>(h->ref_img[l], W, H, L.window / 2, h->stats[l]);

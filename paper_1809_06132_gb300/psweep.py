@@ -64,7 +64,7 @@ class ps_filter(C.Structure):
 class ps_sweep_desc(C.Structure):
     _fields_ = [("ref", ps_camera), ("n_cams", C.c_int32), ("cams", C.POINTER(ps_camera)),
                 ("ref_to_cam", C.POINTER(ps_pose)), ("n_levels", C.c_int32), ("levels", C.POINTER(ps_level)),
-                ("filter", ps_filter)]
+                ("filter", ps_filter), ("image_half", C.c_int32)]
 
 
 class ps_box(C.Structure):
@@ -192,7 +192,7 @@ def level_shape(ref, lv):
 class Sweep:
     """Multi-scale fisheye plane sweep of one rig (psweep_create / psweep_depth)."""
 
-    def __init__(self, rig, levels, filters=None):
+    def __init__(self, rig, levels, filters=None, image_half: bool = False):
         L = load()
         self.rig = rig
         self.levels = list(levels)
@@ -200,7 +200,7 @@ class Sweep:
         self._poses = (ps_pose * len(rig.cams))(*[pose(p) for p in rig.ref_to_cam])
         self._levels = (ps_level * len(self.levels))(*[level(lv) for lv in self.levels])
         d = ps_sweep_desc(ref=camera(rig.ref), n_cams=len(rig.cams), cams=self._cams, ref_to_cam=self._poses,
-                          n_levels=len(self.levels), levels=self._levels)
+                          n_levels=len(self.levels), levels=self._levels, image_half=1 if image_half else 0)
         if filters is not None and filters.enable:
             d.filter = ps_filter(enable=1, window=filters.window, alpha_upper=filters.alpha_upper,
                                  alpha_lower=filters.alpha_lower, split_row=filters.split_row,

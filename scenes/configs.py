@@ -297,3 +297,61 @@ class FrameSource:
         for r, p in zip(self.cam_r, wl.rig.ref_to_cam):
             imgs.append(r.render(wl.scene, p.compose(w2r)))
         return imgs, rng
+
+
+# --------------------------------------------------------------------------
+# ring: reference + 3 matching cameras, 1280x1024, 256 full-resolution planes,
+# 2 cm voxels along a closed 500 m loop
+# --------------------------------------------------------------------------
+
+def ring(seed: int = 0, n_frames: int = 1000, scale: float = 1.0, circumference: float = 500.0) -> Workload:
+    """Precision-at-scale workload: a linear rig (matching cameras 0.5 m left,
+    0.5 m and 1.0 m right of the reference), one full-resolution sweep level
+    of 256 fronto-parallel planes with a 9x9 window, and a TSDF of 2 cm voxels
+    (0.1 m truncation, 60 x 3 x 60 m local map, a 32 GB block pool for the
+    whole loop) along a closed circular road driven in n_frames steps."""
+    rng = np.random.default_rng(4000 + seed)
+    ref = _street_camera(rng, scale)
+    cams, poses = [], []
+    for off in (-0.5, 0.5, 1.0):
+        cams.append(_street_camera(rng, scale))
+        yaw, pitch = (math.radians(float(v)) for v in rng.uniform(-1.0, 1.0, size=2))
+        R_cr = rot_xyz(pitch, yaw, 0.0)
+        c = np.array([off, 0.0, 0.0])
+        poses.append(Pose(R_cr.T, -R_cr.T @ c))
+    rig = Rig(ref=ref, cams=cams, ref_to_cam=poses)
+    height = 1.6
+    R = circumference / (2 * math.pi)
+    scene = Scene(seed=seed)
+    scene.planes.append(Plane(n=(0, 1, 0), h=height, e1=(1, 0, 0), e2=(0, 0, 1), texel=0.05, tex_id=1))
+    # buildings on both sides of the road, axis-aligned boxes around the ring centre (R, 0, 0)
+    tex = 10
+    for side, (r0, r1) in ((1, (R + 5.0, R + 12.0)), (-1, (R - 12.0, R - 5.0))):
+        ang = 0.0
+        while ang < 2 * math.pi:
+            rad = float(rng.uniform(r0, r1))
+            size = float(rng.uniform(3.0, 8.0))
+            h = float(rng.uniform(2.0, 9.0))
+            cxw = R - rad * math.cos(ang)
+            czw = rad * math.sin(ang)
+            scene.boxes.append(Box(lo=(cxw - size / 2, height - h, czw - size / 2),
+                                   hi=(cxw + size / 2, height, czw + size / 2), texel=0.05, tex_id=tex))
+            tex += 1
+            ang += (size + float(rng.uniform(1.0, 5.0))) / rad
+    traj = []
+    for f in range(n_frames):
+        th = 2 * math.pi * f / n_frames
+        p = np.array([R - R * math.cos(th), 0.0, R * math.sin(th)])
+        R_cw = np.stack([np.array([math.cos(th), 0.0, -math.sin(th)]), np.array([0.0, 1.0, 0.0]),
+                         np.array([math.sin(th), 0.0, math.cos(th)])], axis=1)   # camera axes in the world
+        traj.append(Pose(R_cw.T, -R_cw.T @ p))
+    levels = [Level(kind=DOWNSAMPLE, factor=1, window=9, sets=[PlaneSet(FRONTO, 256, 1.0, 80.0)])]
+    # the paper's 60 x 3 x 60 m local map bounds what one frame allocates; the
+    # block pool (2^23 blocks of 4 KB, 32 GB) holds the whole loop's map
+    tsdf = TsdfParams(voxel_size=0.02, mu=0.1, hash_slots=1 << 25, pool_blocks=1 << 23,
+                      local_half=(30.0, 1.5, 30.0), local_offset=(0.0, 0.6, 0.0))
+    W, H = ref.width, ref.height
+    brng = np.random.default_rng(5000 + seed)
+    boxes = [random_boxes(brng, W, H, int(brng.integers(1, 4))) for _ in range(n_frames)]
+    name = f"ring-{W}x{H}-4cam-256planes-2cm"
+    return Workload(name, rig, levels, tsdf, scene, traj, boxes, ss=2)
