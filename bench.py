@@ -55,9 +55,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", choices=["street", "ring"], default="street",
+    ap.add_argument("--config", choices=["street", "ring", "batch"], default="street",
                     help="street: the paper-shaped frame (default); ring: 4 cameras, 256 full-resolution planes, "
-                         "2 cm voxels on a 500 m loop")
+                         "2 cm voxels on a 500 m loop; batch: 64 uneven sweeps in one persistent launch")
+    ap.add_argument("--batch-size", type=int, default=64, help="sweeps per batch (--config batch)")
     ap.add_argument("--half", action="store_true", help="FP16 storage of the matching images")
     return ap.parse_args()
 
@@ -399,10 +400,166 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """64 uneven sweeps (image sizes 256x200 .. 1024x768, 32 .. 256 planes, 1 .. 4
+    matching cameras) per step: autotune the batch options, then time the
+    batch as one persistent launch replayed from a CUDA graph, against the
+    same sweeps as 64 single-frame calls.  Per-sweep latency = device clock
+    from the kernel start to the sweep's finished depth map."""
+    import torch
+    import torch.distributed as dist
+
+    import scenes
+    import paper_1809_06132_gb300 as P
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wls = scenes.batch_mix(args.seed + rank, n=args.batch_size)
+    t_r = time.time()
+    images, boxes, host_imgs = [], [], []
+    for wl in wls:
+        imgs, _ = scenes.FrameSource(wl, device=f"cuda:{local}").frame(0)
+        host_imgs.append([torch.from_numpy(np.ascontiguousarray(i.numpy())).pin_memory() for i in imgs])
+        images.append([h.to(dev) for h in host_imgs[-1]])
+        boxes.append(wls[len(boxes)].boxes[0])
+    render_s = time.time() - t_r
+    sweeps = [P.Sweep(wl.rig, wl.levels) for wl in wls]
+    outs = [torch.empty((wl.rig.ref.height, wl.rig.ref.width), dtype=torch.float32, device=dev) for wl in wls]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    pix_planes = sum(wl.pix_planes() for wl in wls)
+    units = sum(wl.pix_planes() * len(wl.rig.cams) for wl in wls)
+
+    # autotuner: tile height x planes per pass x plane chunk
+    cands = [P.batch_opts(tile_h=t, kp=k, plane_chunk=c) for t in (16, 24) for k in (1, 2) for c in (16, 32, 64)]
+    with torch.cuda.stream(stream):
+        best, tune_ms = P.batch_autotune(sweeps, images, cands, boxes=boxes, outs=outs, reps=3, stream=stream)
+    o = cands[best]
+    tuned = dict(tile_h=o.tile_h, kp=o.kp, plane_chunk=o.plane_chunk)
+    o.use_graph = 1
+    B = P.Batch(sweeps, opts=o)
+
+    def timed(fn, k_steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k_steps)]
+        lat = []
+        for k in range(k_steps):
+            flush.zero_()
+            torch.cuda.current_stream().synchronize()
+            ev[k][0].record(stream)
+            fn()
+            ev[k][1].record(stream)
+            stream.synchronize()
+            if fn is run_batch_once:
+                lat.append(B.timing()[0])
+        return [a.elapsed_time(b) for a, b in ev], lat
+
+    def run_batch_once():
+        B.run(images, boxes=boxes, outs=outs, stream=stream)
+
+    def run_singles():
+        for sw, im, bx, out in zip(sweeps, images, boxes, outs):
+            sw.depth(im, boxes=bx, out=out, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            run_batch_once()
+        stream.synchronize()
+        assert B.status() == P.PS_OK
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.3)
+        if world > 1:
+            dist.barrier()
+        t0 = time.time()
+        ms, lat = timed(run_batch_once, args.steps)
+        t1 = time.time()
+        for _ in range(args.warmup):
+            run_singles()
+        ms_single, _ = timed(run_singles, max(3, args.steps // 4))
+        # the same batch without the graph (four API calls per run)
+        Bg = P.Batch(sweeps, opts=P.batch_opts(tile_h=o.tile_h, kp=o.kp, plane_chunk=o.plane_chunk))
+        for _ in range(2):
+            Bg.run(images, boxes=boxes, outs=outs, stream=stream)
+        ms_nograph = []
+        for k in range(max(3, args.steps // 4)):
+            flush.zero_()
+            stream.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            Bg.run(images, boxes=boxes, outs=outs, stream=stream)
+            b.record(stream)
+            stream.synchronize()
+            ms_nograph.append(a.elapsed_time(b))
+        # end to end: pinned host images in, every depth map out, per step
+        host_out = [torch.empty(o_.shape, dtype=torch.float32).pin_memory() for o_ in outs]
+        e2e = []
+        for k in range(max(3, args.steps // 4)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            ts = time.perf_counter()
+            for hs, ds in zip(host_imgs, images):
+                for h_, d_ in zip(hs, ds):
+                    d_.copy_(h_, non_blocking=True)
+            B.run(images, boxes=boxes, outs=outs, stream=stream)
+            for d_, h_ in zip(outs, host_out):
+                h_.copy_(d_, non_blocking=True)
+            stream.synchronize()
+            e2e.append(time.perf_counter() - ts)
+    clocks.stop()
+    clk = clocks.summary(t0, t1)
+    if not clk.get("samples"):
+        clk = clocks.summary()
+    batch_ms = statistics.median(ms)
+    if world > 1:
+        t = torch.tensor([batch_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        batch_ms = float(t.item())
+    all_lat = sorted(x for step in lat for x in step)
+    pct = lambda q: all_lat[min(len(all_lat) - 1, int(q * len(all_lat)))]  # noqa: E731
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak_tflops = n_sm * 128 * 2 * float(sm_max) * 1e6 / 1e12
+    achieved = units * FLOP_PER_UNIT / (batch_ms * 1e-3) / 1e12
+    h2d = sum(int(h.numel()) for hs in host_imgs for h in hs)
+    d2h = sum(4 * int(o_.numel()) for o_ in outs)
+    line = {
+        "metric": "batched plane-sweep Gpix·planes/s (uneven sweeps, one persistent launch)",
+        "value": world * pix_planes / (batch_ms * 1e-3) / 1e9, "unit": "Gpix·planes/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch-mix-{len(wls)}", "sizes": "256x200 / 320x256 / 640x512 / 1024x768",
+                   "planes": "32 / 64 / 128 / 256 fronto, 7x7", "matching_cams": "1-4",
+                   "pix_planes_per_batch": pix_planes, "tuned": tuned, "graph": True,
+                   "l2": "flushed between steps (256 MB write outside the step events)"},
+        "latency_ms": {"p50": pct(0.5), "p99": pct(0.99), "max": all_lat[-1], "span_median": batch_ms,
+                       "source": "device global timer, kernel start to each sweep's finished depth map"},
+        "compare": {"singles_ms": statistics.median(ms_single), "batch_no_graph_ms": statistics.median(ms_nograph),
+                    "speedup_vs_singles": statistics.median(ms_single) / batch_ms},
+        "autotune": [{"tile_h": c.tile_h, "kp": c.kp, "plane_chunk": c.plane_chunk, "ms": m}
+                     for c, m in zip(cands, tune_ms)],
+        "roofline": {"kernel": "batch_kernel", "bound": "alu", "achieved": achieved, "peak": peak_tflops,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                     "flop_per_unit": FLOP_PER_UNIT, "units_per_launch": units},
+        "e2e": {"value": world * pix_planes / statistics.median(e2e) / 1e9, "unit": "Gpix·planes/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps, "clocks": clk, "render_s": render_s,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 

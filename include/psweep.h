@@ -309,6 +309,88 @@ int tsdf_integrate_dense_static(float* voxels, const int32_t* dims, const double
                                 double mu, double w_max, const float* depth, const ps_camera* cam,
                                 const ps_pose* world_to_cam, void* stream);
 
+/* ---------------------------------------------------------------------
+ * Batched sweeps.  The paper computes one depth map per synchronised frame
+ * of one rig; a batch computes the depth maps of many sweep handles (other
+ * rigs, image sizes, plane counts, camera counts, levels and filters) with
+ * the same results as psweep_depth on each, in ONE persistent kernel
+ * launch.  Every step of psweep_depth (level images, reference statistics,
+ * the sweep's tile x plane-chunk work items, merge, filters, boxes) is a
+ * work item of that kernel, taken from a device queue built at
+ * psbatch_create.  An item that needs other items' results waits for them
+ * on the GPU with a bounded spin; the queue order puts every item after
+ * the items it needs, so the waits end, and a wait longer than its limit
+ * (wait_limit_ms) gives up, skips the rest of the batch and is reported as
+ * PS_ERR_TIMEOUT by psbatch_status.  With use_graph the per-run launch sequence (one
+ * copy of the run's pointers and boxes, two memsets, the kernel) is
+ * captured into a CUDA graph on the first run and replayed afterwards.
+ *
+ * A batch uses the level buffers of its sweep handles: while a batch may
+ * run, do not run psweep_depth on its handles concurrently, and destroy the
+ * batch before its handles.  Every handle may appear once. */
+typedef struct psbatch_s psbatch_t;
+
+#define PS_BATCH_SHORTEST_FIRST 0 /* queue sweeps by ascending work: lowest mean latency */
+#define PS_BATCH_GIVEN_ORDER 1    /* queue sweeps in the order given */
+
+typedef struct {
+    int32_t tile_h;       /* output rows per tile: 16 or 24 (0 = 24); tiles are 64 columns wide */
+    int32_t kp;           /* planes warped per camera before their window sums: 1 or 2 (0 = 2) */
+    int32_t plane_chunk;  /* most planes per sweep work item, 1..4096 (0 = 32) */
+    int32_t order;        /* PS_BATCH_SHORTEST_FIRST or PS_BATCH_GIVEN_ORDER */
+    int32_t use_graph;    /* non-zero: replay the run as a CUDA graph (needs a non-NULL stream) */
+    int32_t grid;         /* persistent CTAs (0 = one per SM; at most one per SM) */
+    int32_t wait_limit_ms;     /* time limit of one dependency wait, 1..60000 (0 = 2000) */
+    int32_t drill_unmet_wait;  /* failure drill, for tests of the error path only: non-zero makes
+                                  every merge item wait for one tile more than its sweep has, so
+                                  that the first such wait runs out after wait_limit_ms, the rest
+                                  of the batch is skipped and psbatch_status reports
+                                  PS_ERR_TIMEOUT with the context still usable */
+} ps_batch_opts;
+
+/* Build the queue and device tables for sweeps[0 .. n) (host array of
+ * handles, 1 <= n <= 4096).  opts may be NULL (defaults).  Allocates; the
+ * only batch call that does. */
+int psbatch_create(psweep_t* const* sweeps, int32_t n, const ps_batch_opts* opts, psbatch_t** out);
+
+/* Depth maps of every sweep of the batch, each as psweep_depth would give it.
+ *   images     host array: for each sweep in turn, 1 + n_cams device image
+ *              pointers as for psweep_depth (concatenated).
+ *   boxes      host array of every sweep's boxes, concatenated (may be NULL
+ *              when no sweep has boxes); n_boxes host int32[n] (NULL = none),
+ *              each at most 256.
+ *   depth_out  host array of n device float32 maps (H x W of each sweep's
+ *              reference camera).
+ * Asynchronous on `stream`; serialise runs of one batch on one stream.
+ * Allocates nothing (the first graph run instantiates the graph). */
+int psbatch_run(psbatch_t* b, const uint8_t* const* images, const ps_box* boxes, const int32_t* n_boxes,
+                float* const* depth_out, void* stream);
+
+/* Synchronises with the last run and reads its device clock stamps:
+ * done_ms host double[n] (may be NULL): time from the start of the kernel to
+ * the completion of each sweep's depth map; *span_ms (may be NULL): the
+ * same for the last sweep.  PS_ERR_TIMEOUT if the run gave up. */
+int psbatch_timing(psbatch_t* b, double* done_ms, double* span_ms);
+
+/* Synchronises with the last run: PS_OK or PS_ERR_TIMEOUT. */
+int psbatch_status(psbatch_t* b);
+
+/* Work items of the batch's queue by kind (host int32[6]: reference rows,
+ * quad rows, statistics rows, sweep items, merge rows, continuity rows). */
+int psbatch_queue_stats(psbatch_t* b, int32_t* counts);
+
+void psbatch_destroy(psbatch_t* b);
+
+/* Autotuner: for each of n_cand candidate options, build a batch of the
+ * given sweeps, run it once untimed and `reps` times timed (CUDA events on
+ * `stream`, a synchronise around each), and write the median milliseconds to
+ * ms_out[i] (host double[n_cand]).  *best receives the index of the fastest
+ * candidate.  The inputs are those of psbatch_run; depth_out is written.
+ * Allocates and synchronises: call it outside timed regions. */
+int psbatch_autotune(psweep_t* const* sweeps, int32_t n, const uint8_t* const* images, const ps_box* boxes,
+                     const int32_t* n_boxes, float* const* depth_out, const ps_batch_opts* candidates,
+                     int32_t n_cand, int32_t reps, int32_t* best, double* ms_out, void* stream);
+
 /* Message for the calling thread's last non-zero status ("" if none). */
 const char* ps_last_error(void);
 

@@ -1,6 +1,6 @@
 """In-tree build of libpsweep.so for sm_103a (nvcc, no cmake).
 
-The three translation units compile in parallel; the shared library links
+The translation units compile in parallel; the shared library links
 the CUDA runtime statically so that it loads next to any PyTorch build.
 """
 from __future__ import annotations
@@ -14,8 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpsweep.so")
-SOURCES = ["common.cu", "sweep.cu", "tsdf.cu"]
-HEADERS = ["internal.cuh"]
+SOURCES = ["common.cu", "sweep.cu", "tsdf.cu", "batch.cu", "batch_k16.cu", "batch_k24.cu"]
+HEADERS = ["internal.cuh", "sweep_dev.cuh", "batch_dev.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 

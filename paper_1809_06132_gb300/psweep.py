@@ -26,7 +26,8 @@ MAX_SETS, MAX_CAMS, MAX_LEVELS = 4, 4, 2
 EXPORTS = ["psweep_create", "psweep_depth", "psweep_destroy", "tsdf_create", "tsdf_integrate", "tsdf_count",
            "tsdf_extract", "tsdf_status", "tsdf_destroy", "psweep_frame_host", "psweep_profile",
            "psweep_profile_read", "tsdf_profile", "tsdf_profile_read", "tsdf_integrate_dense_static",
-           "tsdf_swap_out", "tsdf_load",
+           "tsdf_swap_out", "tsdf_load", "psbatch_create", "psbatch_run", "psbatch_timing", "psbatch_status",
+           "psbatch_queue_stats", "psbatch_destroy", "psbatch_autotune",
            "ps_last_error", "ps_version"]
 
 
@@ -76,6 +77,11 @@ class ps_level_out(C.Structure):
                 ("plane_idx", C.c_void_p)]
 
 
+class ps_batch_opts(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in ("tile_h", "kp", "plane_chunk", "order", "use_graph", "grid",
+                                         "wait_limit_ms", "drill_unmet_wait")]
+
+
 class ps_tsdf_desc(C.Structure):
     _fields_ = [("cam", ps_camera), ("voxel_size", C.c_double), ("mu", C.c_double), ("w_max", C.c_double),
                 ("block_dim", C.c_int32), ("dense_dim", C.c_int32 * 3), ("origin", C.c_double * 3),
@@ -121,6 +127,15 @@ def load(build_if_missing: bool = True):
     L.tsdf_load.argtypes = [P, P, P, P, C.c_int64, P]
     L.tsdf_integrate_dense_static.argtypes = [P, P, P, C.c_double, C.c_double, C.c_double, P,
                                               C.POINTER(ps_camera), C.POINTER(ps_pose), P]
+    L.psbatch_create.argtypes = [P, C.c_int32, C.POINTER(ps_batch_opts), C.POINTER(C.c_void_p)]
+    L.psbatch_run.argtypes = [P, P, P, P, P, P]
+    L.psbatch_timing.argtypes = [P, P, P]
+    L.psbatch_status.argtypes = [P]
+    L.psbatch_queue_stats.argtypes = [P, P]
+    L.psbatch_destroy.argtypes = [P]
+    L.psbatch_destroy.restype = None
+    L.psbatch_autotune.argtypes = [P, C.c_int32, P, P, P, P, C.POINTER(ps_batch_opts), C.c_int32, C.c_int32,
+                                   C.POINTER(C.c_int32), P, P]
     L.ps_last_error.restype = C.c_char_p
     L.ps_version.restype = C.c_char_p
     _lib = L
@@ -277,6 +292,101 @@ class Sweep:
         _check(load().psweep_frame_host(self.h, tsdf.h if tsdf is not None else None, ptrs, bx, nb,
                                         C.byref(pz) if pz is not None else None, lc, dptr, _stream_ptr(stream)))
         return depth_out
+
+
+BATCH_SHORTEST_FIRST, BATCH_GIVEN_ORDER = 0, 1
+QUEUE_KINDS = ("ref", "quad", "stats", "sweep", "merge", "continuity")
+
+
+def batch_opts(tile_h: int = 24, kp: int = 2, plane_chunk: int = 32, order: int = BATCH_SHORTEST_FIRST,
+               use_graph: bool = False, grid: int = 0, wait_limit_ms: int = 2000,
+               drill_unmet_wait: bool = False) -> ps_batch_opts:
+    return ps_batch_opts(int(tile_h), int(kp), int(plane_chunk), int(order), 1 if use_graph else 0, int(grid),
+                         int(wait_limit_ms), 1 if drill_unmet_wait else 0)
+
+
+class _BatchArgs:
+    """C arrays of one batch run: images, boxes and outputs of every sweep."""
+
+    def __init__(self, sweeps, images, boxes, outs):
+        if len(images) != len(sweeps) or len(outs) != len(sweeps):
+            raise ValueError("one image list and one output per sweep")
+        flat = []
+        for i, (sw, ims) in enumerate(zip(sweeps, images)):
+            if len(ims) != 1 + len(sw.rig.cams):
+                raise ValueError(f"sweep {i}: expected {1 + len(sw.rig.cams)} images")
+            flat += [_dev(im, torch.uint8, f"images[{i}]") for im in ims]
+        self.images = (C.c_void_p * len(flat))(*flat)
+        boxes = boxes if boxes is not None else [None] * len(sweeps)
+        allb = [np.zeros((0, 4), np.int32) if b is None else np.ascontiguousarray(b, dtype=np.int32).reshape(-1, 4)
+                for b in boxes]
+        self.n_boxes = (C.c_int32 * len(sweeps))(*[len(b) for b in allb])
+        cat = np.concatenate(allb, axis=0) if allb else np.zeros((0, 4), np.int32)
+        self.boxes, _ = boxes_array(cat)
+        self.outs = (C.c_void_p * len(sweeps))(*[_dev(o, torch.float32, f"out[{i}]") for i, o in enumerate(outs)])
+
+
+class Batch:
+    """Depth maps of many sweeps in one persistent launch (psbatch_*)."""
+
+    def __init__(self, sweeps: Sequence[Sweep], opts: Optional[ps_batch_opts] = None, **kw):
+        L = load()
+        self.sweeps = list(sweeps)
+        self.opts = opts if opts is not None else batch_opts(**kw)
+        hs = (C.c_void_p * len(self.sweeps))(*[s.h for s in self.sweeps])
+        h = C.c_void_p()
+        _check(L.psbatch_create(hs, len(self.sweeps), C.byref(self.opts), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().psbatch_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def alloc_outputs(self, device="cuda"):
+        return [torch.empty((s.rig.ref.height, s.rig.ref.width), dtype=torch.float32, device=device)
+                for s in self.sweeps]
+
+    def run(self, images, boxes=None, outs=None, stream=None):
+        """images: per sweep a list [ref, cam_1, ...] of uint8 CUDA tensors; boxes: per sweep (n, 4) or None."""
+        if outs is None:
+            outs = self.alloc_outputs(images[0][0].device)
+        a = _BatchArgs(self.sweeps, images, boxes, outs)
+        _check(load().psbatch_run(self.h, a.images, a.boxes, a.n_boxes, a.outs, _stream_ptr(stream)))
+        return outs
+
+    def timing(self):
+        """(per-sweep ms from kernel start to its depth map, ms to the last one) of the last run."""
+        done = (C.c_double * len(self.sweeps))()
+        span = C.c_double()
+        _check(load().psbatch_timing(self.h, done, C.byref(span)))
+        return list(done), span.value
+
+    def status(self) -> int:
+        return load().psbatch_status(self.h)
+
+    def queue_stats(self):
+        c = (C.c_int32 * 6)()
+        _check(load().psbatch_queue_stats(self.h, c))
+        return dict(zip(QUEUE_KINDS, list(c)))
+
+
+def batch_autotune(sweeps: Sequence[Sweep], images, candidates: Sequence[ps_batch_opts], boxes=None, outs=None,
+                   reps: int = 3, stream=None):
+    """Time every candidate option set on these inputs; (best index, median ms per candidate)."""
+    if outs is None:
+        outs = [torch.empty((s.rig.ref.height, s.rig.ref.width), dtype=torch.float32, device="cuda")
+                for s in sweeps]
+    a = _BatchArgs(sweeps, images, boxes, outs)
+    hs = (C.c_void_p * len(sweeps))(*[s.h for s in sweeps])
+    cand = (ps_batch_opts * len(candidates))(*candidates)
+    best = C.c_int32()
+    ms = (C.c_double * len(candidates))()
+    _check(load().psbatch_autotune(hs, len(sweeps), a.images, a.boxes, a.n_boxes, a.outs, cand, len(candidates),
+                                   int(reps), C.byref(best), ms, _stream_ptr(stream)))
+    return best.value, list(ms)
 
 
 class Tsdf:

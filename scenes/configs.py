@@ -23,6 +23,7 @@ intrinsics, rays) by itself.
 """
 from __future__ import annotations
 
+import dataclasses
 import math
 from dataclasses import dataclass, field
 from typing import List, Optional, Tuple
@@ -211,19 +212,9 @@ def _street_camera(rng, scale: float, r2_max: float = 2.5) -> Camera:
                   k1=k1, k2=k2, p1=p1, p2=p2, r2_max=r2_max)
 
 
-def street(seed: int = 0, n_frames: int = 100, scale: float = 1.0) -> Workload:
-    rng = np.random.default_rng(2000 + seed)
-    ref = _street_camera(rng, scale)
-    cams, poses = [], []
-    for side in (-1.0, 1.0):
-        cams.append(_street_camera(rng, scale))
-        yaw, pitch = (math.radians(float(v)) for v in rng.uniform(-1.0, 1.0, size=2))
-        R_cr = rot_xyz(pitch, yaw, 0.0)                 # camera axes in the reference frame
-        c = np.array([0.5 * side, 0.0, 0.0])            # camera centre in the reference frame
-        poses.append(Pose(R_cr.T, -R_cr.T @ c))
-    rig = Rig(ref=ref, cams=cams, ref_to_cam=poses)
-
-    height = 1.6
+def _street_scene(rng, seed: int, height: float) -> Scene:
+    """Ground plane, building fronts along both sides of a straight street and
+    parked cars by the kerbs (axis-aligned textured boxes)."""
     scene = Scene(seed=seed)
     scene.planes.append(Plane(n=(0, 1, 0), h=height, e1=(1, 0, 0), e2=(0, 0, 1),
                               texel=0.05, tex_id=1))
@@ -251,6 +242,23 @@ def street(seed: int = 0, n_frames: int = 100, scale: float = 1.0) -> Workload:
                                    texel=0.04, tex_id=tex))
             tex += 1
             z += zl + float(rng.uniform(6.0, 30.0))
+    return scene
+
+
+def street(seed: int = 0, n_frames: int = 100, scale: float = 1.0) -> Workload:
+    rng = np.random.default_rng(2000 + seed)
+    ref = _street_camera(rng, scale)
+    cams, poses = [], []
+    for side in (-1.0, 1.0):
+        cams.append(_street_camera(rng, scale))
+        yaw, pitch = (math.radians(float(v)) for v in rng.uniform(-1.0, 1.0, size=2))
+        R_cr = rot_xyz(pitch, yaw, 0.0)                 # camera axes in the reference frame
+        c = np.array([0.5 * side, 0.0, 0.0])            # camera centre in the reference frame
+        poses.append(Pose(R_cr.T, -R_cr.T @ c))
+    rig = Rig(ref=ref, cams=cams, ref_to_cam=poses)
+
+    height = 1.6
+    scene = _street_scene(rng, seed, height)
     W, H = ref.width, ref.height
     s = 4 if scale >= 1.0 else 2
     crop_w, crop_h = int(round(640 * scale)), int(round(512 * scale))
@@ -355,3 +363,52 @@ def ring(seed: int = 0, n_frames: int = 1000, scale: float = 1.0, circumference:
     boxes = [random_boxes(brng, W, H, int(brng.integers(1, 4))) for _ in range(n_frames)]
     name = f"ring-{W}x{H}-4cam-256planes-2cm"
     return Workload(name, rig, levels, tsdf, scene, traj, boxes, ss=2)
+
+
+# --------------------------------------------------------------------------
+# batch mix: many independent single-frame sweeps of uneven size
+# --------------------------------------------------------------------------
+
+BATCH_SIZES = ((256, 200), (320, 256), (640, 512), (1024, 768))
+BATCH_PLANES = (32, 64, 128, 256)
+
+
+def batch_mix(seed: int = 0, n: int = 64, sizes=BATCH_SIZES, planes=BATCH_PLANES, max_cams: int = 4,
+              ss: int = 1) -> List[Workload]:
+    """n one-frame street workloads whose image size, plane count and number
+    of matching cameras (1 .. max_cams) are drawn per sweep: each has one
+    full-resolution level of fronto-parallel planes on [0.5, 30] m with a 7x7
+    window and 0-3 boxes.  Matching cameras sit 0.3-1.0 m left or right of
+    the reference with small yaw and pitch."""
+    rng = np.random.default_rng(6000 + seed)
+    out = []
+    for i in range(n):
+        W, H = sizes[int(rng.integers(len(sizes)))]
+        n_planes = int(planes[int(rng.integers(len(planes)))])
+        n_cams = int(rng.integers(1, max_cams + 1))
+        scale = W / 1280.0
+
+        def cam():
+            c = _street_camera(rng, scale)
+            return dataclasses.replace(c, width=W, height=H, cx=W / 2.0, cy=H / 2.0)
+
+        ref = cam()
+        cams, poses = [], []
+        for j in range(n_cams):
+            cams.append(cam())
+            side = -1.0 if j % 2 == 0 else 1.0
+            off = side * float(rng.uniform(0.3, 1.0))
+            yaw, pitch = (math.radians(float(v)) for v in rng.uniform(-1.0, 1.0, size=2))
+            R_cr = rot_xyz(pitch, yaw, 0.0)
+            c = np.array([off, 0.0, 0.0])
+            poses.append(Pose(R_cr.T, -R_cr.T @ c))
+        rig = Rig(ref=ref, cams=cams, ref_to_cam=poses)
+        height = 1.6
+        scene = _street_scene(rng, seed * 1000 + i, height)
+        levels = [Level(kind=DOWNSAMPLE, factor=1, window=7, sets=[PlaneSet(FRONTO, n_planes, 0.5, 30.0)])]
+        tsdf = TsdfParams(voxel_size=0.1, mu=0.5, local_half=(30.0, 1.5, 30.0), local_offset=(0.0, 0.6, 0.0))
+        traj = [Pose(np.eye(3), np.array([0.0, 0.0, -float(rng.uniform(0.0, 100.0))]))]
+        boxes = [random_boxes(rng, W, H, int(rng.integers(0, 4)))]
+        name = f"mix{i}-{W}x{H}-{1 + n_cams}cam-{n_planes}planes"
+        out.append(Workload(name, rig, levels, tsdf, scene, traj, boxes, ss=ss))
+    return out

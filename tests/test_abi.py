@@ -74,3 +74,27 @@ def test_argument_errors_without_gpu():
     assert L.tsdf_create(C.byref(td), C.byref(h)) == P.PS_ERR_ARG
     assert L.psweep_depth(None, None, None, 0, None, None, None) == P.PS_ERR_ARG
     assert L.tsdf_integrate(None, None, None, None, None) == P.PS_ERR_ARG
+
+
+def test_batch_argument_errors_without_gpu():
+    L = P.load()
+    h = C.c_void_p()
+    assert C.sizeof(B.ps_batch_opts) == 8 * 4
+    assert L.psbatch_create(None, 0, None, C.byref(h)) == P.PS_ERR_ARG
+    # options are checked before any handle is used (the handles below are never dereferenced)
+    fake = (C.c_void_p * 2)(0x1000, 0x2000)
+    for bad in (dict(tile_h=20), dict(kp=3), dict(plane_chunk=-1), dict(order=5), dict(grid=-2),
+                dict(wait_limit_ms=100000)):
+        o = P.batch_opts(**bad)
+        assert L.psbatch_create(fake, 2, C.byref(o), C.byref(h)) == P.PS_ERR_ARG, bad
+        assert h.value is None
+    same = (C.c_void_p * 2)(0x1000, 0x1000)
+    assert L.psbatch_create(same, 2, None, C.byref(h)) == P.PS_ERR_ARG
+    assert b"twice" in L.ps_last_error()
+    assert L.psbatch_run(None, None, None, None, None, None) == P.PS_ERR_ARG
+    assert L.psbatch_timing(None, None, None) == P.PS_ERR_ARG
+    assert L.psbatch_status(None) == P.PS_ERR_ARG
+    assert L.psbatch_queue_stats(None, None) == P.PS_ERR_ARG
+    best = C.c_int32()
+    ms = (C.c_double * 1)()
+    assert L.psbatch_autotune(None, 0, None, None, None, None, None, 0, 1, C.byref(best), ms, None) == P.PS_ERR_ARG
