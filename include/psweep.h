@@ -261,6 +261,31 @@ int psweep_frame_host(psweep_t* h, tsdf_t* t, const uint8_t* const* host_images,
                       int32_t n_boxes, const ps_pose* world_to_ref, const double* local_center,
                       float* host_depth_out, void* stream);
 
+/* Frame pipeline.  The paper ran depth estimation and fusion on separate
+ * computers at the same time, each on a different frame (Sec. IV-A).  On
+ * one GPU the same overlap comes from CUDA streams: frames from host memory
+ * go through a copy-in stream (host images -> pinned staging -> device), a
+ * sweep stream (psweep_depth) and a fuse stream (tsdf_integrate, then the
+ * depth map back to pinned staging), with two frames in flight, so the
+ * sweep of frame n + 1 and both copies overlap the fusion of frame n.
+ * Every frame gets exactly what psweep_frame_host gives it.
+ *   ps_pipe_create  t may be NULL (no fusion); allocates two sets of device
+ *                   and pinned staging buffers, three streams, six events.
+ *   ps_pipe_push    enqueues one frame (arguments as psweep_frame_host) and
+ *                   returns; it first waits for the frame pushed two calls
+ *                   earlier, whose depth map is then copied to that call's
+ *                   host_depth_out (host float32 H x W, may be NULL).  The
+ *                   host images may be reused when the call returns.
+ *   ps_pipe_flush   waits for every pushed frame and delivers its depth map.
+ * While frames are in flight, do not use the pipeline's sweep or TSDF
+ * handle elsewhere; flush first. */
+typedef struct ps_pipe_s ps_pipe_t;
+int ps_pipe_create(psweep_t* h, tsdf_t* t, ps_pipe_t** out);
+int ps_pipe_push(ps_pipe_t* p, const uint8_t* const* host_images, const ps_box* boxes, int32_t n_boxes,
+                 const ps_pose* world_to_ref, const double* local_center, float* host_depth_out);
+int ps_pipe_flush(ps_pipe_t* p);
+void ps_pipe_destroy(ps_pipe_t* p);
+
 /* Stage timing for measurement tools.  psweep_profile(h, capacity) with
  * capacity > 0 creates 2 x stages x capacity CUDA events (this allocates:
  * call it outside timed or captured regions) and makes the next `capacity`

@@ -27,7 +27,8 @@ EXPORTS = ["psweep_create", "psweep_depth", "psweep_destroy", "tsdf_create", "ts
            "tsdf_extract", "tsdf_status", "tsdf_destroy", "psweep_frame_host", "psweep_profile",
            "psweep_profile_read", "tsdf_profile", "tsdf_profile_read", "tsdf_integrate_dense_static",
            "tsdf_swap_out", "tsdf_load", "psbatch_create", "psbatch_run", "psbatch_timing", "psbatch_status",
-           "psbatch_queue_stats", "psbatch_destroy", "psbatch_autotune",
+           "psbatch_queue_stats", "psbatch_destroy", "psbatch_autotune", "ps_pipe_create", "ps_pipe_push",
+           "ps_pipe_flush", "ps_pipe_destroy",
            "ps_last_error", "ps_version"]
 
 
@@ -136,6 +137,11 @@ def load(build_if_missing: bool = True):
     L.psbatch_destroy.restype = None
     L.psbatch_autotune.argtypes = [P, C.c_int32, P, P, P, P, C.POINTER(ps_batch_opts), C.c_int32, C.c_int32,
                                    C.POINTER(C.c_int32), P, P]
+    L.ps_pipe_create.argtypes = [P, P, C.POINTER(C.c_void_p)]
+    L.ps_pipe_push.argtypes = [P, P, P, C.c_int32, C.POINTER(ps_pose), P, P]
+    L.ps_pipe_flush.argtypes = [P]
+    L.ps_pipe_destroy.argtypes = [P]
+    L.ps_pipe_destroy.restype = None
     L.ps_last_error.restype = C.c_char_p
     L.ps_version.restype = C.c_char_p
     _lib = L
@@ -292,6 +298,48 @@ class Sweep:
         _check(load().psweep_frame_host(self.h, tsdf.h if tsdf is not None else None, ptrs, bx, nb,
                                         C.byref(pz) if pz is not None else None, lc, dptr, _stream_ptr(stream)))
         return depth_out
+
+
+class Pipeline:
+    """Host frames through copy-in / sweep / fuse+copy-out streams, two frames
+    in flight (ps_pipe_*).  push() returns at once; the depth map of a frame
+    lands in its host buffer by the time the push two calls later, or
+    flush(), returns."""
+
+    def __init__(self, sweep: Sweep, tsdf: Optional["Tsdf"] = None):
+        h = C.c_void_p()
+        _check(load().ps_pipe_create(sweep.h, tsdf.h if tsdf is not None else None, C.byref(h)))
+        self.h = h
+        self.sweep, self.tsdf = sweep, tsdf
+        self._keep = [None, None]   # host buffers of the frames in flight
+        self._n = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().ps_pipe_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def push(self, host_images: Sequence[np.ndarray], boxes=None, world_to_ref=None, local_center=None,
+             depth_out: Optional[np.ndarray] = None):
+        n = 1 + len(self.sweep.rig.cams)
+        arrs = [np.ascontiguousarray(a, dtype=np.uint8) if isinstance(a, np.ndarray) else a for a in host_images]
+        ptrs = (C.c_void_p * n)(*[a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr() for a in arrs])
+        bx, nb = boxes_array(boxes)
+        pz = pose(world_to_ref) if world_to_ref is not None else None
+        lc = None if local_center is None else (C.c_double * 3)(*local_center)
+        dptr = None
+        if depth_out is not None:
+            dptr = depth_out.ctypes.data if isinstance(depth_out, np.ndarray) else depth_out.data_ptr()
+        _check(load().ps_pipe_push(self.h, ptrs, bx, nb, C.byref(pz) if pz is not None else None, lc, dptr))
+        self._keep[self._n & 1] = depth_out
+        self._n += 1
+        return depth_out
+
+    def flush(self):
+        _check(load().ps_pipe_flush(self.h))
+        self._keep = [None, None]
 
 
 BATCH_SHORTEST_FIRST, BATCH_GIVEN_ORDER = 0, 1

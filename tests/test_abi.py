@@ -98,3 +98,12 @@ def test_batch_argument_errors_without_gpu():
     best = C.c_int32()
     ms = (C.c_double * 1)()
     assert L.psbatch_autotune(None, 0, None, None, None, None, None, 0, 1, C.byref(best), ms, None) == P.PS_ERR_ARG
+
+
+def test_pipeline_argument_errors_without_gpu():
+    L = P.load()
+    h = C.c_void_p()
+    assert L.ps_pipe_create(None, None, C.byref(h)) == P.PS_ERR_ARG
+    assert h.value is None
+    assert L.ps_pipe_push(None, None, None, 0, None, None, None) == P.PS_ERR_ARG
+    assert L.ps_pipe_flush(None) == P.PS_ERR_ARG
