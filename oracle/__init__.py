@@ -111,6 +111,17 @@ def lib():
             L.orc_tsdf_load.argtypes = [_P, C.c_int64, _P, _D, _D]
             L.orc_tsdf_ever_maybe.argtypes = [_P, _P]
             L.orc_tsdf_ever_maybe.restype = C.c_int64
+            L.orc_project_jacobian.argtypes = [C.POINTER(OrCamera), _D, _D]
+            L.orc_soft_argmin.argtypes = [_D, _D, C.c_int32, C.c_double, _D, _D, _D]
+            L.orc_soft_depth.argtypes = [C.POINTER(OrCamera), C.c_int32, C.POINTER(OrCamera), C.POINTER(OrPose),
+                                         C.POINTER(OrLevel), _P, C.c_double, _D, _D]
+            L.orc_soft_depth_grad.argtypes = [C.POINTER(OrCamera), C.c_int32, C.POINTER(OrCamera),
+                                              C.POINTER(OrPose), C.POINTER(OrLevel), _P, C.c_double, _D, _D, _P,
+                                              _D]
+            L.orc_dense_fuse.argtypes = [_P, _D, C.c_double, C.c_double, C.c_double, _D, _P, C.POINTER(OrCamera),
+                                         C.POINTER(OrPose), _D]
+            L.orc_dense_fuse_grad.argtypes = [_P, _D, C.c_double, C.c_double, C.c_double, _D, _P,
+                                              C.POINTER(OrCamera), C.POINTER(OrPose), _D, _D, _D, _D]
             _lib = L
     return _lib
 
@@ -409,3 +420,87 @@ class Tsdf:
         k = np.zeros((n, 3), dtype=np.int64)
         lib().orc_tsdf_ever_maybe(self.h, k.ctypes.data)
         return k
+
+
+# ----------------------------------------------------------------- differentiable forms
+
+def project_jacobian(cam, X) -> np.ndarray:
+    """d(u, v)/dX of the unified projection with distortion (2 x 3)."""
+    J = np.zeros(6)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    lib().orc_project_jacobian(C.byref(camera(cam)), _dptr(X), _dptr(J))
+    return J.reshape(2, 3)
+
+
+def soft_argmin(costs, rho, T: float):
+    """(weights s, E = sum s rho, soft minimum S) of one pixel; None when no cost is finite."""
+    c = np.ascontiguousarray(costs, dtype=np.float64)
+    r = np.ascontiguousarray(rho, dtype=np.float64)
+    s = np.zeros(len(c))
+    E, S = C.c_double(), C.c_double()
+    ok = lib().orc_soft_argmin(_dptr(c), _dptr(r), len(c), T, _dptr(s), C.byref(E), C.byref(S))
+    return (s, E.value, S.value) if ok else None
+
+
+def _real_images(images):
+    arrs = [np.ascontiguousarray(i, dtype=np.float64) for i in images]
+    ptrs = (C.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+    return arrs, ptrs
+
+
+def soft_depth(rig, lv, images, T: float = 0.05, poses=None, with_cost: bool = False):
+    """Soft-argmin range map of one full-resolution level of real-valued images
+    (and the soft-minimum cost map with with_cost)."""
+    poses = rig.ref_to_cam if poses is None else poses
+    cams = (OrCamera * len(rig.cams))(*[camera(c) for c in rig.cams])
+    ps = (OrPose * len(rig.cams))(*[pose(p) for p in poses])
+    arrs, ptrs = _real_images(images)
+    out = np.zeros((rig.ref.height, rig.ref.width))
+    cost = np.zeros_like(out)
+    lib().orc_soft_depth(C.byref(camera(rig.ref)), len(rig.cams), cams, ps, C.byref(level(lv)), ptrs, T,
+                         _dptr(out), _dptr(cost))
+    return (out, cost) if with_cost else out
+
+
+def soft_depth_grad(rig, lv, images, g, T: float = 0.05, poses=None, g_cost=None):
+    """Gradient of sum(g * range) + sum(g_cost * S): (per-image gradients, (n_cams, 6) pose
+    gradients (w, v)).  g may be None."""
+    poses = rig.ref_to_cam if poses is None else poses
+    cams = (OrCamera * len(rig.cams))(*[camera(c) for c in rig.cams])
+    ps = (OrPose * len(rig.cams))(*[pose(p) for p in poses])
+    arrs, ptrs = _real_images(images)
+    gi = [np.zeros_like(a) for a in arrs]
+    gptr = (C.c_void_p * len(gi))(*[a.ctypes.data for a in gi])
+    gp = np.zeros((len(rig.cams), 6))
+    gg = None if g is None else np.ascontiguousarray(g, dtype=np.float64)
+    gs = None if g_cost is None else np.ascontiguousarray(g_cost, dtype=np.float64)
+    lib().orc_soft_depth_grad(C.byref(camera(rig.ref)), len(rig.cams), cams, ps, C.byref(level(lv)), ptrs, T,
+                              None if gg is None else _dptr(gg), None if gs is None else _dptr(gs), gptr, _dptr(gp))
+    return gi, gp
+
+
+def dense_fuse(vox, nb, origin, voxel, mu, w_max, depth, cam, w2c) -> np.ndarray:
+    """Fusion of one depth map into a dense grid; vox: (n_blocks, 512, 2) {D, w}."""
+    vin = np.ascontiguousarray(vox, dtype=np.float64)
+    out = np.empty_like(vin)
+    nbv = np.ascontiguousarray(nb, dtype=np.int32)
+    o = np.ascontiguousarray(origin, dtype=np.float64)
+    d = np.ascontiguousarray(depth, dtype=np.float32)
+    lib().orc_dense_fuse(nbv.ctypes.data, _dptr(o), voxel, mu, w_max, _dptr(vin), d.ctypes.data,
+                         C.byref(camera(cam)), C.byref(pose(w2c)), _dptr(out))
+    return out
+
+
+def dense_fuse_grad(vox, nb, origin, voxel, mu, w_max, depth, cam, w2c, gD):
+    """Gradient of sum(gD * D_out): (dD_in (n_blocks, 512), d depth (H, W), pose (6,) as (w, v))."""
+    vin = np.ascontiguousarray(vox, dtype=np.float64)
+    nbv = np.ascontiguousarray(nb, dtype=np.int32)
+    o = np.ascontiguousarray(origin, dtype=np.float64)
+    d = np.ascontiguousarray(depth, dtype=np.float32)
+    g = np.ascontiguousarray(gD, dtype=np.float64)
+    gin = np.zeros(g.shape)
+    gd = np.zeros(d.shape)
+    gp = np.zeros(6)
+    lib().orc_dense_fuse_grad(nbv.ctypes.data, _dptr(o), voxel, mu, w_max, _dptr(vin), d.ctypes.data,
+                              C.byref(camera(cam)), C.byref(pose(w2c)), _dptr(g), _dptr(gin), _dptr(gd), _dptr(gp))
+    return gin, gd, gp

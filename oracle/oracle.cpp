@@ -19,6 +19,10 @@
 //   voxel-block allocation along [d - mu, d + mu] ... Sec. III-C
 //   TSDF running average ............ Sec. III-C, Eq. (2), weight cap
 //   local-map allocation gate ....... Sec. III-C (60 m x 60 m x 3 m)
+//   depth filters ................... Sec. III-A "Depth map filtering"
+//   block swap-out / load ........... Sec. III-C (blocks leaving the local map)
+//   differentiable forms (not in the paper): soft-argmin depth over the
+//   plane hypotheses and dense fusion, each with its gradient
 //
 // Readings where the paper is silent are stated beside the code that takes
 // them.  Parity pins: see tests/test_oracle_*.py.
@@ -623,6 +627,150 @@ void integrate(Tsdf& T, const float* depth, const OrCamera& cam, const OrPose& w
     }
 }
 
+// ---------------------------------------------------------------- differentiable forms
+//
+// Not in the paper: the winner-take-all depth is piecewise constant in the
+// images and the poses, so for gradients the plane hypotheses are averaged
+// with softmax weights of their aggregated costs (soft-argmin):
+//   s_k   = exp(-C_k / T) / sum over valid k' of exp(-C_k' / T)
+//   E     = sum_k s_k rho_k,   rho_k = (n_k . r) / d_k   (inverse range of plane k along the ray)
+//   range = 1 / E
+// C_k is the minimum over the matching cameras, as in the sweep; its
+// gradient goes to the camera that attains it (the lowest index on a tie).
+// Beside the range, the soft minimum of the costs
+//   S = -T log sum over valid k of exp(-C_k / T),   dS/dC_k = s_k,
+// is a photometric loss that needs no ground truth.
+// Images are real-valued here (intensities as given, no quantisation).
+
+double norm3(const double X[3]) { return std::sqrt(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]); }
+
+// d(u, v)/dX of project() at X (row-major 2 x 3), by the chain rule through
+// the sphere shift, the perspective division and the distortion polynomial.
+void project_jacobian(const OrCamera& c, const double X[3], double J[6]) {
+    double n = norm3(X);
+    double den = X[2] + c.xi * n;  // mx = X / den, my = Y / den
+    double dden[3] = {c.xi * X[0] / n, c.xi * X[1] / n, 1.0 + c.xi * X[2] / n};
+    double mx = X[0] / den, my = X[1] / den;
+    double dmx[3], dmy[3];
+    for (int i = 0; i < 3; ++i) {
+        dmx[i] = (i == 0 ? 1.0 / den : 0.0) - X[0] * dden[i] / (den * den);
+        dmy[i] = (i == 1 ? 1.0 / den : 0.0) - X[1] * dden[i] / (den * den);
+    }
+    double r2 = mx * mx + my * my;
+    double rad = 1.0 + c.k1 * r2 + c.k2 * r2 * r2, drad = c.k1 + 2.0 * c.k2 * r2;
+    double a = rad + 2.0 * mx * mx * drad + 2.0 * c.p1 * my + 6.0 * c.p2 * mx;  // dxd/dmx
+    double b = 2.0 * mx * my * drad + 2.0 * c.p1 * mx + 2.0 * c.p2 * my;        // dxd/dmy = dyd/dmx
+    double d = rad + 2.0 * my * my * drad + 6.0 * c.p1 * my + 2.0 * c.p2 * mx;  // dyd/dmy
+    for (int i = 0; i < 3; ++i) {
+        J[i] = c.fx * (a * dmx[i] + b * dmy[i]);
+        J[3 + i] = c.fy * (b * dmx[i] + d * dmy[i]);
+    }
+}
+
+// Level of real-valued images at full resolution (the differentiable forms
+// use one full-resolution level).
+void build_level_real(const OrCamera& ref, int n_cams, const OrCamera* cams, const OrLevel& L,
+                      const double* const* images, LevelCtx& ctx) {
+    ctx.ref = ref;
+    ctx.ref_img.W = ref.width;
+    ctx.ref_img.H = ref.height;
+    ctx.ref_img.px.assign(images[0], images[0] + (size_t)ref.width * ref.height);
+    for (int j = 0; j < n_cams; ++j) {
+        ctx.cams.push_back(cams[j]);
+        Image I;
+        I.W = cams[j].width;
+        I.H = cams[j].height;
+        I.px.assign(images[1 + j], images[1 + j] + (size_t)I.W * I.H);
+        ctx.cam_img.push_back(I);
+    }
+    ctx.rho = std::min(L.window, MAX_WINDOW) / 2;
+    make_planes(L, ctx);
+    size_t N = (size_t)ref.width * ref.height;
+    ctx.ray.resize(N);
+    ctx.ray_ok.resize(N);
+    for (int y = 0; y < ref.height; ++y)
+        for (int x = 0; x < ref.width; ++x) {
+            double r[3];
+            bool ok = unproject(ref, x, y, r);
+            size_t i = (size_t)y * ref.width + x;
+            ctx.ray_ok[i] = ok;
+            ctx.ray[i] = {r[0], r[1], r[2]};
+        }
+}
+
+// Soft-argmin of one pixel: costs C (K, +inf = invalid) and inverse ranges
+// rho; weights s (K), E = sum s rho and (if S != NULL) the soft minimum S.
+// False when no plane is valid.
+bool soft_argmin(const double* C, const double* rho, int K, double T, double* s, double* E, double* S = nullptr) {
+    double m = INF;
+    for (int k = 0; k < K; ++k)
+        if (C[k] < m) m = C[k];
+    if (!(m < INF)) return false;
+    double Z = 0.0;
+    for (int k = 0; k < K; ++k) {
+        s[k] = C[k] < INF ? std::exp(-(C[k] - m) / T) : 0.0;
+        Z += s[k];
+    }
+    *E = 0.0;
+    for (int k = 0; k < K; ++k) {
+        s[k] /= Z;
+        *E += s[k] * rho[k];
+    }
+    if (S) *S = m - T * std::log(Z);
+    return true;
+}
+
+// Costs (min over cameras), the attaining camera and inverse ranges of one pixel.
+bool soft_pixel_costs(const LevelCtx& ctx, const OrPose* poses, int px, int py, std::vector<double>& C,
+                      std::vector<int>& jbest, std::vector<double>& rho) {
+    int K = (int)ctx.planes.size();
+    C.assign(K, INF);
+    jbest.assign(K, -1);
+    rho.assign(K, 0.0);
+    int r = ctx.rho;
+    if (!(px >= r && py >= r && px < ctx.ref.width - r && py < ctx.ref.height - r)) return false;
+    size_t i = (size_t)py * ctx.ref.width + px;
+    if (!ctx.ray_ok[i]) return false;
+    const double* ray = ctx.ray[i].data();
+    for (int k = 0; k < K; ++k) {
+        const PlaneH& P = ctx.planes[k];
+        rho[k] = (P.n[0] * ray[0] + P.n[1] * ray[1] + P.n[2] * ray[2]) / P.d;
+        for (int j = 0; j < (int)ctx.cams.size(); ++j) {
+            double c = window_cost(ctx, poses[j], j, P, px, py);
+            if (c < C[k]) {
+                C[k] = c;
+                jbest[k] = j;
+            }
+        }
+    }
+    return true;
+}
+
+// Dense TSDF grid (differentiable fusion): voxel v of block b holds {D, w}
+// at vox[2 (512 b + v)], block b = bx + nbx (by + nby bz), v = x + 8 y + 64 z.
+struct DenseGrid {
+    int nbx, nby, nbz;
+    double origin[3], voxel, mu, w_max;
+};
+
+// Observation of one voxel by one depth map (Sec. III-C): eta and the pixel,
+// or false when the voxel is not updated (no projection, no depth, eta < -mu).
+bool dense_voxel_obs(const DenseGrid& G, int gx, int gy, int gz, const float* depth, const OrCamera& cam,
+                     const OrPose& w2c, double Xc[3], double* eta, size_t* pix) {
+    double X[3] = {G.origin[0] + (gx + 0.5) * G.voxel, G.origin[1] + (gy + 0.5) * G.voxel,
+                   G.origin[2] + (gz + 0.5) * G.voxel};
+    apply(w2c, X, Xc);
+    double u, v;
+    if (!project(cam, Xc, &u, &v)) return false;
+    double pu = std::floor(u + 0.5), pv = std::floor(v + 0.5);
+    if (pu < 0 || pv < 0 || pu >= cam.width || pv >= cam.height) return false;
+    *pix = (size_t)pv * cam.width + (size_t)pu;
+    double dm = depth[*pix];
+    if (!(dm > 0.0) || !std::isfinite(dm)) return false;
+    *eta = dm - norm3(Xc);
+    return *eta >= -G.mu;
+}
+
 }  // namespace
 
 // ===================================================================== C ABI
@@ -968,6 +1116,189 @@ int64_t orc_tsdf_ever_maybe(void* h, int64_t* keys) {
             ++i;
         }
     return (int64_t)T->ever_maybe.size();
+}
+
+// ---------------------------------------------------------------- differentiable forms (C API)
+
+void orc_project_jacobian(const OrCamera* c, const double* X, double* J) { project_jacobian(*c, X, J); }
+
+int orc_soft_argmin(const double* C, const double* rho, int32_t K, double T, double* s, double* E, double* S) {
+    return soft_argmin(C, rho, K, T, s, E, S);
+}
+
+// Soft-argmin range map of one full-resolution level of real-valued images
+// (ref, then the matching cameras) and the soft-minimum cost map (cost may be
+// NULL); both 0 where no plane is valid.
+void orc_soft_depth(const OrCamera* ref, int32_t n_cams, const OrCamera* cams, const OrPose* poses,
+                    const OrLevel* L, const double* const* images, double T, double* range, double* cost) {
+    LevelCtx ctx;
+    build_level_real(*ref, n_cams, cams, *L, images, ctx);
+    const int K = (int)ctx.planes.size();
+    std::vector<double> C, rho, sw(K);
+    std::vector<int> jb;
+    for (int y = 0; y < ref->height; ++y)
+        for (int x = 0; x < ref->width; ++x) {
+            double E = 0.0, S = 0.0;
+            size_t i = (size_t)y * ref->width + x;
+            range[i] = 0.0;
+            if (cost) cost[i] = 0.0;
+            if (soft_pixel_costs(ctx, poses, x, y, C, jb, rho) &&
+                soft_argmin(C.data(), rho.data(), K, T, sw.data(), &E, &S)) {
+                range[i] = 1.0 / E;
+                if (cost) cost[i] = S;
+            }
+        }
+}
+
+// Gradient of L = sum_p g(p) range(p) + gs(p) S(p) (gs may be NULL) with respect to the images (g_images:
+// one array per image, ADDED to) and to left perturbations of each
+// ref_to_cam pose, T_j <- exp([w]x, v) T_j (g_pose: 6 per camera, (w, v),
+// ADDED to).  Chain: range = 1/E; dE/dC_k = -s_k (rho_k - E) / T; C_k is the
+// winning camera's (1 - ZNCC) / 2; ZNCC's derivative with respect to each
+// window sample of either window; bilinear weights (image) and the bilinear
+// slope times the projection Jacobian (pose: dX_j = w x X_j + v).
+void orc_soft_depth_grad(const OrCamera* ref, int32_t n_cams, const OrCamera* cams, const OrPose* poses,
+                         const OrLevel* L, const double* const* images, double T, const double* g,
+                         const double* gs, double* const* g_images, double* g_pose) {
+    LevelCtx ctx;
+    build_level_real(*ref, n_cams, cams, *L, images, ctx);
+    const int K = (int)ctx.planes.size(), r = ctx.rho, N = (2 * r + 1) * (2 * r + 1);
+    std::vector<double> C, rho, sw(K);
+    std::vector<int> jb;
+    std::vector<double> a(N), b(N);
+    for (int py = 0; py < ref->height; ++py)
+        for (int px = 0; px < ref->width; ++px) {
+            const double gp = g ? g[(size_t)py * ref->width + px] : 0.0;
+            const double gsp = gs ? gs[(size_t)py * ref->width + px] : 0.0;
+            double E = 0.0;
+            if (gp == 0.0 && gsp == 0.0) continue;
+            if (!soft_pixel_costs(ctx, poses, px, py, C, jb, rho)) continue;
+            if (!soft_argmin(C.data(), rho.data(), K, T, sw.data(), &E)) continue;
+            const double gE = -gp / (E * E);
+            for (int k = 0; k < K; ++k) {
+                if (!(C[k] < INF)) continue;
+                const double gC = gE * (-sw[k] * (rho[k] - E) / T) + gsp * sw[k];
+                const int j = jb[k];
+                const PlaneH& P = ctx.planes[k];
+                // the two windows of the winning camera
+                int n = 0;
+                for (int dy = -r; dy <= r; ++dy)
+                    for (int dx = -r; dx <= r; ++dx) {
+                        a[n] = ctx.ref_img.at(px + dx, py + dy);
+                        warped_sample(ctx, poses[j], j, P, px + dx, py + dy, &b[n]);
+                        ++n;
+                    }
+                double ma = 0, mb = 0;
+                for (int q = 0; q < N; ++q) {
+                    ma += a[q];
+                    mb += b[q];
+                }
+                ma /= N;
+                mb /= N;
+                double cov = 0, va = 0, vb = 0;
+                for (int q = 0; q < N; ++q) {
+                    cov += (a[q] - ma) * (b[q] - mb);
+                    va += (a[q] - ma) * (a[q] - ma);
+                    vb += (b[q] - mb) * (b[q] - mb);
+                }
+                const double sab = std::sqrt(va * vb), z = cov / sab;
+                const double gz = -0.5 * gC;  // cost = (1 - z) / 2
+                n = 0;
+                for (int dy = -r; dy <= r; ++dy)
+                    for (int dx = -r; dx <= r; ++dx, ++n) {
+                        const int qx = px + dx, qy = py + dy;
+                        const double dza = (b[n] - mb) / sab - z * (a[n] - ma) / va;
+                        const double dzb = (a[n] - ma) / sab - z * (b[n] - mb) / vb;
+                        g_images[0][(size_t)qy * ref->width + qx] += gz * dza;
+                        const double gb = gz * dzb;
+                        // the warp of q: X on the plane, X_j in camera j, (u, v), bilinear
+                        const double* ray = ctx.ray[(size_t)qy * ref->width + qx].data();
+                        const double lam = P.d / (P.n[0] * ray[0] + P.n[1] * ray[1] + P.n[2] * ray[2]);
+                        double X[3] = {lam * ray[0], lam * ray[1], lam * ray[2]}, Xj[3];
+                        apply(poses[j], X, Xj);
+                        double u, v;
+                        project(ctx.cams[j], Xj, &u, &v);
+                        const Image& I = ctx.cam_img[j];
+                        int x0 = (int)std::floor(u), y0 = (int)std::floor(v);
+                        double ax = u - x0, ay = v - y0;
+                        int x1 = std::min(x0 + 1, I.W - 1), y1 = std::min(y0 + 1, I.H - 1);
+                        double* G = g_images[1 + j];
+                        G[(size_t)y0 * I.W + x0] += gb * (1 - ax) * (1 - ay);
+                        G[(size_t)y0 * I.W + x1] += gb * ax * (1 - ay);
+                        G[(size_t)y1 * I.W + x0] += gb * (1 - ax) * ay;
+                        G[(size_t)y1 * I.W + x1] += gb * ax * ay;
+                        const double dwdu = (1 - ay) * (I.at(x1, y0) - I.at(x0, y0)) + ay * (I.at(x1, y1) - I.at(x0, y1));
+                        const double dwdv = (1 - ax) * (I.at(x0, y1) - I.at(x0, y0)) + ax * (I.at(x1, y1) - I.at(x1, y0));
+                        double J[6];
+                        project_jacobian(ctx.cams[j], Xj, J);
+                        double gX[3];
+                        for (int i = 0; i < 3; ++i) gX[i] = gb * (dwdu * J[i] + dwdv * J[3 + i]);
+                        double* gp6 = g_pose + 6 * j;
+                        gp6[0] += Xj[1] * gX[2] - Xj[2] * gX[1];  // w: X_j x gX
+                        gp6[1] += Xj[2] * gX[0] - Xj[0] * gX[2];
+                        gp6[2] += Xj[0] * gX[1] - Xj[1] * gX[0];
+                        gp6[3] += gX[0];                          // v
+                        gp6[4] += gX[1];
+                        gp6[5] += gX[2];
+                    }
+            }
+        }
+}
+
+// Differentiable fusion of one depth map into a dense grid (Sec. III-C,
+// Eq. 2 with unit observation weight): out = in, then every observed voxel
+// D <- (w D + min(1, eta/mu)) / (w + 1), w <- min(w + 1, w_max).
+void orc_dense_fuse(const int32_t* nb, const double* origin, double voxel, double mu, double w_max,
+                    const double* vox_in, const float* depth, const OrCamera* cam, const OrPose* w2c,
+                    double* vox_out) {
+    DenseGrid G{nb[0], nb[1], nb[2], {origin[0], origin[1], origin[2]}, voxel, mu, w_max};
+    const size_t n = (size_t)nb[0] * nb[1] * nb[2] * 512;
+    std::memcpy(vox_out, vox_in, sizeof(double) * 2 * n);
+    for (size_t i = 0; i < n; ++i) {
+        size_t b = i / 512, v = i % 512;
+        int gx = (int)(b % nb[0]) * 8 + (int)(v % 8), gy = (int)((b / nb[0]) % nb[1]) * 8 + (int)((v / 8) % 8),
+            gz = (int)(b / ((size_t)nb[0] * nb[1])) * 8 + (int)(v / 64);
+        double Xc[3], eta;
+        size_t pix;
+        if (!dense_voxel_obs(G, gx, gy, gz, depth, *cam, *w2c, Xc, &eta, &pix)) continue;
+        double w = vox_in[2 * i + 1];
+        vox_out[2 * i] = (w * vox_in[2 * i] + std::min(1.0, eta / mu)) / (w + 1.0);
+        vox_out[2 * i + 1] = std::min(w + 1.0, w_max);
+    }
+}
+
+// Gradient of L = sum_i gD[i] D_out[i] (the weights are counts: no gradient)
+// with respect to D_in (written), the depth map (ADDED to) and a left
+// perturbation of world_to_cam, X_c <- exp([w]x, v) X_c (6 values, ADDED to).
+// An observed voxel passes w / (w + 1) to D_in; when eta < mu it passes
+// 1 / (mu (w + 1)) to its pixel's depth, and minus that times X_c / |X_c| to X_c.
+void orc_dense_fuse_grad(const int32_t* nb, const double* origin, double voxel, double mu, double w_max,
+                         const double* vox_in, const float* depth, const OrCamera* cam, const OrPose* w2c,
+                         const double* gD, double* gD_in, double* g_depth, double* g_pose) {
+    DenseGrid G{nb[0], nb[1], nb[2], {origin[0], origin[1], origin[2]}, voxel, mu, w_max};
+    const size_t n = (size_t)nb[0] * nb[1] * nb[2] * 512;
+    for (size_t i = 0; i < n; ++i) {
+        size_t b = i / 512, v = i % 512;
+        int gx = (int)(b % nb[0]) * 8 + (int)(v % 8), gy = (int)((b / nb[0]) % nb[1]) * 8 + (int)((v / 8) % 8),
+            gz = (int)(b / ((size_t)nb[0] * nb[1])) * 8 + (int)(v / 64);
+        double Xc[3], eta;
+        size_t pix;
+        gD_in[i] = gD[i];
+        if (!dense_voxel_obs(G, gx, gy, gz, depth, *cam, *w2c, Xc, &eta, &pix)) continue;
+        double w = vox_in[2 * i + 1];
+        gD_in[i] = gD[i] * w / (w + 1.0);
+        if (!(eta < mu)) continue;  // truncated at 1: no dependence on eta
+        double ge = gD[i] / (mu * (w + 1.0));
+        g_depth[pix] += ge;
+        double nrm = norm3(Xc), gX[3];
+        for (int k = 0; k < 3; ++k) gX[k] = -ge * Xc[k] / nrm;
+        g_pose[0] += Xc[1] * gX[2] - Xc[2] * gX[1];
+        g_pose[1] += Xc[2] * gX[0] - Xc[0] * gX[2];
+        g_pose[2] += Xc[0] * gX[1] - Xc[1] * gX[0];
+        g_pose[3] += gX[0];
+        g_pose[4] += gX[1];
+        g_pose[5] += gX[2];
+    }
 }
 
 }  // extern "C"

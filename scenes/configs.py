@@ -412,3 +412,54 @@ def batch_mix(seed: int = 0, n: int = 64, sizes=BATCH_SIZES, planes=BATCH_PLANES
         name = f"mix{i}-{W}x{H}-{1 + n_cams}cam-{n_planes}planes"
         out.append(Workload(name, rig, levels, tsdf, scene, traj, boxes, ss=ss))
     return out
+
+
+# --------------------------------------------------------------------------
+# diff: the small rig of the differentiable forms
+# --------------------------------------------------------------------------
+
+def diff(seed: int = 0, width: int = 96, height: int = 80, n_planes: int = 32) -> Workload:
+    """Reference + 2 matching cameras (0.4 m left and right, distortion drawn
+    as for the street rig) at 96 x 80, f = 0.8 W, looking at 3-5 textured
+    fronto-parallel rectangles at 2-7 m in front of a textured background
+    at 8-10 m; one full-resolution level of n_planes fronto planes on
+    2-12 m with a 5x5 window; a dense 32^3 grid of 10 cm voxels around the
+    nearest rectangle."""
+    rng = np.random.default_rng(7000 + seed)
+    scale = width / 1280.0
+
+    def cam():
+        c = _street_camera(rng, scale)
+        return dataclasses.replace(c, width=width, height=height, cx=width / 2.0, cy=height / 2.0,
+                                   fx=0.8 * width, fy=0.8 * width)
+
+    ref = cam()
+    cams, poses = [], []
+    for side in (-1.0, 1.0):
+        cams.append(cam())
+        yaw, pitch = (math.radians(float(v)) for v in rng.uniform(-1.0, 1.0, size=2))
+        R_cr = rot_xyz(pitch, yaw, 0.0)
+        c = np.array([0.4 * side, 0.0, 0.0])
+        poses.append(Pose(R_cr.T, -R_cr.T @ c))
+    rig = Rig(ref=ref, cams=cams, ref_to_cam=poses)
+    scene = Scene(seed=seed)
+    zb = float(rng.uniform(8.0, 10.0))
+    scene.rects.append(Rect(c=(0.0, 0.0, zb), e1=(1, 0, 0), e2=(0, 1, 0), a=3.0 * zb, b=2.4 * zb,
+                            texel=0.04 * zb, tex_id=1))
+    nearest = None
+    for i in range(int(rng.integers(3, 6))):
+        z = float(rng.uniform(2.0, 7.0))
+        ax = math.radians(rng.uniform(-35, 35))
+        ay = math.radians(rng.uniform(-25, 25))
+        c = (z * math.tan(ax), z * math.tan(ay), z)
+        half = float(rng.uniform(0.2, 0.4)) * z
+        scene.rects.append(Rect(c=c, e1=(1, 0, 0), e2=(0, 1, 0), a=half, b=half * 0.8, texel=0.04 * z,
+                                tex_id=10 + i))
+        if nearest is None or z < nearest[2]:
+            nearest = c
+    origin = (nearest[0] - 1.6, nearest[1] - 1.6, nearest[2] - 1.6)
+    tsdf = TsdfParams(voxel_size=0.1, mu=0.3, dense_dim=(32, 32, 32), origin=origin)
+    levels = [Level(kind=DOWNSAMPLE, factor=1, window=5, sets=[PlaneSet(FRONTO, n_planes, 2.0, 12.0)])]
+    traj = [Pose(np.eye(3), np.zeros(3))]
+    boxes = [np.zeros((0, 4), dtype=np.int32)]
+    return Workload(f"diff-{width}x{height}-3cam-{n_planes}planes", rig, levels, tsdf, scene, traj, boxes, ss=4)
