@@ -416,6 +416,73 @@ int psbatch_autotune(psweep_t* const* sweeps, int32_t n, const uint8_t* const* i
                      const int32_t* n_boxes, float* const* depth_out, const ps_batch_opts* candidates,
                      int32_t n_cand, int32_t reps, int32_t* best, double* ms_out, void* stream);
 
+/* ---------------------------------------------------------------------
+ * Differentiable forms (the paper has none: its winner-take-all depth and
+ * its fusion are used forward only; these make the sweep and the fusion
+ * usable inside gradient-based calibration or learning).
+ *
+ * Soft-argmin depth over the plane hypotheses of one full-resolution level
+ * (Sec. III-A costs on real-valued images):
+ *   C_k   = min over matching cameras of (1 - ZNCC) / 2 (lowest camera index
+ *           on a tie; invalid windows as in psweep_depth)
+ *   s_k   = exp(-C_k / T) / sum over valid k' of exp(-C_k' / T)
+ *   range = 1 / sum_k s_k rho_k,  rho_k = (n_k . r) / d_k, the inverse range
+ *           of plane k along the pixel's unit ray r (Eq. 1)
+ *   cost  = -T log sum over valid k of exp(-C_k / T)   (soft minimum)
+ * Both are 0 where no plane is valid.  psdiff_backward gives the gradient of
+ * L = sum g_range * range + g_cost * cost with respect to every image and
+ * to a left perturbation (w, v) of each ref_to_cam pose:
+ * T_j <- exp([w]x, v) T_j, i.e. X_j <- X_j + w x X_j + v to first order. */
+typedef struct psdiff_s psdiff_t;
+
+typedef struct {
+    ps_camera ref;
+    int32_t n_cams;          /* 1 .. PS_MAX_CAMS */
+    const ps_camera* cams;   /* host array of n_cams */
+    ps_level level;          /* kind PS_LEVEL_DOWNSAMPLE, factor 1; window 5, 7 or 9 */
+    double temperature;      /* T > 0 */
+} ps_diff_desc;
+
+/* Builds the reference ray table (Eq. 1) and the plane table; allocates. */
+int psdiff_create(const ps_diff_desc* desc, psdiff_t** out);
+
+/* images: host array of 1 + n_cams device float32 images (reference first,
+ * each H x W of its camera), real-valued intensities.  ref_to_cam: host
+ * array of n_cams poses (per call: they may be the variables of an
+ * optimisation).  range, cost (may be NULL): device float32 H x W.  aux:
+ * device float32 H x W x 3 that psdiff_backward needs (may be NULL when no
+ * backward follows).  Asynchronous on `stream`. */
+int psdiff_forward(psdiff_t* h, const float* const* images, const ps_pose* ref_to_cam, float* range, float* cost,
+                   float* aux, void* stream);
+
+/* Same images and poses as the forward whose aux is passed.  g_range,
+ * g_cost: device float32 H x W (either may be NULL).  g_images: host array
+ * of 1 + n_cams device float32 buffers shaped like the images (entries may
+ * be NULL), ADDED to.  g_pose: device double[6 n_cams], (w, v) per camera,
+ * ADDED to (may be NULL).  Asynchronous; the costs are recomputed per tile,
+ * nothing of the forward but aux is kept. */
+int psdiff_backward(psdiff_t* h, const float* const* images, const ps_pose* ref_to_cam, const float* aux,
+                    const float* g_range, const float* g_cost, float* const* g_images, double* g_pose,
+                    void* stream);
+
+void psdiff_destroy(psdiff_t* h);
+
+/* Gradient of one fusion step into a caller-owned dense grid (the step
+ * tsdf_integrate_dense_static performs; Eq. 2 with unit observation
+ * weight): voxels_in is the grid BEFORE the step (same layout), g_D_out the
+ * gradient with respect to the D of every voxel after it (float32 per
+ * voxel; weights are counts and carry none).  Writes g_D_in (float32 per
+ * voxel, may be NULL); ADDS to g_depth (device float32 H x W of cam, may be
+ * NULL) and g_pose (device double[6], a left perturbation (w, v) of
+ * world_to_cam, may be NULL).  An observed voxel (eta >= -mu) passes
+ * w / (w + 1) of its gradient to D_in; if eta < mu also 1 / (mu (w + 1)) to
+ * its pixel's depth and minus that along X_c / |X_c| to the camera-frame
+ * point.  Asynchronous on `stream`; allocates nothing. */
+int tsdf_dense_fuse_backward(const float* voxels_in, const int32_t* dims, const double* origin, double voxel_size,
+                             double mu, double w_max, const float* depth, const ps_camera* cam,
+                             const ps_pose* world_to_cam, const float* g_D_out, float* g_D_in, float* g_depth,
+                             double* g_pose, void* stream);
+
 /* Message for the calling thread's last non-zero status ("" if none). */
 const char* ps_last_error(void);
 

@@ -118,6 +118,9 @@ def lib():
             L.orc_soft_depth_grad.argtypes = [C.POINTER(OrCamera), C.c_int32, C.POINTER(OrCamera),
                                               C.POINTER(OrPose), C.POINTER(OrLevel), _P, C.c_double, _D, _D, _P,
                                               _D]
+            L.orc_soft_depth_ties.argtypes = [C.POINTER(OrCamera), C.c_int32, C.POINTER(OrCamera),
+                                              C.POINTER(OrPose), C.POINTER(OrLevel), _P, C.c_double, C.c_double,
+                                              _P]
             L.orc_dense_fuse.argtypes = [_P, _D, C.c_double, C.c_double, C.c_double, _D, _P, C.POINTER(OrCamera),
                                          C.POINTER(OrPose), _D]
             L.orc_dense_fuse_grad.argtypes = [_P, _D, C.c_double, C.c_double, C.c_double, _D, _P,
@@ -477,6 +480,19 @@ def soft_depth_grad(rig, lv, images, g, T: float = 0.05, poses=None, g_cost=None
     lib().orc_soft_depth_grad(C.byref(camera(rig.ref)), len(rig.cams), cams, ps, C.byref(level(lv)), ptrs, T,
                               None if gg is None else _dptr(gg), None if gs is None else _dptr(gs), gptr, _dptr(gp))
     return gi, gp
+
+
+def soft_depth_ties(rig, lv, images, tau: float = 1e-5, tau_px: float = 0.0, poses=None) -> np.ndarray:
+    """Pixels where some valid plane's two lowest camera costs lie within tau,
+    or (tau_px > 0) a winning window sample lies within tau_px of a pixel-grid line."""
+    poses = rig.ref_to_cam if poses is None else poses
+    cams = (OrCamera * len(rig.cams))(*[camera(c) for c in rig.cams])
+    ps = (OrPose * len(rig.cams))(*[pose(p) for p in poses])
+    arrs, ptrs = _real_images(images)
+    amb = np.zeros((rig.ref.height, rig.ref.width), np.uint8)
+    lib().orc_soft_depth_ties(C.byref(camera(rig.ref)), len(rig.cams), cams, ps, C.byref(level(lv)), ptrs, tau,
+                              tau_px, amb.ctypes.data)
+    return amb.astype(bool)
 
 
 def dense_fuse(vox, nb, origin, voxel, mu, w_max, depth, cam, w2c) -> np.ndarray:

@@ -1150,6 +1150,51 @@ void orc_soft_depth(const OrCamera* ref, int32_t n_cams, const OrCamera* cams, c
         }
 }
 
+// Pixels whose soft-argmin gradient depends on a floating-point decision:
+// some valid plane's two lowest camera costs lie within tau of each other
+// (float rounding may route that plane's gradient to either camera), or a
+// window sample of the winning camera lies within tau_px of a pixel-grid
+// line (the bilinear slope, which the pose gradient uses, jumps there).
+// amb: one byte per pixel, 1 = marked.
+void orc_soft_depth_ties(const OrCamera* ref, int32_t n_cams, const OrCamera* cams, const OrPose* poses,
+                         const OrLevel* L, const double* const* images, double tau, double tau_px, uint8_t* amb) {
+    LevelCtx ctx;
+    build_level_real(*ref, n_cams, cams, *L, images, ctx);
+    const int K = (int)ctx.planes.size(), r = ctx.rho;
+    for (int y = 0; y < ref->height; ++y)
+        for (int x = 0; x < ref->width; ++x) {
+            uint8_t a = 0;
+            if (x >= r && y >= r && x < ref->width - r && y < ref->height - r)
+                for (int k = 0; k < K && !a; ++k) {
+                    double c1 = INF, c2 = INF;
+                    int jb = -1;
+                    for (int j = 0; j < n_cams; ++j) {
+                        double c = window_cost(ctx, poses[j], j, ctx.planes[k], x, y);
+                        if (c < c1) {
+                            c2 = c1;
+                            c1 = c;
+                            jb = j;
+                        } else if (c < c2) {
+                            c2 = c;
+                        }
+                    }
+                    if (c2 < INF && c2 - c1 < tau) a = 1;
+                    if (jb < 0 || tau_px <= 0.0) continue;
+                    const PlaneH& P = ctx.planes[k];
+                    for (int dy = -r; dy <= r && !a; ++dy)
+                        for (int dx = -r; dx <= r && !a; ++dx) {
+                            const double* ray = ctx.ray[(size_t)(y + dy) * ref->width + (x + dx)].data();
+                            const double lam = P.d / (P.n[0] * ray[0] + P.n[1] * ray[1] + P.n[2] * ray[2]);
+                            double X[3] = {lam * ray[0], lam * ray[1], lam * ray[2]}, Xj[3], u, v;
+                            apply(poses[jb], X, Xj);
+                            project(ctx.cams[jb], Xj, &u, &v);
+                            if (frac_dist(u) < tau_px || frac_dist(v) < tau_px) a = 1;
+                        }
+                }
+            amb[(size_t)y * ref->width + x] = a;
+        }
+}
+
 // Gradient of L = sum_p g(p) range(p) + gs(p) S(p) (gs may be NULL) with respect to the images (g_images:
 // one array per image, ADDED to) and to left perturbations of each
 // ref_to_cam pose, T_j <- exp([w]x, v) T_j (g_pose: 6 per camera, (w, v),

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpsweep.so")
-SOURCES = ["common.cu", "sweep.cu", "tsdf.cu", "batch.cu", "batch_k16.cu", "batch_k24.cu", "pipe.cu"]
+SOURCES = ["common.cu", "sweep.cu", "tsdf.cu", "batch.cu", "batch_k16.cu", "batch_k24.cu", "pipe.cu", "diff.cu"]
 HEADERS = ["internal.cuh", "sweep_dev.cuh", "batch_dev.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]

@@ -1,0 +1,502 @@
+// Differentiable plane sweep: soft-argmin depth over the plane hypotheses
+// and its gradient with respect to the images and the matching cameras'
+// poses.  Not in the paper: the winner-take-all depth (Sec. III-A) is
+// piecewise constant, so for gradients the planes are averaged with softmax
+// weights of their aggregated costs:
+//   s_k = exp(-C_k / T) / sum over valid k' of exp(-C_k' / T)
+//   range = 1 / sum_k s_k rho_k,   rho_k = (n_k . r) / d_k,
+// and the soft minimum S = -T log sum_k exp(-C_k / T) is a second output.
+// C_k = min over the matching cameras of (1 - ZNCC) / 2 (lowest camera index
+// on a tie), exactly the sweep's cost but on real-valued images.
+//
+// Kernels (one CTA per 16 x 16 output tile, one thread per output pixel):
+//   soft_fwd_kernel  per plane and camera, warp the tile + window halo into
+//                    shared memory; two-pass window ZNCC per pixel; minimum
+//                    over cameras; online softmax over planes.
+//   soft_bwd_kernel  recomputes the same costs (bit-identical), forms
+//                    dL/dC_k, spreads dL/dZNCC over both windows with shared
+//                    atomics, then per warped halo sample scatters dL/dI to
+//                    the 4 bilinear texels and chains dL/dw through the
+//                    bilinear slope and the projection Jacobian to a left
+//                    perturbation (w, v) of each ref_to_cam pose (CTA
+//                    reduction, FP64 atomics).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "sweep_dev.cuh"
+
+namespace ps {
+int build_rays(const ps_camera& cam, float4* rays, double* max_angle);
+
+namespace {
+
+constexpr int DT = 16;                 // output tile edge
+constexpr int DNT = DT * DT;           // threads per CTA
+constexpr int DMAX_HALO = DT + 2 * 4;  // halo edge for the widest window (9 x 9)
+
+struct DiffCam {
+    float R[9], t[3];
+    CamF c;
+    const float* img;
+};
+
+struct DiffP {
+    int W, H, rho, K, n_cams;
+    float T;
+    const float4* rays;
+    const PlaneD* planes;
+    const float* ref;
+    DiffCam cams[PS_MAX_CAMS];
+};
+
+// Projection of X_j (camera frame) with the unified model and distortion;
+// false where the point does not project (the sweep's validity rules).
+__device__ __forceinline__ bool project_f(const CamF& c, float X, float Y, float Z, float* u, float* v,
+                                          float* n_out) {
+    float n = sqrtf(fmaf(X, X, fmaf(Y, Y, Z * Z)));
+    float inv = 1.0f / fmaf(c.xi, n, Z);
+    float mx = X * inv, my = Y * inv;
+    float r2 = fmaf(mx, mx, my * my);
+    float rad = fmaf(r2, fmaf(c.k2, r2, c.k1), 1.0f);
+    float mxy = mx * my;
+    float xd = fmaf(mx, rad, fmaf(2.0f * c.p1, mxy, c.p2 * fmaf(2.0f * mx, mx, r2)));
+    float yd = fmaf(my, rad, fmaf(c.p1, fmaf(2.0f * my, my, r2), 2.0f * c.p2 * mxy));
+    *u = fmaf(c.fx, xd, c.cx);
+    *v = fmaf(c.fy, yd, c.cy);
+    *n_out = n;
+    return (Z > c.lim * n) && (r2 <= c.r2_max);
+}
+
+// d(u, v)/dX of project_f (row-major 2 x 3).
+__device__ __forceinline__ void project_jac_f(const CamF& c, float X, float Y, float Z, float J[6]) {
+    float n = sqrtf(fmaf(X, X, fmaf(Y, Y, Z * Z)));
+    float den = fmaf(c.xi, n, Z), id = 1.0f / den;
+    float dden[3] = {c.xi * X / n, c.xi * Y / n, 1.0f + c.xi * Z / n};
+    float mx = X * id, my = Y * id;
+    float dmx[3], dmy[3];
+    for (int i = 0; i < 3; ++i) {
+        dmx[i] = (i == 0 ? id : 0.0f) - mx * dden[i] * id;
+        dmy[i] = (i == 1 ? id : 0.0f) - my * dden[i] * id;
+    }
+    float r2 = fmaf(mx, mx, my * my);
+    float rad = fmaf(r2, fmaf(c.k2, r2, c.k1), 1.0f), drad = fmaf(2.0f * c.k2, r2, c.k1);
+    float a = rad + 2.0f * mx * mx * drad + 2.0f * c.p1 * my + 6.0f * c.p2 * mx;
+    float b = 2.0f * mx * my * drad + 2.0f * c.p1 * mx + 2.0f * c.p2 * my;
+    float d = rad + 2.0f * my * my * drad + 6.0f * c.p1 * my + 2.0f * c.p2 * mx;
+    for (int i = 0; i < 3; ++i) {
+        J[i] = c.fx * (a * dmx[i] + b * dmy[i]);
+        J[3 + i] = c.fy * (b * dmx[i] + d * dmy[i]);
+    }
+}
+
+// The warp of halo position (gx, gy) through plane P into camera C: the
+// point in the camera frame, the pixel and the bilinear sample (NaN when
+// invalid: no ray, plane behind the ray, no projection, outside the image).
+struct Warp {
+    float X, Y, Z, u, v, w;
+};
+
+__device__ __forceinline__ Warp warp_at(const DiffP& P, const DiffCam& C, const PlaneD& pl, int gx, int gy) {
+    const float nan = __int_as_float(0x7fc00000);
+    Warp o{0.f, 0.f, 0.f, 0.f, 0.f, nan};
+    if (gx < 0 || gy < 0 || gx >= P.W || gy >= P.H) return o;
+    float4 r = P.rays[(size_t)gy * P.W + gx];
+    float nr = pl.nx * r.x + pl.ny * r.y + pl.nz * r.z;
+    if (!(nr > 0.0f)) return o;
+    float lam = pl.d / nr;
+    float x = lam * r.x, y = lam * r.y, z = lam * r.z;
+    o.X = fmaf(C.R[0], x, fmaf(C.R[1], y, fmaf(C.R[2], z, C.t[0])));
+    o.Y = fmaf(C.R[3], x, fmaf(C.R[4], y, fmaf(C.R[5], z, C.t[1])));
+    o.Z = fmaf(C.R[6], x, fmaf(C.R[7], y, fmaf(C.R[8], z, C.t[2])));
+    float n;
+    if (!project_f(C.c, o.X, o.Y, o.Z, &o.u, &o.v, &n)) return o;
+    if (!(o.u >= 0.0f && o.u <= (float)(C.c.width - 1) && o.v >= 0.0f && o.v <= (float)(C.c.height - 1))) return o;
+    int x0 = (int)floorf(o.u), y0 = (int)floorf(o.v);
+    int x1 = min(x0 + 1, C.c.width - 1), y1 = min(y0 + 1, C.c.height - 1);
+    float ax = o.u - (float)x0, ay = o.v - (float)y0;
+    const float* I = C.img;
+    float i00 = I[(size_t)y0 * C.c.width + x0], i10 = I[(size_t)y0 * C.c.width + x1];
+    float i01 = I[(size_t)y1 * C.c.width + x0], i11 = I[(size_t)y1 * C.c.width + x1];
+    o.w = (1.0f - ay) * ((1.0f - ax) * i00 + ax * i10) + ay * ((1.0f - ax) * i01 + ax * i11);
+    return o;
+}
+
+// Two-pass ZNCC of the pixel's window: reference samples R (halo layout),
+// warped samples Wv.  False when a sample is invalid or a window is flat.
+struct Zn {
+    float z, ma, mb, va, vb, sab;
+};
+
+__device__ __forceinline__ bool window_zncc(const float* R, const float* Wv, int hw, int lx, int ly, int rho, Zn* o) {
+    const int N = (2 * rho + 1) * (2 * rho + 1);
+    float sa = 0.f, sb = 0.f;
+    bool ok = true;
+    for (int dy = 0; dy <= 2 * rho; ++dy)
+        for (int dx = 0; dx <= 2 * rho; ++dx) {
+            int q = (ly + dy) * hw + lx + dx;
+            float b = Wv[q];
+            ok &= !isnan(b);
+            sa += R[q];
+            sb += b;
+        }
+    if (!ok) return false;
+    float ma = sa / (float)N, mb = sb / (float)N;
+    float cov = 0.f, va = 0.f, vb = 0.f;
+    for (int dy = 0; dy <= 2 * rho; ++dy)
+        for (int dx = 0; dx <= 2 * rho; ++dx) {
+            int q = (ly + dy) * hw + lx + dx;
+            float ea = R[q] - ma, eb = Wv[q] - mb;
+            cov = fmaf(ea, eb, cov);
+            va = fmaf(ea, ea, va);
+            vb = fmaf(eb, eb, vb);
+        }
+    if (va < (float)N * 1e-8f || vb < (float)N * 1e-8f) return false;
+    o->sab = sqrtf(va * vb);
+    o->z = cov / o->sab;
+    o->ma = ma;
+    o->mb = mb;
+    o->va = va;
+    o->vb = vb;
+    return true;
+}
+
+__device__ __forceinline__ bool pixel_inside(const DiffP& P, int gx, int gy) {
+    return gx >= P.rho && gy >= P.rho && gx < P.W - P.rho && gy < P.H - P.rho;
+}
+
+__global__ void __launch_bounds__(DNT) soft_fwd_kernel(const __grid_constant__ DiffP P, float* range, float* cost,
+                                                      float* aux) {
+    __shared__ float Rs[DMAX_HALO * DMAX_HALO];
+    __shared__ float Ws[DMAX_HALO * DMAX_HALO];
+    const int hw = DT + 2 * P.rho, npos = hw * hw;
+    const int tid = threadIdx.x, lx = tid % DT, ly = tid / DT;
+    const int x0 = blockIdx.x * DT - P.rho, y0 = blockIdx.y * DT - P.rho;
+    const int gx = blockIdx.x * DT + lx, gy = blockIdx.y * DT + ly;
+    for (int p = tid; p < npos; p += DNT) {
+        int hx = x0 + p % hw, hy = y0 + p / hw;
+        Rs[p] = (hx >= 0 && hy >= 0 && hx < P.W && hy < P.H) ? P.ref[(size_t)hy * P.W + hx] : 0.0f;
+    }
+    const bool in = gx < P.W && gy < P.H;
+    float4 ray = in ? P.rays[(size_t)gy * P.W + gx] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool use = in && pixel_inside(P, gx, gy) && !isnan(ray.x);
+    const float inf = __int_as_float(0x7f800000);
+    float cmin = inf, Z = 0.f, Nr = 0.f;
+    for (int k = 0; k < P.K; ++k) {
+        const PlaneD pl = P.planes[k];
+        float best = inf;
+        for (int j = 0; j < P.n_cams; ++j) {
+            __syncthreads();
+            for (int p = tid; p < npos; p += DNT) Ws[p] = warp_at(P, P.cams[j], pl, x0 + p % hw, y0 + p / hw).w;
+            __syncthreads();
+            Zn zn;
+            if (use && window_zncc(Rs, Ws, hw, lx, ly, P.rho, &zn)) {
+                float c = 0.5f * (1.0f - zn.z);
+                if (c < best) best = c;
+            }
+        }
+        if (best < inf) {
+            float rho_k = (pl.nx * ray.x + pl.ny * ray.y + pl.nz * ray.z) / pl.d;
+            if (best < cmin) {  // rescale the running sums to the new minimum
+                float f = cmin < inf ? __expf(-(cmin - best) / P.T) : 0.f;
+                Z *= f;
+                Nr *= f;
+                cmin = best;
+            }
+            float e = __expf(-(best - cmin) / P.T);
+            Z += e;
+            Nr = fmaf(e, rho_k, Nr);
+        }
+    }
+    if (!in) return;
+    const size_t o = (size_t)gy * P.W + gx;
+    const bool ok = cmin < inf;
+    range[o] = ok ? Z / Nr : 0.f;
+    if (cost) cost[o] = ok ? cmin - P.T * logf(Z) : 0.f;
+    if (aux) {
+        aux[3 * o] = ok ? cmin : inf;
+        aux[3 * o + 1] = Z;
+        aux[3 * o + 2] = ok ? Nr / Z : 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(DNT) soft_bwd_kernel(const __grid_constant__ DiffP P, const float* aux,
+                                                      const float* g_range, const float* g_cost, float* g_ref,
+                                                      float* g_cam0, float* g_cam1, float* g_cam2, float* g_cam3,
+                                                      double* g_pose) {
+    extern __shared__ float sm[];
+    const int hw = DT + 2 * P.rho, npos = hw * hw;
+    float* Rs = sm;                           // [npos] reference
+    float* gR = Rs + npos;                    // [npos] dL/dref, summed over planes
+    float* Ws = gR + npos;                    // [n_cams][npos] warped samples of the current plane
+    float* gW = Ws + P.n_cams * npos;         // [n_cams][npos] dL/dw of the current plane
+    __shared__ float red[DNT / 32][6 * PS_MAX_CAMS];
+    float* g_cam[PS_MAX_CAMS] = {g_cam0, g_cam1, g_cam2, g_cam3};
+    const int tid = threadIdx.x, lx = tid % DT, ly = tid / DT;
+    const int x0 = blockIdx.x * DT - P.rho, y0 = blockIdx.y * DT - P.rho;
+    const int gx = blockIdx.x * DT + lx, gy = blockIdx.y * DT + ly;
+    for (int p = tid; p < npos; p += DNT) {
+        int hx = x0 + p % hw, hy = y0 + p / hw;
+        Rs[p] = (hx >= 0 && hy >= 0 && hx < P.W && hy < P.H) ? P.ref[(size_t)hy * P.W + hx] : 0.0f;
+        gR[p] = 0.f;
+    }
+    const bool in = gx < P.W && gy < P.H;
+    const size_t o = in ? (size_t)gy * P.W + gx : 0;
+    float4 ray = in ? P.rays[o] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float inf = __int_as_float(0x7f800000);
+    float cmin = inf, Z = 1.f, E = 0.f, gr = 0.f, gs = 0.f;
+    if (in) {
+        cmin = aux[3 * o];
+        Z = aux[3 * o + 1];
+        E = aux[3 * o + 2];
+        gr = g_range ? g_range[o] : 0.f;
+        gs = g_cost ? g_cost[o] : 0.f;
+    }
+    const bool use = in && pixel_inside(P, gx, gy) && !isnan(ray.x) && cmin < inf && (gr != 0.f || gs != 0.f);
+    const float gE = use ? -gr / (E * E) : 0.f;
+    float pose_acc[6 * PS_MAX_CAMS];
+    for (int i = 0; i < 6 * PS_MAX_CAMS; ++i) pose_acc[i] = 0.f;
+    for (int k = 0; k < P.K; ++k) {
+        const PlaneD pl = P.planes[k];
+        __syncthreads();
+        for (int p = tid; p < npos; p += DNT)
+            for (int j = 0; j < P.n_cams; ++j) {
+                Ws[j * npos + p] = warp_at(P, P.cams[j], pl, x0 + p % hw, y0 + p / hw).w;
+                gW[j * npos + p] = 0.f;
+            }
+        __syncthreads();
+        // the pixel's cost for this plane (as in the forward) and its camera
+        float best = inf;
+        int jb = -1;
+        Zn zb;
+        for (int j = 0; use && j < P.n_cams; ++j) {
+            Zn zn;
+            if (window_zncc(Rs, Ws + j * npos, hw, lx, ly, P.rho, &zn)) {
+                float c = 0.5f * (1.0f - zn.z);
+                if (c < best) {
+                    best = c;
+                    jb = j;
+                    zb = zn;
+                }
+            }
+        }
+        if (jb >= 0) {
+            const float s = __expf(-(best - cmin) / P.T) / Z;
+            const float rho_k = (pl.nx * ray.x + pl.ny * ray.y + pl.nz * ray.z) / pl.d;
+            const float gC = gE * (-s * (rho_k - E) / P.T) + gs * s;
+            const float gz = -0.5f * gC;
+            const float* Wj = Ws + jb * npos;
+            float* gWj = gW + jb * npos;
+            for (int dy = 0; dy <= 2 * P.rho; ++dy)
+                for (int dx = 0; dx <= 2 * P.rho; ++dx) {
+                    int q = (ly + dy) * hw + lx + dx;
+                    float ea = Rs[q] - zb.ma, eb = Wj[q] - zb.mb;
+                    atomicAdd(&gR[q], gz * (eb / zb.sab - zb.z * ea / zb.va));
+                    atomicAdd(&gWj[q], gz * (ea / zb.sab - zb.z * eb / zb.vb));
+                }
+        }
+        __syncthreads();
+        // chain dL/dw of every warped halo sample to the image and the pose
+        for (int p = tid; p < npos; p += DNT)
+            for (int j = 0; j < P.n_cams; ++j) {
+                const float gw = gW[j * npos + p];
+                if (gw == 0.f) continue;
+                const DiffCam& C = P.cams[j];
+                Warp wp = warp_at(P, C, pl, x0 + p % hw, y0 + p / hw);
+                int xa = (int)floorf(wp.u), ya = (int)floorf(wp.v);
+                int xb = min(xa + 1, C.c.width - 1), yb = min(ya + 1, C.c.height - 1);
+                float ax = wp.u - (float)xa, ay = wp.v - (float)ya;
+                const float* I = C.img;
+                const int Wc = C.c.width;
+                float i00 = I[(size_t)ya * Wc + xa], i10 = I[(size_t)ya * Wc + xb];
+                float i01 = I[(size_t)yb * Wc + xa], i11 = I[(size_t)yb * Wc + xb];
+                if (g_cam[j]) {
+                    float* G = g_cam[j];
+                    atomicAdd(&G[(size_t)ya * Wc + xa], gw * (1.f - ax) * (1.f - ay));
+                    atomicAdd(&G[(size_t)ya * Wc + xb], gw * ax * (1.f - ay));
+                    atomicAdd(&G[(size_t)yb * Wc + xa], gw * (1.f - ax) * ay);
+                    atomicAdd(&G[(size_t)yb * Wc + xb], gw * ax * ay);
+                }
+                float dwdu = (1.f - ay) * (i10 - i00) + ay * (i11 - i01);
+                float dwdv = (1.f - ax) * (i01 - i00) + ax * (i11 - i10);
+                float J[6];
+                project_jac_f(C.c, wp.X, wp.Y, wp.Z, J);
+                float gx3[3];
+                for (int i = 0; i < 3; ++i) gx3[i] = gw * (dwdu * J[i] + dwdv * J[3 + i]);
+                float* acc = pose_acc + 6 * j;
+                acc[0] += wp.Y * gx3[2] - wp.Z * gx3[1];
+                acc[1] += wp.Z * gx3[0] - wp.X * gx3[2];
+                acc[2] += wp.X * gx3[1] - wp.Y * gx3[0];
+                acc[3] += gx3[0];
+                acc[4] += gx3[1];
+                acc[5] += gx3[2];
+            }
+    }
+    __syncthreads();
+    if (g_ref)
+        for (int p = tid; p < npos; p += DNT) {
+            float g = gR[p];
+            if (g != 0.f) atomicAdd(&g_ref[(size_t)(y0 + p / hw) * P.W + (x0 + p % hw)], g);
+        }
+    if (g_pose) {
+        const int lane = tid & 31, wid = tid >> 5;
+        for (int i = 0; i < 6 * P.n_cams; ++i) {
+            float v = pose_acc[i];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+            if (lane == 0) red[wid][i] = v;
+        }
+        __syncthreads();
+        if (tid < 6 * P.n_cams) {
+            double s = 0.0;
+            for (int w = 0; w < DNT / 32; ++w) s += (double)red[w][tid];
+            atomicAdd(&g_pose[tid], s);
+        }
+    }
+}
+
+}  // namespace
+}  // namespace ps
+
+using namespace ps;
+
+struct psdiff_s {
+    ps_camera ref;
+    int n_cams = 0;
+    ps_camera cams[PS_MAX_CAMS];
+    int rho = 0, K = 0;
+    double T = 0.05;
+    float4* rays = nullptr;
+    PlaneD* planes = nullptr;
+};
+
+namespace {
+
+void free_diff(psdiff_t* h) {
+    if (!h) return;
+    cudaFree(h->rays);
+    cudaFree(h->planes);
+    delete h;
+}
+
+int fill_params(const psdiff_t* h, const float* const* images, const ps_pose* ref_to_cam, DiffP& P) {
+    std::memset(&P, 0, sizeof(P));
+    P.W = h->ref.width;
+    P.H = h->ref.height;
+    P.rho = h->rho;
+    P.K = h->K;
+    P.n_cams = h->n_cams;
+    P.T = (float)h->T;
+    P.rays = h->rays;
+    P.planes = h->planes;
+    PS_ARG(images != nullptr && images[0] != nullptr, "psdiff: images[0] is NULL");
+    PS_ARG(ref_to_cam != nullptr, "psdiff: ref_to_cam is NULL");
+    P.ref = images[0];
+    for (int j = 0; j < h->n_cams; ++j) {
+        PS_ARG(images[1 + j] != nullptr, "psdiff: images[%d] is NULL", 1 + j);
+        for (int i = 0; i < 12; ++i)
+            PS_ARG(std::isfinite(i < 9 ? ref_to_cam[j].R[i] : ref_to_cam[j].t[i - 9]), "psdiff: pose %d not finite", j);
+        for (int i = 0; i < 9; ++i) P.cams[j].R[i] = (float)ref_to_cam[j].R[i];
+        for (int i = 0; i < 3; ++i) P.cams[j].t[i] = (float)ref_to_cam[j].t[i];
+        P.cams[j].c = to_camf(h->cams[j]);
+        P.cams[j].img = images[1 + j];
+    }
+    return PS_OK;
+}
+
+}  // namespace
+
+extern "C" int psdiff_create(const ps_diff_desc* d, psdiff_t** out) {
+    clear_error();
+    PS_ARG(out != nullptr, "psdiff_create: out is NULL");
+    *out = nullptr;
+    PS_ARG(d != nullptr && d->cams != nullptr, "psdiff_create: desc or cams is NULL");
+    PS_ARG(d->n_cams >= 1 && d->n_cams <= PS_MAX_CAMS, "psdiff_create: n_cams must be in 1..%d", PS_MAX_CAMS);
+    PS_ARG(d->ref.width > 0 && d->ref.height > 0 && d->ref.width <= 16384 && d->ref.height <= 16384 &&
+               d->ref.fx > 0 && d->ref.fy > 0 && d->ref.xi >= 0,
+           "psdiff_create: bad reference camera");
+    for (int j = 0; j < d->n_cams; ++j)
+        PS_ARG(d->cams[j].width > 1 && d->cams[j].height > 1 && d->cams[j].fx > 0 && d->cams[j].fy > 0 &&
+                   d->cams[j].xi >= 0,
+               "psdiff_create: bad matching camera %d", j);
+    const ps_level& L = d->level;
+    PS_ARG(L.kind == PS_LEVEL_DOWNSAMPLE && L.factor == 1, "psdiff_create: one full-resolution level (factor 1)");
+    PS_ARG(L.window == 5 || L.window == 7 || L.window == 9, "psdiff_create: window must be 5, 7 or 9");
+    PS_ARG(L.n_sets >= 1 && L.n_sets <= PS_MAX_SETS, "psdiff_create: n_sets must be in 1..%d", PS_MAX_SETS);
+    PS_ARG(d->temperature > 0 && std::isfinite(d->temperature), "psdiff_create: temperature must be > 0");
+    std::vector<PlaneD> planes;
+    for (int s = 0; s < L.n_sets; ++s) {
+        const ps_plane_set& S = L.sets[s];
+        PS_ARG(S.count >= 1 && S.count <= 4096 && S.a > 0 && S.b >= S.a, "psdiff_create: bad plane set %d", s);
+        PS_ARG(S.family == PS_PLANES_FRONTO || S.family == PS_PLANES_GROUND, "psdiff_create: bad family");
+        double n[3] = {0, 0, 1};
+        if (S.family == PS_PLANES_GROUND) {
+            double nn = std::sqrt(S.n[0] * S.n[0] + S.n[1] * S.n[1] + S.n[2] * S.n[2]);
+            PS_ARG(nn > 0, "psdiff_create: ground normal is zero");
+            for (int i = 0; i < 3; ++i) n[i] = S.n[i] / nn;
+        }
+        for (int i = 0; i < S.count; ++i) {
+            double t = S.count > 1 ? (double)i / (S.count - 1) : 0.0;
+            double dd = S.family == PS_PLANES_FRONTO ? 1.0 / (1.0 / S.b + t * (1.0 / S.a - 1.0 / S.b))
+                                                     : S.a + t * (S.b - S.a);
+            planes.push_back({(float)n[0], (float)n[1], (float)n[2], (float)dd});
+        }
+    }
+    psdiff_t* h = new psdiff_t();
+    h->ref = d->ref;
+    h->n_cams = d->n_cams;
+    for (int j = 0; j < d->n_cams; ++j) h->cams[j] = d->cams[j];
+    h->rho = L.window / 2;
+    h->K = (int)planes.size();
+    h->T = d->temperature;
+    const size_t npx = (size_t)d->ref.width * d->ref.height;
+    cudaError_t e = cudaMalloc(&h->rays, sizeof(float4) * npx);
+    if (e == cudaSuccess) e = cudaMalloc(&h->planes, sizeof(PlaneD) * planes.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->planes, planes.data(), sizeof(PlaneD) * planes.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_diff(h);
+        set_error("psdiff_create: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? PS_ERR_OOM : PS_ERR_CUDA;
+    }
+    if (build_rays(d->ref, h->rays, nullptr) != PS_OK || cudaDeviceSynchronize() != cudaSuccess) {
+        free_diff(h);
+        return PS_ERR_CUDA;
+    }
+    *out = h;
+    return PS_OK;
+}
+
+extern "C" void psdiff_destroy(psdiff_t* h) { free_diff(h); }
+
+extern "C" int psdiff_forward(psdiff_t* h, const float* const* images, const ps_pose* ref_to_cam, float* range,
+                              float* cost, float* aux, void* stream) {
+    clear_error();
+    PS_ARG(h != nullptr && range != nullptr, "psdiff_forward: handle or range is NULL");
+    DiffP P;
+    int st = fill_params(h, images, ref_to_cam, P);
+    if (st) return st;
+    dim3 grid((P.W + DT - 1) / DT, (P.H + DT - 1) / DT);
+    soft_fwd_kernel<<<grid, DNT, 0, (cudaStream_t)stream>>>(P, range, cost, aux);
+    PS_CUDA(cudaGetLastError());
+    return PS_OK;
+}
+
+extern "C" int psdiff_backward(psdiff_t* h, const float* const* images, const ps_pose* ref_to_cam, const float* aux,
+                               const float* g_range, const float* g_cost, float* const* g_images, double* g_pose,
+                               void* stream) {
+    clear_error();
+    PS_ARG(h != nullptr && aux != nullptr, "psdiff_backward: handle or aux is NULL");
+    DiffP P;
+    int st = fill_params(h, images, ref_to_cam, P);
+    if (st) return st;
+    float* gi[1 + PS_MAX_CAMS] = {};
+    if (g_images)
+        for (int i = 0; i <= h->n_cams; ++i) gi[i] = g_images[i];
+    const int hw = DT + 2 * P.rho;
+    const size_t smem = sizeof(float) * (size_t)hw * hw * (2 + 2 * P.n_cams);  // at most 23 KB
+    dim3 grid((P.W + DT - 1) / DT, (P.H + DT - 1) / DT);
+    soft_bwd_kernel<<<grid, DNT, smem, (cudaStream_t)stream>>>(P, aux, g_range, g_cost, gi[0], gi[1], gi[2], gi[3],
+                                                               gi[4], g_pose);
+    PS_CUDA(cudaGetLastError());
+    return PS_OK;
+}

@@ -247,9 +247,13 @@ __global__ void visible_kernel(const __grid_constant__ FrameP F, TsdfDev T) {
     }
 }
 
-// Eq. 2 on one voxel.  a = voxel index - camera voxel (exact int), F.fb the
-// sub-voxel part, so the voxel centre sits at vox * (a + fb) from the camera.
-__device__ __forceinline__ void update_voxel(const FrameP& F, const float* depth, int ax, int ay, int az, float2& dw) {
+// Observation of a voxel by the depth map (Sec. III-C): eta, the pixel index
+// and the point in the camera frame.  a = voxel index - camera voxel (exact
+// int), F.fb the sub-voxel part, so the voxel centre sits at vox * (a + fb)
+// from the camera.  False when the voxel does not project into the image or
+// its pixel has no depth; eta < -mu is left to the caller.
+__device__ __forceinline__ bool observe_voxel(const FrameP& F, const float* depth, int ax, int ay, int az, float* eta_out,
+                                              size_t* pix_out, float Xc[3]) {
     const CamF& c = F.cam;
     float bx = F.fb[0], by = F.fb[1], bz = F.fb[2];
     float vx = ((float)ax + bx) * F.vox, vy = ((float)ay + by) * F.vox, vz = ((float)az + bz) * F.vox;
@@ -266,11 +270,12 @@ __device__ __forceinline__ void update_voxel(const FrameP& F, const float* depth
     float xd = fmaf(mx, rad, fmaf(2.0f * c.p1, mxy, c.p2 * fmaf(2.0f * mx, mx, r2)));
     float yd = fmaf(my, rad, fmaf(c.p1, fmaf(2.0f * my, my, r2), 2.0f * c.p2 * mxy));
     float u = fmaf(c.fx, xd, c.cx), v = fmaf(c.fy, yd, c.cy);
-    if (!((Z > c.lim * n) && (r2 <= c.r2_max))) return;
+    if (!((Z > c.lim * n) && (r2 <= c.r2_max))) return false;
     float pu = floorf(u + 0.5f), pv = floorf(v + 0.5f);
-    if (!(pu >= 0.f && pv >= 0.f && pu < (float)c.width && pv < (float)c.height)) return;
-    float d = __ldg(&depth[(size_t)pv * c.width + (size_t)pu]);
-    if (!(d > 0.f) || !(d < 3.0e38f)) return;
+    if (!(pu >= 0.f && pv >= 0.f && pu < (float)c.width && pv < (float)c.height)) return false;
+    const size_t pix = (size_t)pv * c.width + (size_t)pu;
+    float d = __ldg(&depth[pix]);
+    if (!(d > 0.f) || !(d < 3.0e38f)) return false;
     // |X_d| in voxel units: (a + b)^2 = a^2 (exact int) + (2a + b) b
     int A2 = ax * ax + ay * ay + az * az;
     float Bs = fmaf(fmaf(2.0f, (float)ax, bx), bx, fmaf(fmaf(2.0f, (float)ay, by), by, fmaf(2.0f, (float)az, bz) * bz));
@@ -282,7 +287,19 @@ __device__ __forceinline__ void update_voxel(const FrameP& F, const float* depth
     // eta = d - vox * (y + corr), with the product vox * y split exactly
     float q = F.vox * y;
     float qe = fmaf(F.vox, y, -q);
-    float eta = ((d - q) - qe) - fmaf(F.vox_lo, y, F.vox * corr);
+    *eta_out = ((d - q) - qe) - fmaf(F.vox_lo, y, F.vox * corr);
+    *pix_out = pix;
+    Xc[0] = X;
+    Xc[1] = Y;
+    Xc[2] = Z;
+    return true;
+}
+
+// Eq. 2 on one voxel.
+__device__ __forceinline__ void update_voxel(const FrameP& F, const float* depth, int ax, int ay, int az, float2& dw) {
+    float eta, Xc[3];
+    size_t pix;
+    if (!observe_voxel(F, depth, ax, ay, az, &eta, &pix, Xc)) return;
     if (eta < -F.mu) return;
     float sdf = fminf(1.0f, eta * F.inv_mu);
     float w = dw.y;
@@ -826,6 +843,96 @@ __global__ void static_dense_keys_kernel(int4* keys, int* n_alloc, int nx, int n
 }  // namespace
 }  // namespace ps
 
+namespace ps {
+namespace {
+
+// Frame record of a caller-owned dense grid at `origin` (no local map).
+int dense_frame(const double* origin, double voxel_size, double mu, double w_max, const ps_camera* cam,
+                const ps_pose* w2c, FrameP& F) {
+    std::memset(&F, 0, sizeof(F));
+    F.cam = to_camf(*cam);
+    for (int i = 0; i < 3; ++i) {
+        double Cw = -(w2c->R[i] * w2c->t[0] + w2c->R[3 + i] * w2c->t[1] + w2c->R[6 + i] * w2c->t[2]);
+        for (int k = 0; k < 3; ++k) {
+            F.R[3 * i + k] = (float)w2c->R[3 * i + k];
+            F.Rt[3 * i + k] = (float)w2c->R[3 * k + i];
+        }
+        double rel = Cw - origin[i];
+        F.C[i] = (float)rel;
+        double cv = rel / voxel_size;
+        double ic = std::floor(cv + 0.5);
+        PS_ARG(std::fabs(ic) < 1e8, "dense fusion: camera too far from the grid origin");
+        F.ic[i] = (int)ic;
+        F.fb[i] = (float)(0.5 - (cv - ic));
+    }
+    F.vox = (float)voxel_size;
+    F.vox_lo = (float)(voxel_size - (double)F.vox);
+    F.mu = (float)mu;
+    F.inv_mu = (float)(1.0 / mu);
+    F.w_max = (float)w_max;
+    F.block = (float)(8.0 * voxel_size);
+    F.view_angle = 4.0f;  // no view-cone culling: the range test alone keeps the list a superset
+    return PS_OK;
+}
+
+// Gradient of one dense fusion step (Eq. 2, unit observation weight) for
+// every voxel of an nbx x nby x nbz block grid: dL/dD_in = g w / (w + 1) on
+// observed voxels (g elsewhere); observed voxels with eta < mu add
+// g / (mu (w + 1)) to their pixel's depth gradient and -that * X_c / |X_c|
+// to X_c, which a left perturbation (w, v) of world_to_cam moves by
+// w x X_c + v (CTA reduction, FP64 atomics).
+__global__ void __launch_bounds__(256) dense_fuse_bwd_kernel(const __grid_constant__ FrameP F, int nbx, int nby,
+                                                            int nbz, const float2* vox_in, const float* depth,
+                                                            const float* gD, float* gD_in, float* g_depth,
+                                                            double* g_pose) {
+    __shared__ float red[8][6];
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const long long n = (long long)nbx * nby * nbz * B3;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / B3;
+        const int v = (int)(i % B3);
+        const int gx = (int)(b % nbx) * B + (v & 7), gy = (int)((b / nbx) % nby) * B + ((v >> 3) & 7),
+                  gz = (int)(b / ((long long)nbx * nby)) * B + (v >> 6);
+        const float g = gD[i];
+        float out = g;
+        float eta, Xc[3];
+        size_t pix;
+        if (observe_voxel(F, depth, gx - F.ic[0], gy - F.ic[1], gz - F.ic[2], &eta, &pix, Xc) && !(eta < -F.mu)) {
+            const float w = vox_in[i].y;
+            out = g * w / (w + 1.0f);
+            if (eta < F.mu && g != 0.f) {
+                const float ge = g / (F.mu * (w + 1.0f));
+                if (g_depth) atomicAdd(&g_depth[pix], ge);
+                const float s = -ge / sqrtf(Xc[0] * Xc[0] + Xc[1] * Xc[1] + Xc[2] * Xc[2]);
+                const float gx3[3] = {s * Xc[0], s * Xc[1], s * Xc[2]};
+                acc[0] += Xc[1] * gx3[2] - Xc[2] * gx3[1];
+                acc[1] += Xc[2] * gx3[0] - Xc[0] * gx3[2];
+                acc[2] += Xc[0] * gx3[1] - Xc[1] * gx3[0];
+                acc[3] += gx3[0];
+                acc[4] += gx3[1];
+                acc[5] += gx3[2];
+            }
+        }
+        if (gD_in) gD_in[i] = out;
+    }
+    if (!g_pose) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = 0; k < 6; ++k) {
+        float v = acc[k];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) red[wid][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += (double)red[w][threadIdx.x];
+        atomicAdd(&g_pose[threadIdx.x], s);
+    }
+}
+
+}  // namespace
+}  // namespace ps
+
 extern "C" int tsdf_integrate_dense_static(float* voxels, const int32_t* dims, const double* origin,
                                            double voxel_size, double mu, double w_max, const float* depth,
                                            const ps_camera* cam, const ps_pose* w2c, void* stream) {
@@ -858,29 +965,8 @@ extern "C" int tsdf_integrate_dense_static(float* voxels, const int32_t* dims, c
     T.pool_cap = (int)n_blocks;
 
     FrameP F;
-    std::memset(&F, 0, sizeof(F));
-    F.cam = to_camf(*cam);
-    for (int i = 0; i < 3; ++i) {
-        double Cw = -(w2c->R[i] * w2c->t[0] + w2c->R[3 + i] * w2c->t[1] + w2c->R[6 + i] * w2c->t[2]);
-        for (int k = 0; k < 3; ++k) {
-            F.R[3 * i + k] = (float)w2c->R[3 * i + k];
-            F.Rt[3 * i + k] = (float)w2c->R[3 * k + i];
-        }
-        double rel = Cw - origin[i];
-        F.C[i] = (float)rel;
-        double cv = rel / voxel_size;
-        double ic = std::floor(cv + 0.5);
-        PS_ARG(std::fabs(ic) < 1e8, "tsdf_integrate_dense_static: camera too far from the grid origin");
-        F.ic[i] = (int)ic;
-        F.fb[i] = (float)(0.5 - (cv - ic));
-    }
-    F.vox = (float)voxel_size;
-    F.vox_lo = (float)(voxel_size - (double)F.vox);
-    F.mu = (float)mu;
-    F.inv_mu = (float)(1.0 / mu);
-    F.w_max = (float)w_max;
-    F.block = (float)(8.0 * voxel_size);
-    F.view_angle = 4.0f;  // no view-cone culling: the range test alone keeps the list a superset
+    st = dense_frame(origin, voxel_size, mu, w_max, cam, w2c, F);
+    if (st) return st;
     int dev = 0, sms = 0;
     PS_CUDA(cudaGetDevice(&dev));
     PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -894,6 +980,34 @@ extern "C" int tsdf_integrate_dense_static(float* voxels, const int32_t* dims, c
     visible_kernel<<<sms * 4, 256, 0, s>>>(F, T);
     PS_CUDA(cudaGetLastError());
     integrate_kernel<<<sms * 8, IT, 0, s>>>(F, T, depth);
+    PS_CUDA(cudaGetLastError());
+    return PS_OK;
+}
+
+extern "C" int tsdf_dense_fuse_backward(const float* voxels_in, const int32_t* dims, const double* origin,
+                                        double voxel_size, double mu, double w_max, const float* depth,
+                                        const ps_camera* cam, const ps_pose* w2c, const float* g_D_out,
+                                        float* g_D_in, float* g_depth, double* g_pose, void* stream) {
+    clear_error();
+    PS_ARG(voxels_in && dims && origin && depth && cam && w2c && g_D_out, "tsdf_dense_fuse_backward: NULL argument");
+    PS_ARG(voxel_size > 0 && mu > 0 && w_max >= 1, "tsdf_dense_fuse_backward: need voxel_size > 0, mu > 0, w_max >= 1");
+    PS_ARG(cam->width > 0 && cam->height > 0 && cam->fx > 0 && cam->fy > 0 && cam->xi >= 0,
+           "tsdf_dense_fuse_backward: bad camera");
+    for (int i = 0; i < 3; ++i)
+        PS_ARG(dims[i] > 0 && dims[i] % 8 == 0, "tsdf_dense_fuse_backward: dims must be positive multiples of 8");
+    for (int i = 0; i < 12; ++i)
+        PS_ARG(std::isfinite(i < 9 ? w2c->R[i] : w2c->t[i - 9]), "tsdf_dense_fuse_backward: pose not finite");
+    FrameP F;
+    int st = dense_frame(origin, voxel_size, mu, w_max, cam, w2c, F);
+    if (st) return st;
+    int dev = 0, sms = 0;
+    PS_CUDA(cudaGetDevice(&dev));
+    PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const long long n = (long long)dims[0] * dims[1] * dims[2];
+    const int grid = (int)std::min<long long>((n + 255) / 256, (long long)sms * 8);
+    dense_fuse_bwd_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(F, dims[0] / 8, dims[1] / 8, dims[2] / 8,
+                                                                 reinterpret_cast<const float2*>(voxels_in), depth,
+                                                                 g_D_out, g_D_in, g_depth, g_pose);
     PS_CUDA(cudaGetLastError());
     return PS_OK;
 }

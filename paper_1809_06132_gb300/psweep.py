@@ -28,7 +28,8 @@ EXPORTS = ["psweep_create", "psweep_depth", "psweep_destroy", "tsdf_create", "ts
            "psweep_profile_read", "tsdf_profile", "tsdf_profile_read", "tsdf_integrate_dense_static",
            "tsdf_swap_out", "tsdf_load", "psbatch_create", "psbatch_run", "psbatch_timing", "psbatch_status",
            "psbatch_queue_stats", "psbatch_destroy", "psbatch_autotune", "ps_pipe_create", "ps_pipe_push",
-           "ps_pipe_flush", "ps_pipe_destroy",
+           "ps_pipe_flush", "ps_pipe_destroy", "psdiff_create", "psdiff_forward", "psdiff_backward",
+           "psdiff_destroy", "tsdf_dense_fuse_backward",
            "ps_last_error", "ps_version"]
 
 
@@ -81,6 +82,11 @@ class ps_level_out(C.Structure):
 class ps_batch_opts(C.Structure):
     _fields_ = [(n, C.c_int32) for n in ("tile_h", "kp", "plane_chunk", "order", "use_graph", "grid",
                                          "wait_limit_ms", "drill_unmet_wait")]
+
+
+class ps_diff_desc(C.Structure):
+    _fields_ = [("ref", ps_camera), ("n_cams", C.c_int32), ("cams", C.POINTER(ps_camera)), ("level", ps_level),
+                ("temperature", C.c_double)]
 
 
 class ps_tsdf_desc(C.Structure):
@@ -142,6 +148,13 @@ def load(build_if_missing: bool = True):
     L.ps_pipe_flush.argtypes = [P]
     L.ps_pipe_destroy.argtypes = [P]
     L.ps_pipe_destroy.restype = None
+    L.psdiff_create.argtypes = [C.POINTER(ps_diff_desc), C.POINTER(C.c_void_p)]
+    L.psdiff_forward.argtypes = [P, P, P, P, P, P, P]
+    L.psdiff_backward.argtypes = [P, P, P, P, P, P, P, P, P]
+    L.psdiff_destroy.argtypes = [P]
+    L.psdiff_destroy.restype = None
+    L.tsdf_dense_fuse_backward.argtypes = [P, P, P, C.c_double, C.c_double, C.c_double, P, C.POINTER(ps_camera),
+                                           C.POINTER(ps_pose), P, P, P, P, P]
     L.ps_last_error.restype = C.c_char_p
     L.ps_version.restype = C.c_char_p
     _lib = L
@@ -539,3 +552,164 @@ def tsdf_integrate_dense_static(voxels: torch.Tensor, dims, origin, voxel_size: 
 
 def version() -> str:
     return load().ps_version().decode()
+
+
+# ----------------------------------------------------------------- differentiable forms
+
+def se3_exp_left(xi, p):
+    """exp([w]x, v) applied on the left of pose p (R, t): rotation Exp(w) R,
+    translation Exp(w) t + v; xi = (w, v)."""
+    xi = np.asarray(xi, dtype=np.float64).reshape(6)
+    w, v = xi[:3], xi[3:]
+    th = float(np.linalg.norm(w))
+    K = np.array([[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]])
+    Rw = np.eye(3) if th == 0.0 else np.eye(3) + np.sin(th) / th * K + (1 - np.cos(th)) / th ** 2 * K @ K
+    R = np.asarray(p.R, dtype=np.float64).reshape(3, 3)
+    t = np.asarray(p.t, dtype=np.float64).reshape(3)
+
+    class _P:
+        pass
+    o = _P()
+    o.R, o.t = Rw @ R, Rw @ t + v
+    return o
+
+
+class SoftSweep:
+    """Soft-argmin depth of one full-resolution level and its gradient
+    (psdiff_*): images are float32 CUDA tensors (reference first), poses the
+    matching cameras' ref_to_cam."""
+
+    def __init__(self, rig, lv, temperature: float = 0.05):
+        L = load()
+        self.rig, self.level, self.T = rig, lv, float(temperature)
+        self._cams = (ps_camera * len(rig.cams))(*[camera(c) for c in rig.cams])
+        d = ps_diff_desc(ref=camera(rig.ref), n_cams=len(rig.cams), cams=self._cams, level=level(lv),
+                         temperature=self.T)
+        h = C.c_void_p()
+        _check(L.psdiff_create(C.byref(d), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().psdiff_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def _args(self, images, poses):
+        n = 1 + len(self.rig.cams)
+        if len(images) != n:
+            raise ValueError(f"expected {n} images")
+        ims = (C.c_void_p * n)(*[_dev(im, torch.float32, f"images[{i}]") for i, im in enumerate(images)])
+        poses = self.rig.ref_to_cam if poses is None else poses
+        ps = (ps_pose * len(poses))(*[pose(p) for p in poses])
+        return ims, ps
+
+    def forward(self, images, poses=None, want_aux: bool = True, stream=None):
+        """(range, soft-minimum cost, aux) maps; aux feeds backward()."""
+        ims, ps = self._args(images, poses)
+        H, W = self.rig.ref.height, self.rig.ref.width
+        dev = images[0].device
+        rng = torch.empty((H, W), dtype=torch.float32, device=dev)
+        cost = torch.empty((H, W), dtype=torch.float32, device=dev)
+        aux = torch.empty((H, W, 3), dtype=torch.float32, device=dev) if want_aux else None
+        _check(load().psdiff_forward(self.h, ims, ps, rng.data_ptr(), cost.data_ptr(),
+                                     aux.data_ptr() if aux is not None else None, _stream_ptr(stream)))
+        return rng, cost, aux
+
+    def backward(self, images, poses, aux, g_range=None, g_cost=None, stream=None):
+        """(per-image gradients, (n_cams, 6) float64 pose gradients (w, v))."""
+        ims, ps = self._args(images, poses)
+        gi = [torch.zeros_like(im) for im in images]
+        gptr = (C.c_void_p * len(gi))(*[g.data_ptr() for g in gi])
+        gp = torch.zeros((len(self.rig.cams), 6), dtype=torch.float64, device=images[0].device)
+        gr = _dev(g_range.contiguous(), torch.float32, "g_range") if g_range is not None else None
+        gc = _dev(g_cost.contiguous(), torch.float32, "g_cost") if g_cost is not None else None
+        _check(load().psdiff_backward(self.h, ims, ps, _dev(aux, torch.float32, "aux"), gr, gc, gptr,
+                                      gp.data_ptr(), _stream_ptr(stream)))
+        return gi, gp
+
+
+class _SoftDepthFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, sweep, base_poses, delta, *images):
+        d = delta.detach().cpu().double().numpy().reshape(len(base_poses), 6)
+        poses = [se3_exp_left(d[j], p) for j, p in enumerate(base_poses)]
+        ims = [im.contiguous() for im in images]
+        rng, cost, aux = sweep.forward(ims, poses)
+        ctx.sweep, ctx.poses, ctx.delta_meta = sweep, poses, (delta.dtype, delta.device)
+        ctx.save_for_backward(aux, *ims)
+        return rng, cost
+
+    @staticmethod
+    def backward(ctx, g_range, g_cost):
+        aux, *ims = ctx.saved_tensors
+        gi, gp = ctx.sweep.backward(ims, ctx.poses, aux, g_range, g_cost)
+        dt, dev = ctx.delta_meta
+        return (None, None, gp.to(dtype=dt, device=dev)) + tuple(gi)
+
+
+def soft_depth(sweep: SoftSweep, images, delta: Optional[torch.Tensor] = None, base_poses=None):
+    """Differentiable (range, soft-minimum cost) maps.  delta: (n_cams, 6)
+    left perturbation (w, v) of base_poses (default: the rig's ref_to_cam);
+    its gradient is exact at delta = 0 (update the base pose and reset delta
+    between steps).  The images receive gradients when they require them."""
+    base = list(sweep.rig.ref_to_cam if base_poses is None else base_poses)
+    if delta is None:
+        delta = torch.zeros((len(base), 6), dtype=torch.float64)
+    return _SoftDepthFn.apply(sweep, base, delta, *images)
+
+
+def tsdf_dense_fuse_backward(voxels_in, dims, origin, voxel_size, mu, w_max, depth, cam, world_to_cam, g_D_out,
+                             want_depth: bool = True, want_pose: bool = True, stream=None):
+    """(dL/dD_in per voxel, dL/ddepth, (6,) float64 pose gradient) of one fusion step."""
+    gD = _dev(g_D_out.contiguous(), torch.float32, "g_D_out")
+    gin = torch.empty(g_D_out.shape, dtype=torch.float32, device=voxels_in.device)
+    gd = torch.zeros(depth.shape, dtype=torch.float32, device=depth.device) if want_depth else None
+    gp = torch.zeros(6, dtype=torch.float64, device=depth.device) if want_pose else None
+    dims_a = (C.c_int32 * 3)(*[int(v) for v in dims])
+    org = (C.c_double * 3)(*[float(v) for v in origin])
+    _check(load().tsdf_dense_fuse_backward(_dev(voxels_in, torch.float32, "voxels_in"), dims_a, org,
+                                           float(voxel_size), float(mu), float(w_max),
+                                           _dev(depth, torch.float32, "depth"), C.byref(camera(cam)),
+                                           C.byref(pose(world_to_cam)), gD, gin.data_ptr(),
+                                           gd.data_ptr() if gd is not None else None,
+                                           gp.data_ptr() if gp is not None else None, _stream_ptr(stream)))
+    return gin, gd, gp
+
+
+class _DenseFuseFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, grid, base_pose, delta, vox_in, depth):
+        dims, origin, vs, mu, w_max, cam = grid
+        d = delta.detach().cpu().double().numpy().reshape(6)
+        p = se3_exp_left(d, base_pose)
+        vin = vox_in.contiguous()
+        dep = depth.contiguous()
+        out = vin.clone()
+        tsdf_integrate_dense_static(out, dims, origin, vs, mu, w_max, dep, cam, p)
+        ctx.grid, ctx.pose, ctx.delta_meta = grid, p, (delta.dtype, delta.device)
+        ctx.save_for_backward(vin, dep)
+        return out
+
+    @staticmethod
+    def backward(ctx, g_out):
+        vin, dep = ctx.saved_tensors
+        dims, origin, vs, mu, w_max, cam = ctx.grid
+        gin, gd, gp = tsdf_dense_fuse_backward(vin, dims, origin, vs, mu, w_max, dep, cam, ctx.pose,
+                                               g_out[..., 0])
+        g_vox = torch.zeros_like(vin)
+        g_vox[..., 0] = gin            # weights are observation counts: no gradient
+        dt, dev = ctx.delta_meta
+        return None, None, gp.to(dtype=dt, device=dev), g_vox, gd
+
+
+def dense_fuse(voxels: torch.Tensor, depth: torch.Tensor, params, cam, world_to_cam,
+               delta: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Differentiable fusion of one depth map into a dense (n_blocks, 512, 2)
+    {D, w} grid (params: TsdfParams with dense_dim); out of place.  delta:
+    (6,) left perturbation (w, v) of world_to_cam, exact at 0."""
+    grid = (tuple(params.dense_dim), tuple(params.origin), params.voxel_size, params.mu, params.w_max, cam)
+    if delta is None:
+        delta = torch.zeros(6, dtype=torch.float64)
+    return _DenseFuseFn.apply(grid, world_to_cam, delta, voxels, depth)

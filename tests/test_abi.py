@@ -107,3 +107,26 @@ def test_pipeline_argument_errors_without_gpu():
     assert h.value is None
     assert L.ps_pipe_push(None, None, None, 0, None, None, None) == P.PS_ERR_ARG
     assert L.ps_pipe_flush(None) == P.PS_ERR_ARG
+
+
+def test_differentiable_argument_errors_without_gpu():
+    L = P.load()
+    h = C.c_void_p()
+    assert L.psdiff_create(None, C.byref(h)) == P.PS_ERR_ARG
+    d = B.ps_diff_desc()
+    d.ref = B.ps_camera(xi=1.0, fx=48, fy=48, cx=48, cy=40, r2_max=1e30, width=96, height=80)
+    cams = (B.ps_camera * 1)(d.ref)
+    d.n_cams, d.cams = 1, cams
+    d.level.kind, d.level.factor, d.level.window, d.level.n_sets = 0, 2, 5, 1      # factor 2: refused
+    d.level.sets[0] = B.ps_plane_set(family=0, count=8, a=1.0, b=10.0)
+    d.temperature = 0.05
+    assert L.psdiff_create(C.byref(d), C.byref(h)) == P.PS_ERR_ARG
+    d.level.factor = 1
+    d.temperature = 0.0                                                           # T must be > 0
+    assert L.psdiff_create(C.byref(d), C.byref(h)) == P.PS_ERR_ARG
+    assert b"temperature" in L.ps_last_error()
+    assert h.value is None
+    assert L.psdiff_forward(None, None, None, None, None, None, None) == P.PS_ERR_ARG
+    assert L.psdiff_backward(None, None, None, None, None, None, None, None, None) == P.PS_ERR_ARG
+    assert L.tsdf_dense_fuse_backward(None, None, None, 0.1, 0.3, 100.0, None, None, None, None, None, None, None,
+                                      None) == P.PS_ERR_ARG

@@ -268,3 +268,25 @@ def test_soft_depth_camera_ties_go_to_the_lowest_index():
     gi2, gp2 = oracle.soft_depth_grad(wl.rig, wl.levels[0], [ims[0], ims[1], ims[1]], g)
     assert np.array_equal(gp2[0], gp1[0]) and (gp2[1] == 0).all() and np.abs(gp1[0]).max() > 0
     assert np.array_equal(gi2[1], gi1[1]) and (gi2[2] == 0).all()
+
+
+def test_tie_marks():
+    # one camera: never tied; two identical cameras: every pixel with a valid plane is tied
+    wl, ims = _tiny_rig(n_cams=1)
+    assert not oracle.soft_depth_ties(wl.rig, wl.levels[0], ims).any()
+    r = oracle.soft_depth(wl.rig, wl.levels[0], ims)
+    wl.rig = Rig(ref=wl.rig.ref, cams=[wl.rig.cams[0]] * 2, ref_to_cam=[wl.rig.ref_to_cam[0]] * 2)
+    amb = oracle.soft_depth_ties(wl.rig, wl.levels[0], [ims[0], ims[1], ims[1]])
+    assert np.array_equal(amb, r > 0)
+
+
+def test_grid_line_marks():
+    # a zero-baseline identity camera samples exactly on the pixel grid: every
+    # pixel with a valid plane is marked at any tau_px > 0, none at 0
+    wl, ims = _tiny_rig(n_cams=1)
+    wl.rig = Rig(ref=wl.rig.ref, cams=[wl.rig.ref], ref_to_cam=[Pose(np.eye(3), np.zeros(3))])
+    valid = oracle.soft_depth(wl.rig, wl.levels[0], [ims[0], ims[0] + 0.01 * ims[1]]) > 0
+    assert valid.any()
+    assert not oracle.soft_depth_ties(wl.rig, wl.levels[0], [ims[0], ims[0] + 0.01 * ims[1]]).any()
+    amb = oracle.soft_depth_ties(wl.rig, wl.levels[0], [ims[0], ims[0] + 0.01 * ims[1]], tau_px=1e-6)
+    assert np.array_equal(amb, valid)
