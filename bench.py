@@ -55,9 +55,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", choices=["street", "ring", "batch"], default="street",
+    ap.add_argument("--config", choices=["street", "ring", "batch", "diff"], default="street",
                     help="street: the paper-shaped frame (default); ring: 4 cameras, 256 full-resolution planes, "
-                         "2 cm voxels on a 500 m loop; batch: 64 uneven sweeps in one persistent launch")
+                         "2 cm voxels on a 500 m loop; batch: 64 uneven sweeps in one persistent launch; "
+                         "diff: soft-argmin forward/backward and extrinsic refinement")
     ap.add_argument("--batch-size", type=int, default=64, help="sweeps per batch (--config batch)")
     ap.add_argument("--half", action="store_true", help="FP16 storage of the matching images")
     return ap.parse_args()
@@ -580,12 +581,99 @@ def run_batch(args):
     return 0
 
 
+def run_diff(args):
+    """Differentiable sweep: forward and backward time of the soft-argmin
+    depth on the 96x80 rig (2 matching cameras, 32 planes, 5x5) and on a
+    640x512 rig (2 cameras, 128 planes), and a 50-step extrinsic refinement
+    from a 0.5 degree / 2 cm perturbation on the 192x160 rig."""
+    import torch
+
+    import scenes
+    import paper_1809_06132_gb300 as P
+    from paper_1809_06132_gb300.refine import refine_extrinsic
+    from scenes.configs import Rig
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = {}
+    for name, kw in (("diff-96x80-2cam-32planes", dict(width=96, height=80, n_planes=32)),
+                     ("diff-640x512-2cam-128planes", dict(width=640, height=512, n_planes=128))):
+        wl = scenes.diff(args.seed, **kw)
+        imgs, _ = scenes.FrameSource(wl, device=f"cuda:{local}").frame(0)
+        ims = [torch.from_numpy(i.numpy().astype(np.float32) / 255.0).to(dev) for i in imgs]
+        sw = P.SoftSweep(wl.rig, wl.levels[0])
+        g = torch.ones((wl.rig.ref.height, wl.rig.ref.width), dtype=torch.float32, device=dev)
+        for _ in range(args.warmup):
+            r, c, aux = sw.forward(ims)
+            sw.backward(ims, None, aux, g, g)
+        tf, tb = [], []
+        for _ in range(args.steps):
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            r, c, aux = sw.forward(ims)
+            e[1].record()
+            sw.backward(ims, None, aux, g, g)
+            e[2].record()
+            torch.cuda.synchronize()
+            tf.append(e[0].elapsed_time(e[1]))
+            tb.append(e[1].elapsed_time(e[2]))
+        pp = wl.pix_planes()
+        fm, bm = statistics.median(tf), statistics.median(tb)
+        out[name] = {"forward_ms": fm, "backward_ms": bm, "pix_planes": pp,
+                     "forward_gpix_planes_s": pp / (fm * 1e-3) / 1e9,
+                     "backward_gpix_planes_s": pp / (bm * 1e-3) / 1e9}
+    # refinement
+    wl = scenes.diff(args.seed, width=192, height=160, n_planes=64)
+    imgs, rng = scenes.FrameSource(wl, device=f"cuda:{local}").frame(0, with_range=True)
+    rig = Rig(ref=wl.rig.ref, cams=wl.rig.cams[1:], ref_to_cam=wl.rig.ref_to_cam[1:])
+    ims = [torch.from_numpy(imgs[0].numpy().astype(np.float32) / 255.0).to(dev),
+           torch.from_numpy(imgs[2].numpy().astype(np.float32) / 255.0).to(dev)]
+    gt = torch.from_numpy(rng.numpy().astype(np.float32)).to(dev)
+    true = rig.ref_to_cam[0]
+    rs = np.random.default_rng(args.seed)
+    ax, tv = rs.normal(size=3), rs.normal(size=3)
+    xi0 = np.concatenate([ax / np.linalg.norm(ax) * math.radians(0.5), tv / np.linalg.norm(tv) * 0.02])
+    sw = P.SoftSweep(rig, wl.levels[0])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    poses = refine_extrinsic(sw, ims, gt, P.se3_exp_left(xi0, true), steps=50)
+    torch.cuda.synchronize()
+    ref_s = time.perf_counter() - t0
+
+    def err(p):
+        dR = np.asarray(p.R) @ np.asarray(true.R).T
+        return (math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(dR) - 1) / 2)))),
+                float(np.linalg.norm(np.asarray(p.t) - np.asarray(true.t))))
+    e0, e1 = err(poses[0]), err(poses[-1])
+    main_case = out["diff-640x512-2cam-128planes"]
+    line = {
+        "metric": "differentiable plane sweep: forward + backward Gpix·planes/s", "unit": "Gpix·planes/s",
+        "value": main_case["pix_planes"] / ((main_case["forward_ms"] + main_case["backward_ms"]) * 1e-3) / 1e9,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": main_case["forward_ms"] + main_case["backward_ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "diff-640x512-2cam-128planes", "temperature": 0.05,
+                   "l2": "flushed between steps (256 MB write outside the step events)"},
+        "cases": out,
+        "refinement": {"rig": "diff-192x160-1cam-64planes", "steps": 50, "start_deg": e0[0], "start_m": e0[1],
+                       "end_deg": e1[0], "end_m": e1[1], "seconds": ref_s},
+        "gpu_launches": 2 * args.steps,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.config == "batch":
         return run_batch(args)
+    if args.config == "diff":
+        return run_diff(args)
     return run_ours(args)
 
 

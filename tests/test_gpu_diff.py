@@ -177,3 +177,36 @@ def test_dense_fuse_forward_and_gradient_parity():
     # float atomics add in any order: equal to rounding
     assert torch.allclose(dd.grad.cpu(), torch.from_numpy(gd), rtol=1e-5, atol=1e-6 * np.abs(gd).max())
     assert torch.allclose(delta.grad, torch.from_numpy(gp), rtol=1e-5, atol=1e-9 * np.abs(gp).max())
+
+
+def _pose_error(p, true):
+    dR = np.asarray(p.R) @ np.asarray(true.R).T
+    ang = math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(dR) - 1) / 2))))
+    return ang, float(np.linalg.norm(np.asarray(p.t) - np.asarray(true.t)))
+
+
+def test_extrinsic_refinement_from_a_perturbed_pose():
+    # 192 x 160 version of the rig, 64 planes, the right camera perturbed by
+    # 0.5 degrees and 2 cm; 50 steps of the photometric + range loss
+    from paper_1809_06132_gb300.refine import refine_extrinsic
+    from scenes.configs import Rig
+    wl = scenes.diff(0, width=192, height=160, n_planes=64)
+    imgs, rng = scenes.FrameSource(wl, device="cuda").frame(0, with_range=True)
+    rig = Rig(ref=wl.rig.ref, cams=wl.rig.cams[1:], ref_to_cam=wl.rig.ref_to_cam[1:])
+    dev = [torch.from_numpy(imgs[0].numpy().astype(np.float32) / 255.0).cuda(),
+           torch.from_numpy(imgs[2].numpy().astype(np.float32) / 255.0).cuda()]
+    gt = torch.from_numpy(rng.numpy().astype(np.float32)).cuda()
+    true = rig.ref_to_cam[0]
+    r = np.random.default_rng(0)
+    ax = r.normal(size=3)
+    tv = r.normal(size=3)
+    xi0 = np.concatenate([ax / np.linalg.norm(ax) * math.radians(0.5), tv / np.linalg.norm(tv) * 0.02])
+    pose0 = P.se3_exp_left(xi0, true)
+    sw = P.SoftSweep(rig, wl.levels[0], temperature=0.05)
+    poses = refine_extrinsic(sw, dev, gt, pose0, steps=50, lam=0.3, lr=1e-3)
+    errs = [_pose_error(p, true) for p in poses]
+    print("refinement (deg, m):", [(round(a, 3), round(t, 4)) for a, t in errs[::10] + [errs[-1]]])
+    a0, t0 = errs[0]
+    a1, t1 = errs[-1]
+    assert abs(a0 - 0.5) < 1e-6 and t0 > 0.015
+    assert a1 < 0.15 and t1 < 0.008
