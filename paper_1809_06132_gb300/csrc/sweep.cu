@@ -4,9 +4,10 @@
 //   ray_table_kernel   Eq. 1 back-projection of every reference pixel of a
 //                      level, in double precision, stored as float4 (once
 //                      per rig, at psweep_create).
-//   ref_level_kernel   reference image of a level (s x s box mean, or the
-//                      centred crop), centred intensities I/255 - 1/2.
-//   quad_level_kernel  matching image of a level in "quad" layout: entry
+//   ref_stats_kernel   reference image of a level (s x s box mean, or the
+//                      centred crop), centred intensities I/255 - 1/2, and
+//                      its window mean and sum of squared deviations.
+//   quad_level_kernel  matching images of a level in "quad" layout: entry
 //                      (x, y) holds the 2 x 2 neighbourhood used by one
 //                      bilinear sample, so a sample is one 16-byte gather.
 //   sweep_kernel       the hot loop.  One CTA owns a 64 x 24 tile of output
@@ -117,25 +118,61 @@ __global__ void view_angle_kernel(ps_camera c, int W, int H, unsigned* out) {
     atomicMax(out, __float_as_uint(ang));
 }
 
-__global__ void ref_level_kernel(const uint8_t* img, int W, int s, int x0, int y0, int Wl, int Hl, float* out) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y;
+// Reference level image and its window statistics in one pass: a 32 x 8
+// tile of level pixels plus a window halo is formed in shared memory, the
+// tile is written out and each pixel's statistics come from shared memory.
+constexpr int RS_TX = 32, RS_TY = 8, RS_MAXH = 4;
+__global__ void __launch_bounds__(RS_TX * RS_TY) ref_stats_kernel(const uint8_t* img, int W, int s, int x0, int y0,
+                                                                  int Wl, int Hl, int rho, float* ref, float2* stats) {
+    __shared__ float tile[(RS_TY + 2 * RS_MAXH) * (RS_TX + 2 * RS_MAXH)];
+    const int hw = RS_TX + 2 * rho, hh = RS_TY + 2 * rho;
+    const int bx = blockIdx.x * RS_TX - rho, by = blockIdx.y * RS_TY - rho;
+    const int tid = threadIdx.y * RS_TX + threadIdx.x;
+    for (int p = tid; p < hw * hh; p += RS_TX * RS_TY) {
+        int x = bx + p % hw, y = by + p / hw;
+        tile[p] = (x >= 0 && y >= 0 && x < Wl && y < Hl) ? ref_px(img, W, s, x0, y0, Wl, Hl, x, y) : 0.0f;
+    }
+    __syncthreads();
+    const int x = blockIdx.x * RS_TX + threadIdx.x, y = blockIdx.y * RS_TY + threadIdx.y;
     if (x >= Wl || y >= Hl) return;
-    out[(size_t)y * Wl + x] = ref_px(img, W, s, x0, y0, Wl, Hl, x, y);
+    const float* c = tile + (threadIdx.y + rho) * hw + threadIdx.x + rho;
+    ref[(size_t)y * Wl + x] = *c;
+    stats[(size_t)y * Wl + x] = (x >= rho && y >= rho && x < Wl - rho && y < Hl - rho) ? window_stats(c, hw, rho)
+                                                                                      : make_float2(0.f, -1.f);
 }
 
-__global__ void quad_level_kernel(const uint8_t* img, int W, int s, int Wl, int Hl, void* out, int half) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y;
-    if (x >= Wl || y >= Hl) return;
-    quad_px(img, W, s, Wl, Hl, out, half, x, y);
-}
+// Quad images of every matching camera of a level (blockIdx.z = camera).
+// Each thread forms the level pixels (x, y) and (x, y + 1) and takes the
+// (x + 1) column from its lane neighbour, so every level pixel is computed
+// about twice instead of four times.
+struct QuadJobs {
+    const uint8_t* img[PS_MAX_CAMS];
+    void* out[PS_MAX_CAMS];
+    int W[PS_MAX_CAMS], Wl[PS_MAX_CAMS], Hl[PS_MAX_CAMS];
+    int s, half;
+};
 
-__global__ void ref_stats_kernel(const float* ref, int W, int H, int rho, float2* out) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y;
-    if (x >= W || y >= H) return;
-    out[(size_t)y * W + x] = stats_px(ref, W, H, rho, x, y);
+__global__ void __launch_bounds__(128) quad_level_kernel(const __grid_constant__ QuadJobs Q) {
+    const int j = blockIdx.z;
+    const int Wl = Q.Wl[j], Hl = Q.Hl[j];
+    if ((int)(blockIdx.x * blockDim.x) >= Wl || (int)blockIdx.y >= Hl) return;  // whole block outside this camera
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    const uint8_t* img = Q.img[j];
+    const int W = Q.W[j], s = Q.s;
+    float a = level_px(img, W, Wl, Hl, s, x, y), b = level_px(img, W, Wl, Hl, s, x, y + 1);
+    float a1 = __shfl_down_sync(0xffffffffu, a, 1), b1 = __shfl_down_sync(0xffffffffu, b, 1);
+    if ((threadIdx.x & 31) == 31) {
+        a1 = level_px(img, W, Wl, Hl, s, x + 1, y);
+        b1 = level_px(img, W, Wl, Hl, s, x + 1, y + 1);
+    }
+    if (x >= Wl) return;
+    const size_t o = (size_t)y * Wl + x;
+    if (Q.half) {  // FP16 storage: four halves in 8 bytes
+        __half2 p = __floats2half2_rn(a, a1), q = __floats2half2_rn(b, b1);
+        static_cast<uint2*>(Q.out[j])[o] = make_uint2(*reinterpret_cast<unsigned*>(&p), *reinterpret_cast<unsigned*>(&q));
+    } else {
+        static_cast<float4*>(Q.out[j])[o] = make_float4(a, a1, b, b1);
+    }
 }
 
 // Persistent CTAs take work items (a tile and a chunk of its planes) from a
@@ -567,25 +604,28 @@ extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_
         const int l = order[oi];
         const ps_level& L = h->levels[l];
         const int W = h->lW[l], H = h->lH[l];
-        if (L.kind == PS_LEVEL_DOWNSAMPLE) {
-            int sf = L.factor;
-            ref_level_kernel<<<dim3((W + 127) / 128, H), 128, 0, s>>>(images[0], h->ref.width, sf, 0, 0, W, H,
-                                                                       h->ref_img[l]);
+        const bool down = L.kind == PS_LEVEL_DOWNSAMPLE;
+        ref_stats_kernel<<<dim3((W + RS_TX - 1) / RS_TX, (H + RS_TY - 1) / RS_TY), dim3(RS_TX, RS_TY), 0, s>>>(
+            images[0], h->ref.width, down ? L.factor : 0, down ? 0 : h->cx0[l], down ? 0 : h->cy0[l], W, H,
+            L.window / 2, h->ref_img[l], h->stats[l]);
+        {
+            QuadJobs Q;
+            std::memset(&Q, 0, sizeof(Q));
+            int wmax = 0, hmax = 0;
             for (int j = 0; j < h->n_cams; ++j) {
                 const ps_camera& cj = h->lcam[l][j];
-                quad_level_kernel<<<dim3((cj.width + 127) / 128, cj.height), 128, 0, s>>>(
-                    images[1 + j], h->cams[j].width, sf, cj.width, cj.height, h->quad[l][j], h->image_half);
+                Q.img[j] = images[1 + j];
+                Q.out[j] = h->quad[l][j];
+                Q.W[j] = h->cams[j].width;
+                Q.Wl[j] = cj.width;
+                Q.Hl[j] = cj.height;
+                wmax = std::max(wmax, cj.width);
+                hmax = std::max(hmax, cj.height);
             }
-        } else {
-            ref_level_kernel<<<dim3((W + 127) / 128, H), 128, 0, s>>>(images[0], h->ref.width, 0, h->cx0[l],
-                                                                       h->cy0[l], W, H, h->ref_img[l]);
-            for (int j = 0; j < h->n_cams; ++j) {
-                const ps_camera& cj = h->lcam[l][j];
-                quad_level_kernel<<<dim3((cj.width + 127) / 128, cj.height), 128, 0, s>>>(
-                    images[1 + j], h->cams[j].width, 1, cj.width, cj.height, h->quad[l][j], h->image_half);
-            }
+            Q.s = down ? L.factor : 1;
+            Q.half = h->image_half;
+            quad_level_kernel<<<dim3((wmax + 127) / 128, hmax, h->n_cams), 128, 0, s>>>(Q);
         }
-        ref_stats_kernel<<<dim3((W + 127) / 128, H), 128, 0, s>>>(h->ref_img[l], W, H, L.window / 2, h->stats[l]);
         LevelD& D = P.lv[oi];
         fill_level(h, l, TH_SINGLE, h->chunk[l], D);
         D.partial = h->partial[l];

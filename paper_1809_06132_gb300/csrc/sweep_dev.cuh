@@ -70,14 +70,30 @@ struct SweepParams {
 
 // ------------------------------------------------------------- level images
 
-// Centred intensity of the s x s block at level pixel (x, y), clamped to the image.
+// Centred intensity of the s x s block at level pixel (x, y), clamped to the
+// image.  Blocks of 2 or 4 bytes per row are read as one 2- or 4-byte word
+// when the image base allows it (the integer sum is the same either way).
 __device__ __forceinline__ float level_px(const uint8_t* img, int W, int Wl, int Hl, int s, int x, int y) {
     x = min(x, Wl - 1);
     y = min(y, Hl - 1);
     int acc = 0;
-    for (int dy = 0; dy < s; ++dy)
-        for (int dx = 0; dx < s; ++dx) acc += img[(size_t)(s * y + dy) * W + (s * x + dx)];
-    return (float)acc * (1.0f / (255.0f * s * s)) - 0.5f;
+    const bool words = ((reinterpret_cast<uintptr_t>(img) | (uintptr_t)W) & (uintptr_t)(s - 1)) == 0;
+    if (s == 4 && words) {
+        for (int dy = 0; dy < 4; ++dy) {
+            unsigned v = *reinterpret_cast<const unsigned*>(img + (size_t)(4 * y + dy) * W + 4 * x);
+            acc += (int)((v & 0xffu) + ((v >> 8) & 0xffu) + ((v >> 16) & 0xffu) + (v >> 24));
+        }
+    } else if (s == 2 && words) {
+        for (int dy = 0; dy < 2; ++dy) {
+            unsigned short v = *reinterpret_cast<const unsigned short*>(img + (size_t)(2 * y + dy) * W + 2 * x);
+            acc += (int)((v & 0xffu) + (v >> 8));
+        }
+    } else {
+        for (int dy = 0; dy < s; ++dy)
+            for (int dx = 0; dx < s; ++dx) acc += img[(size_t)(s * y + dy) * W + (s * x + dx)];
+    }
+    // one explicit rounding, whatever the calling kernel lets the compiler contract
+    return __fmaf_rn((float)acc, 1.0f / (255.0f * (float)(s * s)), -0.5f);
 }
 
 // Reference intensity at level pixel (x, y): the s x s block mean (s > 0), or
@@ -85,7 +101,7 @@ __device__ __forceinline__ float level_px(const uint8_t* img, int W, int Wl, int
 __device__ __forceinline__ float ref_px(const uint8_t* img, int W, int s, int x0, int y0, int Wl, int Hl, int x,
                                         int y) {
     if (s > 0) return level_px(img, W, Wl, Hl, s, x, y);
-    return img[(size_t)(y0 + y) * W + (x0 + x)] * (1.0f / 255.0f) - 0.5f;
+    return __fmaf_rn((float)img[(size_t)(y0 + y) * W + (x0 + x)], 1.0f / 255.0f, -0.5f);
 }
 
 // Matching image of a level in "quad" layout: entry (x, y) holds the
@@ -107,25 +123,28 @@ __device__ __forceinline__ void quad_px(const uint8_t* img, int W, int s, int Wl
     }
 }
 
+// Mean and sum of squared deviations of the window of radius rho centred on
+// base[0] (row stride `stride`), by the two-pass direct sums.
+__device__ __forceinline__ float2 window_stats(const float* base, int stride, int rho) {
+    float s = 0.f;
+    for (int dy = -rho; dy <= rho; ++dy)
+        for (int dx = -rho; dx <= rho; ++dx) s += base[dy * stride + dx];
+    float m = s / (float)((2 * rho + 1) * (2 * rho + 1));
+    float v = 0.f;
+    for (int dy = -rho; dy <= rho; ++dy)
+        for (int dx = -rho; dx <= rho; ++dx) {
+            float e = base[dy * stride + dx] - m;
+            v = fmaf(e, e, v);
+        }
+    return make_float2(m, v);
+}
+
 // Mean and sum of squared deviations of the reference window around level
-// pixel (x, y) (two-pass, direct sums); var = -1 where the window leaves the
-// image.  Computed once per frame, read by the sweep for every plane.
+// pixel (x, y); var = -1 where the window leaves the image.  Computed once
+// per frame, read by the sweep for every plane.
 __device__ __forceinline__ float2 stats_px(const float* ref, int W, int H, int rho, int x, int y) {
-    float2 o = make_float2(0.f, -1.f);
-    if (x >= rho && y >= rho && x < W - rho && y < H - rho) {
-        float s = 0.f;
-        for (int dy = -rho; dy <= rho; ++dy)
-            for (int dx = -rho; dx <= rho; ++dx) s += ref[(size_t)(y + dy) * W + x + dx];
-        float m = s / (float)((2 * rho + 1) * (2 * rho + 1));
-        float v = 0.f;
-        for (int dy = -rho; dy <= rho; ++dy)
-            for (int dx = -rho; dx <= rho; ++dx) {
-                float e = ref[(size_t)(y + dy) * W + x + dx] - m;
-                v = fmaf(e, e, v);
-            }
-        o = make_float2(m, v);
-    }
-    return o;
+    if (x >= rho && y >= rho && x < W - rho && y < H - rho) return window_stats(ref + (size_t)y * W + x, W, rho);
+    return make_float2(0.f, -1.f);
 }
 
 // ------------------------------------------------------------- sweep
