@@ -45,6 +45,9 @@ UNIT = "frames/s"
 FLOP_PER_UNIT = 92
 # TSDF integration: each voxel of a listed block is read and written once ({D, w} float32 pairs)
 BYTES_PER_VOXEL = 16
+# dram__bytes_read.sum + dram__bytes_write.sum of one sweep_kernel launch on the street frame (FP32 images),
+# from an ncu capture of the current kernel (28.2 MB read + 7.8 MB written)
+SWEEP_DRAM_BYTES_STREET = 35_983_872
 
 
 def parse():
@@ -407,7 +410,8 @@ def run_ours(args):
                                "visible": tsdf_ms[2] / max(1, n_ts), "integrate": integ_ms},
                  "blocks_allocated": n_blocks, "status": st},
         "roofline": {"kernel": "sweep_kernel", "bound": "alu", "achieved": achieved, "peak": peak_tflops,
-                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                     "traffic": SWEEP_DRAM_BYTES_STREET if args.config == "street" and not args.half else None,
                      "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 (FMA) x {sm_max:.0f} MHz "
                                     f"(max SM clock, {'sampled' if clk.get('sm_max_mhz') else 'recipe'})",
                      "flop_per_unit": FLOP_PER_UNIT, "units_per_launch": units},
