@@ -33,7 +33,6 @@ namespace {
 
 constexpr int DT = 16;                 // output tile edge
 constexpr int DNT = DT * DT;           // threads per CTA
-constexpr int DMAX_HALO = DT + 2 * 4;  // halo edge for the widest window (9 x 9)
 
 struct DiffCam {
     float R[9], t[3];
@@ -122,19 +121,27 @@ __device__ __forceinline__ Warp warp_at(const DiffP& P, const DiffCam& C, const 
     return o;
 }
 
-// Two-pass ZNCC of the pixel's window: reference samples R (halo layout),
-// warped samples Wv.  False when a sample is invalid or a window is flat.
+// Two-pass ZNCC of the pixel's window: reference samples R and warped
+// samples Wv in the halo layout (row stride DS).  False when a sample is
+// invalid or a window is flat.
 struct Zn {
     float z, ma, mb, va, vb, sab;
 };
 
-__device__ __forceinline__ bool window_zncc(const float* R, const float* Wv, int hw, int lx, int ly, int rho, Zn* o) {
-    const int N = (2 * rho + 1) * (2 * rho + 1);
+// Shared-memory row stride of the halo buffers: 48 = 16 (mod 32), so the two
+// output rows of a warp (16 pixels each) read disjoint banks.
+constexpr int DS = 48;
+
+template <int RHO>
+__device__ __forceinline__ bool window_zncc(const float* R, const float* Wv, int lx, int ly, Zn* o) {
+    constexpr int N = (2 * RHO + 1) * (2 * RHO + 1);
     float sa = 0.f, sb = 0.f;
     bool ok = true;
-    for (int dy = 0; dy <= 2 * rho; ++dy)
-        for (int dx = 0; dx <= 2 * rho; ++dx) {
-            int q = (ly + dy) * hw + lx + dx;
+#pragma unroll
+    for (int dy = 0; dy <= 2 * RHO; ++dy)
+#pragma unroll
+        for (int dx = 0; dx <= 2 * RHO; ++dx) {
+            const int q = (ly + dy) * DS + lx + dx;
             float b = Wv[q];
             ok &= !isnan(b);
             sa += R[q];
@@ -143,9 +150,11 @@ __device__ __forceinline__ bool window_zncc(const float* R, const float* Wv, int
     if (!ok) return false;
     float ma = sa / (float)N, mb = sb / (float)N;
     float cov = 0.f, va = 0.f, vb = 0.f;
-    for (int dy = 0; dy <= 2 * rho; ++dy)
-        for (int dx = 0; dx <= 2 * rho; ++dx) {
-            int q = (ly + dy) * hw + lx + dx;
+#pragma unroll
+    for (int dy = 0; dy <= 2 * RHO; ++dy)
+#pragma unroll
+        for (int dx = 0; dx <= 2 * RHO; ++dx) {
+            const int q = (ly + dy) * DS + lx + dx;
             float ea = R[q] - ma, eb = Wv[q] - mb;
             cov = fmaf(ea, eb, cov);
             va = fmaf(ea, ea, va);
@@ -161,25 +170,22 @@ __device__ __forceinline__ bool window_zncc(const float* R, const float* Wv, int
     return true;
 }
 
-__device__ __forceinline__ bool pixel_inside(const DiffP& P, int gx, int gy) {
-    return gx >= P.rho && gy >= P.rho && gx < P.W - P.rho && gy < P.H - P.rho;
-}
-
+template <int RHO>
 __global__ void __launch_bounds__(DNT) soft_fwd_kernel(const __grid_constant__ DiffP P, float* range, float* cost,
                                                       float* aux) {
-    __shared__ float Rs[DMAX_HALO * DMAX_HALO];
-    __shared__ float Ws[DMAX_HALO * DMAX_HALO];
-    const int hw = DT + 2 * P.rho, npos = hw * hw;
+    constexpr int HW = DT + 2 * RHO, NPOS = HW * HW;
+    __shared__ float Rs[HW * DS];
+    __shared__ float Ws[HW * DS];
     const int tid = threadIdx.x, lx = tid % DT, ly = tid / DT;
-    const int x0 = blockIdx.x * DT - P.rho, y0 = blockIdx.y * DT - P.rho;
+    const int x0 = blockIdx.x * DT - RHO, y0 = blockIdx.y * DT - RHO;
     const int gx = blockIdx.x * DT + lx, gy = blockIdx.y * DT + ly;
-    for (int p = tid; p < npos; p += DNT) {
-        int hx = x0 + p % hw, hy = y0 + p / hw;
-        Rs[p] = (hx >= 0 && hy >= 0 && hx < P.W && hy < P.H) ? P.ref[(size_t)hy * P.W + hx] : 0.0f;
+    for (int p = tid; p < NPOS; p += DNT) {
+        const int hx = p % HW, hy = p / HW, x = x0 + hx, y = y0 + hy;
+        Rs[hy * DS + hx] = (x >= 0 && y >= 0 && x < P.W && y < P.H) ? P.ref[(size_t)y * P.W + x] : 0.0f;
     }
     const bool in = gx < P.W && gy < P.H;
     float4 ray = in ? P.rays[(size_t)gy * P.W + gx] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const bool use = in && pixel_inside(P, gx, gy) && !isnan(ray.x);
+    const bool use = in && gx >= RHO && gy >= RHO && gx < P.W - RHO && gy < P.H - RHO && !isnan(ray.x);
     const float inf = __int_as_float(0x7f800000);
     float cmin = inf, Z = 0.f, Nr = 0.f;
     for (int k = 0; k < P.K; ++k) {
@@ -187,10 +193,13 @@ __global__ void __launch_bounds__(DNT) soft_fwd_kernel(const __grid_constant__ D
         float best = inf;
         for (int j = 0; j < P.n_cams; ++j) {
             __syncthreads();
-            for (int p = tid; p < npos; p += DNT) Ws[p] = warp_at(P, P.cams[j], pl, x0 + p % hw, y0 + p / hw).w;
+            for (int p = tid; p < NPOS; p += DNT) {
+                const int hx = p % HW, hy = p / HW;
+                Ws[hy * DS + hx] = warp_at(P, P.cams[j], pl, x0 + hx, y0 + hy).w;
+            }
             __syncthreads();
             Zn zn;
-            if (use && window_zncc(Rs, Ws, hw, lx, ly, P.rho, &zn)) {
+            if (use && window_zncc<RHO>(Rs, Ws, lx, ly, &zn)) {
                 float c = 0.5f * (1.0f - zn.z);
                 if (c < best) best = c;
             }
@@ -220,25 +229,28 @@ __global__ void __launch_bounds__(DNT) soft_fwd_kernel(const __grid_constant__ D
     }
 }
 
+struct GradOut {
+    float* cam[PS_MAX_CAMS];
+};
+
+template <int RHO>
 __global__ void __launch_bounds__(DNT) soft_bwd_kernel(const __grid_constant__ DiffP P, const float* aux,
                                                       const float* g_range, const float* g_cost, float* g_ref,
-                                                      float* g_cam0, float* g_cam1, float* g_cam2, float* g_cam3,
-                                                      double* g_pose) {
+                                                      const __grid_constant__ GradOut G, double* g_pose) {
+    constexpr int HW = DT + 2 * RHO, NPOS = HW * HW, BUF = HW * DS;
     extern __shared__ float sm[];
-    const int hw = DT + 2 * P.rho, npos = hw * hw;
-    float* Rs = sm;                           // [npos] reference
-    float* gR = Rs + npos;                    // [npos] dL/dref, summed over planes
-    float* Ws = gR + npos;                    // [n_cams][npos] warped samples of the current plane
-    float* gW = Ws + P.n_cams * npos;         // [n_cams][npos] dL/dw of the current plane
+    float* Rs = sm;                   // reference
+    float* gR = Rs + BUF;             // dL/dref, summed over planes
+    float* Ws = gR + BUF;             // [n_cams] warped samples of the current plane
+    float* gW = Ws + P.n_cams * BUF;  // [n_cams] dL/dw of the current plane
     __shared__ float red[DNT / 32][6 * PS_MAX_CAMS];
-    float* g_cam[PS_MAX_CAMS] = {g_cam0, g_cam1, g_cam2, g_cam3};
     const int tid = threadIdx.x, lx = tid % DT, ly = tid / DT;
-    const int x0 = blockIdx.x * DT - P.rho, y0 = blockIdx.y * DT - P.rho;
+    const int x0 = blockIdx.x * DT - RHO, y0 = blockIdx.y * DT - RHO;
     const int gx = blockIdx.x * DT + lx, gy = blockIdx.y * DT + ly;
-    for (int p = tid; p < npos; p += DNT) {
-        int hx = x0 + p % hw, hy = y0 + p / hw;
-        Rs[p] = (hx >= 0 && hy >= 0 && hx < P.W && hy < P.H) ? P.ref[(size_t)hy * P.W + hx] : 0.0f;
-        gR[p] = 0.f;
+    for (int p = tid; p < NPOS; p += DNT) {
+        const int hx = p % HW, hy = p / HW, x = x0 + hx, y = y0 + hy;
+        Rs[hy * DS + hx] = (x >= 0 && y >= 0 && x < P.W && y < P.H) ? P.ref[(size_t)y * P.W + x] : 0.0f;
+        gR[hy * DS + hx] = 0.f;
     }
     const bool in = gx < P.W && gy < P.H;
     const size_t o = in ? (size_t)gy * P.W + gx : 0;
@@ -252,18 +264,22 @@ __global__ void __launch_bounds__(DNT) soft_bwd_kernel(const __grid_constant__ D
         gr = g_range ? g_range[o] : 0.f;
         gs = g_cost ? g_cost[o] : 0.f;
     }
-    const bool use = in && pixel_inside(P, gx, gy) && !isnan(ray.x) && cmin < inf && (gr != 0.f || gs != 0.f);
+    const bool use = in && gx >= RHO && gy >= RHO && gx < P.W - RHO && gy < P.H - RHO && !isnan(ray.x) &&
+                     cmin < inf && (gr != 0.f || gs != 0.f);
     const float gE = use ? -gr / (E * E) : 0.f;
     float pose_acc[6 * PS_MAX_CAMS];
+#pragma unroll
     for (int i = 0; i < 6 * PS_MAX_CAMS; ++i) pose_acc[i] = 0.f;
     for (int k = 0; k < P.K; ++k) {
         const PlaneD pl = P.planes[k];
         __syncthreads();
-        for (int p = tid; p < npos; p += DNT)
+        for (int p = tid; p < NPOS; p += DNT) {
+            const int hx = p % HW, hy = p / HW;
             for (int j = 0; j < P.n_cams; ++j) {
-                Ws[j * npos + p] = warp_at(P, P.cams[j], pl, x0 + p % hw, y0 + p / hw).w;
-                gW[j * npos + p] = 0.f;
+                Ws[j * BUF + hy * DS + hx] = warp_at(P, P.cams[j], pl, x0 + hx, y0 + hy).w;
+                gW[j * BUF + hy * DS + hx] = 0.f;
             }
+        }
         __syncthreads();
         // the pixel's cost for this plane (as in the forward) and its camera
         float best = inf;
@@ -271,7 +287,7 @@ __global__ void __launch_bounds__(DNT) soft_bwd_kernel(const __grid_constant__ D
         Zn zb;
         for (int j = 0; use && j < P.n_cams; ++j) {
             Zn zn;
-            if (window_zncc(Rs, Ws + j * npos, hw, lx, ly, P.rho, &zn)) {
+            if (window_zncc<RHO>(Rs, Ws + j * BUF, lx, ly, &zn)) {
                 float c = 0.5f * (1.0f - zn.z);
                 if (c < best) {
                     best = c;
@@ -285,24 +301,30 @@ __global__ void __launch_bounds__(DNT) soft_bwd_kernel(const __grid_constant__ D
             const float rho_k = (pl.nx * ray.x + pl.ny * ray.y + pl.nz * ray.z) / pl.d;
             const float gC = gE * (-s * (rho_k - E) / P.T) + gs * s;
             const float gz = -0.5f * gC;
-            const float* Wj = Ws + jb * npos;
-            float* gWj = gW + jb * npos;
-            for (int dy = 0; dy <= 2 * P.rho; ++dy)
-                for (int dx = 0; dx <= 2 * P.rho; ++dx) {
-                    int q = (ly + dy) * hw + lx + dx;
+            const float* Wj = Ws + jb * BUF;
+            float* gWj = gW + jb * BUF;
+            const float ka = gz / zb.sab, kz_a = gz * zb.z / zb.va, kz_b = gz * zb.z / zb.vb;
+#pragma unroll
+            for (int dy = 0; dy <= 2 * RHO; ++dy)
+#pragma unroll
+                for (int dx = 0; dx <= 2 * RHO; ++dx) {
+                    const int q = (ly + dy) * DS + lx + dx;
                     float ea = Rs[q] - zb.ma, eb = Wj[q] - zb.mb;
-                    atomicAdd(&gR[q], gz * (eb / zb.sab - zb.z * ea / zb.va));
-                    atomicAdd(&gWj[q], gz * (ea / zb.sab - zb.z * eb / zb.vb));
+                    atomicAdd(&gR[q], fmaf(ka, eb, -kz_a * ea));
+                    atomicAdd(&gWj[q], fmaf(ka, ea, -kz_b * eb));
                 }
         }
         __syncthreads();
         // chain dL/dw of every warped halo sample to the image and the pose
-        for (int p = tid; p < npos; p += DNT)
-            for (int j = 0; j < P.n_cams; ++j) {
-                const float gw = gW[j * npos + p];
+        for (int p = tid; p < NPOS; p += DNT) {
+            const int hx = p % HW, hy = p / HW;
+#pragma unroll
+            for (int j = 0; j < PS_MAX_CAMS; ++j) {
+                if (j >= P.n_cams) break;
+                const float gw = gW[j * BUF + hy * DS + hx];
                 if (gw == 0.f) continue;
                 const DiffCam& C = P.cams[j];
-                Warp wp = warp_at(P, C, pl, x0 + p % hw, y0 + p / hw);
+                Warp wp = warp_at(P, C, pl, x0 + hx, y0 + hy);
                 int xa = (int)floorf(wp.u), ya = (int)floorf(wp.v);
                 int xb = min(xa + 1, C.c.width - 1), yb = min(ya + 1, C.c.height - 1);
                 float ax = wp.u - (float)xa, ay = wp.v - (float)ya;
@@ -310,37 +332,40 @@ __global__ void __launch_bounds__(DNT) soft_bwd_kernel(const __grid_constant__ D
                 const int Wc = C.c.width;
                 float i00 = I[(size_t)ya * Wc + xa], i10 = I[(size_t)ya * Wc + xb];
                 float i01 = I[(size_t)yb * Wc + xa], i11 = I[(size_t)yb * Wc + xb];
-                if (g_cam[j]) {
-                    float* G = g_cam[j];
-                    atomicAdd(&G[(size_t)ya * Wc + xa], gw * (1.f - ax) * (1.f - ay));
-                    atomicAdd(&G[(size_t)ya * Wc + xb], gw * ax * (1.f - ay));
-                    atomicAdd(&G[(size_t)yb * Wc + xa], gw * (1.f - ax) * ay);
-                    atomicAdd(&G[(size_t)yb * Wc + xb], gw * ax * ay);
+                if (G.cam[j]) {
+                    float* Gj = G.cam[j];
+                    atomicAdd(&Gj[(size_t)ya * Wc + xa], gw * (1.f - ax) * (1.f - ay));
+                    atomicAdd(&Gj[(size_t)ya * Wc + xb], gw * ax * (1.f - ay));
+                    atomicAdd(&Gj[(size_t)yb * Wc + xa], gw * (1.f - ax) * ay);
+                    atomicAdd(&Gj[(size_t)yb * Wc + xb], gw * ax * ay);
                 }
                 float dwdu = (1.f - ay) * (i10 - i00) + ay * (i11 - i01);
                 float dwdv = (1.f - ax) * (i01 - i00) + ax * (i11 - i10);
                 float J[6];
                 project_jac_f(C.c, wp.X, wp.Y, wp.Z, J);
                 float gx3[3];
+#pragma unroll
                 for (int i = 0; i < 3; ++i) gx3[i] = gw * (dwdu * J[i] + dwdv * J[3 + i]);
-                float* acc = pose_acc + 6 * j;
-                acc[0] += wp.Y * gx3[2] - wp.Z * gx3[1];
-                acc[1] += wp.Z * gx3[0] - wp.X * gx3[2];
-                acc[2] += wp.X * gx3[1] - wp.Y * gx3[0];
-                acc[3] += gx3[0];
-                acc[4] += gx3[1];
-                acc[5] += gx3[2];
+                pose_acc[6 * j + 0] += wp.Y * gx3[2] - wp.Z * gx3[1];
+                pose_acc[6 * j + 1] += wp.Z * gx3[0] - wp.X * gx3[2];
+                pose_acc[6 * j + 2] += wp.X * gx3[1] - wp.Y * gx3[0];
+                pose_acc[6 * j + 3] += gx3[0];
+                pose_acc[6 * j + 4] += gx3[1];
+                pose_acc[6 * j + 5] += gx3[2];
             }
+        }
     }
     __syncthreads();
     if (g_ref)
-        for (int p = tid; p < npos; p += DNT) {
-            float g = gR[p];
-            if (g != 0.f) atomicAdd(&g_ref[(size_t)(y0 + p / hw) * P.W + (x0 + p % hw)], g);
+        for (int p = tid; p < NPOS; p += DNT) {
+            const int hx = p % HW, hy = p / HW;
+            float g = gR[hy * DS + hx];
+            if (g != 0.f) atomicAdd(&g_ref[(size_t)(y0 + hy) * P.W + (x0 + hx)], g);
         }
     if (g_pose) {
         const int lane = tid & 31, wid = tid >> 5;
-        for (int i = 0; i < 6 * P.n_cams; ++i) {
+#pragma unroll
+        for (int i = 0; i < 6 * PS_MAX_CAMS; ++i) {
             float v = pose_acc[i];
             for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
             if (lane == 0) red[wid][i] = v;
@@ -476,7 +501,13 @@ extern "C" int psdiff_forward(psdiff_t* h, const float* const* images, const ps_
     int st = fill_params(h, images, ref_to_cam, P);
     if (st) return st;
     dim3 grid((P.W + DT - 1) / DT, (P.H + DT - 1) / DT);
-    soft_fwd_kernel<<<grid, DNT, 0, (cudaStream_t)stream>>>(P, range, cost, aux);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (P.rho == 2)
+        soft_fwd_kernel<2><<<grid, DNT, 0, s>>>(P, range, cost, aux);
+    else if (P.rho == 3)
+        soft_fwd_kernel<3><<<grid, DNT, 0, s>>>(P, range, cost, aux);
+    else
+        soft_fwd_kernel<4><<<grid, DNT, 0, s>>>(P, range, cost, aux);
     PS_CUDA(cudaGetLastError());
     return PS_OK;
 }
@@ -489,14 +520,19 @@ extern "C" int psdiff_backward(psdiff_t* h, const float* const* images, const ps
     DiffP P;
     int st = fill_params(h, images, ref_to_cam, P);
     if (st) return st;
-    float* gi[1 + PS_MAX_CAMS] = {};
-    if (g_images)
-        for (int i = 0; i <= h->n_cams; ++i) gi[i] = g_images[i];
-    const int hw = DT + 2 * P.rho;
-    const size_t smem = sizeof(float) * (size_t)hw * hw * (2 + 2 * P.n_cams);  // at most 23 KB
-    dim3 grid((P.W + DT - 1) / DT, (P.H + DT - 1) / DT);
-    soft_bwd_kernel<<<grid, DNT, smem, (cudaStream_t)stream>>>(P, aux, g_range, g_cost, gi[0], gi[1], gi[2], gi[3],
-                                                               gi[4], g_pose);
+    float* g_ref = g_images ? g_images[0] : nullptr;
+    GradOut G;
+    for (int j = 0; j < PS_MAX_CAMS; ++j) G.cam[j] = (g_images && j < h->n_cams) ? g_images[1 + j] : nullptr;
+    const int hw = 16 + 2 * P.rho;
+    const size_t smem = sizeof(float) * (size_t)hw * 48 * (2 + 2 * P.n_cams);  // at most 46 KB
+    dim3 grid((P.W + 15) / 16, (P.H + 15) / 16);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (P.rho == 2)
+        soft_bwd_kernel<2><<<grid, DNT, smem, s>>>(P, aux, g_range, g_cost, g_ref, G, g_pose);
+    else if (P.rho == 3)
+        soft_bwd_kernel<3><<<grid, DNT, smem, s>>>(P, aux, g_range, g_cost, g_ref, G, g_pose);
+    else
+        soft_bwd_kernel<4><<<grid, DNT, smem, s>>>(P, aux, g_range, g_cost, g_ref, G, g_pose);
     PS_CUDA(cudaGetLastError());
     return PS_OK;
 }
