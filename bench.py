@@ -81,6 +81,23 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(values, device="cpu"):
+    """Each value's maximum over the ranks of the job (the job ends when its
+    slowest rank does); the values themselves when there is one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def rank_seed(seed: int, rank: int) -> int:
+    """Seed of a rank's independent sequence (replicas: no data exchange)."""
+    return seed + rank
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -264,7 +281,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     peaks, peaks_src = load_peaks()
 
-    wl = workload(args, args.seed + rank)
+    wl = workload(args, rank_seed(args.seed, rank))
     n_total = args.warmup + args.steps
     nf = min(n_total, 100 if args.config == "street" else 40)
     t_r = time.time()
@@ -311,10 +328,7 @@ def run_ours(args):
     sweep_ms, n_sw = sw.profile_read()
     tsdf_ms, n_ts = T.profile_read()
     st = T.status(stream)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks([ms], dev)[0]
     ms_per_step = ms / args.steps
     value = world * args.steps / (ms / 1e3)
     n_blocks = T.count(stream)
@@ -367,10 +381,7 @@ def run_ours(args):
     pipe_ms = (time.perf_counter() - ts) * 1e3
     assert T3.status() == P.PS_OK
     pipe.close()
-    if world > 1:
-        t = torch.tensor([e2e_ms, pipe_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms, pipe_ms = (float(v) for v in t.tolist())
+    e2e_ms, pipe_ms = max_over_ranks([e2e_ms, pipe_ms], dev)
     clocks.stop()
     clk = clocks.summary(t0, t1)
     if not clk.get("samples"):
@@ -449,7 +460,7 @@ def run_batch(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    wls = scenes.batch_mix(args.seed + rank, n=args.batch_size)
+    wls = scenes.batch_mix(rank_seed(args.seed, rank), n=args.batch_size)
     t_r = time.time()
     images, boxes, host_imgs = [], [], []
     for wl in wls:
@@ -544,11 +555,7 @@ def run_batch(args):
     clk = clocks.summary(t0, t1)
     if not clk.get("samples"):
         clk = clocks.summary()
-    batch_ms = statistics.median(ms)
-    if world > 1:
-        t = torch.tensor([batch_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        batch_ms = float(t.item())
+    batch_ms = max_over_ranks([statistics.median(ms)], dev)[0]
     all_lat = sorted(x for step in lat for x in step)
     pct = lambda q: all_lat[min(len(all_lat) - 1, int(q * len(all_lat)))]  # noqa: E731
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
