@@ -61,3 +61,51 @@ def test_oracle_depth_fused_like_oracle():
     s = tsdf_compare(ok, oD, oW, oamb, k.cpu().numpy(), D.cpu().numpy(), W.cpu().numpy())
     assert s["n_updated"] > 1000
     assert s["D_abs_max"] <= TSDF_ABS and s["W_mismatch"] == 0, s
+
+
+def _sorted_map(T):
+    k, D, W = T.extract()
+    k, D, W = k.cpu().numpy(), D.cpu().numpy(), W.cpu().numpy()
+    o = np.lexsort((k[:, 2], k[:, 1], k[:, 0]))
+    return k[o], D[o], W[o]
+
+
+def test_tsdf_fusion_is_deterministic():
+    # every voxel is updated by one thread: two maps fed the same frames are bit-identical
+    wl = scenes.street(2, n_frames=4, scale=0.25)
+    src = scenes.FrameSource(wl, device="cuda")
+    A, B = P.Tsdf(wl.tsdf, wl.rig.ref), P.Tsdf(wl.tsdf, wl.rig.ref)
+    for f in range(4):
+        _, rng = src.frame(f, with_range=True)
+        d = torch.from_numpy(rng.numpy().astype(np.float32)).cuda()
+        for T in (A, B):
+            T.integrate(d, wl.world_to_ref[f], wl.local_center(f))
+    a, b = _sorted_map(A), _sorted_map(B)
+    assert len(a[0]) > 100
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+def test_hundred_frame_street_trajectory():
+    # the whole path over the 100-frame trajectory: estimated depth against the
+    # renderer's true range, fusion status and the local-map-bounded block count
+    wl = scenes.street(0, n_frames=100, scale=0.25)
+    src = scenes.FrameSource(wl, device="cuda")
+    sw = P.Sweep(wl.rig, wl.levels, filters=scenes.Filters())
+    T = P.Tsdf(wl.tsdf, wl.rig.ref)
+    rels, counts = [], []
+    for f in range(100):
+        imgs, rng = src.frame(f, with_range=True)
+        dev = [torch.from_numpy(i.numpy()).cuda() for i in imgs]
+        depth = sw.depth(dev, boxes=wl.boxes[f])
+        T.integrate(depth, wl.world_to_ref[f], wl.local_center(f))
+        if f % 10 == 9:
+            d = depth.cpu().numpy()
+            gt = rng.numpy()
+            v = (d > 0) & (gt > 0)
+            assert v.mean() > 0.1, f
+            rels.append(float(np.median(np.abs(d[v] - gt[v]) / gt[v])))
+            assert T.status() == P.PS_OK, f
+            counts.append(T.count())
+    print("median relative depth error per 10 frames", [round(r, 4) for r in rels], "blocks", counts)
+    assert max(rels) < 0.05
+    assert counts == sorted(counts) and 0 < counts[-1] < wl.tsdf.pool_blocks
