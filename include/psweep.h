@@ -483,6 +483,18 @@ int tsdf_dense_fuse_backward(const float* voxels_in, const int32_t* dims, const 
                              const ps_pose* world_to_cam, const float* g_D_out, float* g_D_in, float* g_depth,
                              double* g_pose, void* stream);
 
+/* Checked build (libpsweep_check.so, compiled with -DPS_CHECK; there is no
+ * sanitizer on every machine this runs on): the kernels test the accesses
+ * whose addresses come from data (image gathers at projected coordinates,
+ * pixel indices, voxel-block pool slots from the hash table, work items of
+ * the persistent queues), skip a failing access and record a bit:
+ * 1 gather outside the image, 2 pixel outside the image, 4 pool slot outside
+ * the pool, 8 work item outside its level or queue.  ps_check_read
+ * synchronises the device and returns (and clears) the bits recorded since
+ * the last read; in the normal build it always returns 0 bits, and
+ * ps_version says which build is loaded. */
+int ps_check_read(uint32_t* bits);
+
 /* Message for the calling thread's last non-zero status ("" if none). */
 const char* ps_last_error(void);
 

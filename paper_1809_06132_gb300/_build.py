@@ -14,6 +14,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpsweep.so")
+# checked build: bounds checks at data-dependent accesses (see PS_CHECK in csrc/internal.cuh)
+BUILD_CHECK = os.path.join(HERE, "_build_check")
+LIB_CHECK = os.path.join(BUILD_CHECK, "libpsweep_check.so")
 SOURCES = ["common.cu", "sweep.cu", "tsdf.cu", "batch.cu", "batch_k16.cu", "batch_k24.cu", "pipe.cu", "diff.cu"]
 HEADERS = ["internal.cuh", "sweep_dev.cuh", "batch_dev.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -32,17 +35,20 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, check: bool = False) -> str:
+    """Compile libpsweep.so (or, with check, the bounds-checked libpsweep_check.so)."""
+    out_dir, lib = (BUILD_CHECK, LIB_CHECK) if check else (BUILD, LIB)
+    flags = FLAGS + (["-DPS_CHECK"] if check else [])
+    os.makedirs(out_dir, exist_ok=True)
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "psweep.h")]
     objs = []
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(out_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
-            jobs.append([_nvcc(), *ARCH, *FLAGS, "-c", s, "-o", o])
+            jobs.append([_nvcc(), *ARCH, *flags, "-c", s, "-o", o])
 
     def run(cmd):
         if verbose:
@@ -51,11 +57,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".{os.getpid()}.tmp"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".{os.getpid()}.tmp"
         run([_nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

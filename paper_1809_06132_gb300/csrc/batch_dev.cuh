@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(NT, 1) batch_kernel(const __grid_constant__ Ba
         } else if (kind == Q_REF || kind == Q_STATS) {
             const PrepD& P = J.prep[lvl];
             const int y0 = idx * PREP_ROWS, n = min(PREP_ROWS, P.Hl - y0) * P.Wl;
+            (void)PS_DCHECK(y0 >= 0 && y0 < P.Hl, CHK_ITEM);
             for (int i = tid; i < n; i += NT) {
                 const int y = y0 + i / P.Wl, x = i % P.Wl;
                 if (kind == Q_REF)
@@ -190,6 +191,7 @@ __global__ void __launch_bounds__(NT, 1) batch_kernel(const __grid_constant__ Ba
             const PrepD& P = J.prep[lvl];
             const int Wl = P.cam_Wl[cam], Hl = P.cam_Hl[cam];
             const int y0 = idx * PREP_ROWS, n = min(PREP_ROWS, Hl - y0) * Wl;
+            (void)PS_DCHECK(y0 >= 0 && y0 < Hl && cam < J.n_cams, CHK_ITEM);
             for (int i = tid; i < n; i += NT)
                 quad_px(io.img[1 + cam], J.cam_w[cam], P.cam_s, Wl, Hl, P.quad[cam], J.image_half, i % Wl,
                         y0 + i / Wl);
@@ -197,6 +199,7 @@ __global__ void __launch_bounds__(NT, 1) batch_kernel(const __grid_constant__ Ba
         } else {  // Q_MERGE or Q_CONT
             const int W = J.M.W, H = J.M.H;
             const int y0 = idx * MERGE_ROWS, n = min(MERGE_ROWS, H - y0) * W;
+            (void)PS_DCHECK(y0 >= 0 && y0 < H, CHK_ITEM);
             const ps_box* bx = A.boxes + io.box0;
             const bool last = kind == Q_CONT || !J.filter;  // this pass writes the output
             for (int i = tid; i < n; i += NT) {

@@ -9,3 +9,7 @@ const void* batch_kernel_th16(int kp) {
 }
 
 }  // namespace ps
+
+namespace ps {
+PS_DEFINE_CHECK_READER(check_bits_batch16)
+}  // namespace ps

@@ -66,4 +66,15 @@ int StageProfiler::read(double* ms, int32_t* calls) {
 
 extern "C" const char* ps_last_error(void) { return ps::g_err; }
 
-extern "C" const char* ps_version(void) { return "psweep-gb300 0.1 (sm_103a)"; }
+extern "C" const char* ps_version(void) {
+    return PS_CHECKED ? "psweep-gb300 0.1 (sm_103a, checked)" : "psweep-gb300 0.1 (sm_103a)";
+}
+
+extern "C" int ps_check_read(uint32_t* bits) {
+    ps::clear_error();
+    PS_ARG(bits != nullptr, "ps_check_read: bits is NULL");
+    PS_CUDA(cudaDeviceSynchronize());
+    *bits = ps::check_bits_sweep() | ps::check_bits_tsdf() | ps::check_bits_batch16() | ps::check_bits_batch24() |
+            ps::check_bits_diff();
+    return PS_OK;
+}

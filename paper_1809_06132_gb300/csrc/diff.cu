@@ -327,6 +327,7 @@ __global__ void __launch_bounds__(DNT) soft_bwd_kernel(const __grid_constant__ D
                 Warp wp = warp_at(P, C, pl, x0 + hx, y0 + hy);
                 int xa = (int)floorf(wp.u), ya = (int)floorf(wp.v);
                 int xb = min(xa + 1, C.c.width - 1), yb = min(ya + 1, C.c.height - 1);
+                if (!PS_DCHECK(xa >= 0 && ya >= 0 && xa < C.c.width && ya < C.c.height, CHK_GATHER)) continue;
                 float ax = wp.u - (float)xa, ay = wp.v - (float)ya;
                 const float* I = C.img;
                 const int Wc = C.c.width;
@@ -360,7 +361,8 @@ __global__ void __launch_bounds__(DNT) soft_bwd_kernel(const __grid_constant__ D
         for (int p = tid; p < NPOS; p += DNT) {
             const int hx = p % HW, hy = p / HW;
             float g = gR[hy * DS + hx];
-            if (g != 0.f) atomicAdd(&g_ref[(size_t)(y0 + hy) * P.W + (x0 + hx)], g);
+            if (g != 0.f && PS_DCHECK(x0 + hx >= 0 && y0 + hy >= 0 && x0 + hx < P.W && y0 + hy < P.H, CHK_PIXEL))
+                atomicAdd(&g_ref[(size_t)(y0 + hy) * P.W + (x0 + hx)], g);
         }
     if (g_pose) {
         const int lane = tid & 31, wid = tid >> 5;
@@ -536,3 +538,7 @@ extern "C" int psdiff_backward(psdiff_t* h, const float* const* images, const ps
     PS_CUDA(cudaGetLastError());
     return PS_OK;
 }
+
+namespace ps {
+PS_DEFINE_CHECK_READER(check_bits_diff)
+}  // namespace ps

@@ -40,6 +40,45 @@ enum : uint32_t {
     DEV_TIMEOUT = 2u,   // bounded probe loop gave up
 };
 
+// Checked build (compiled with -DPS_CHECK): bounds checks at the accesses
+// whose address comes from data (image gathers from projected coordinates,
+// pool slots from the hash table, queue items) set a bit in a device word of
+// the translation unit and skip the access.  In the normal build the checks
+// compile to nothing.  ps_check_read() collects and clears the bits.
+enum : uint32_t {
+    CHK_GATHER = 1u,  // image gather outside the image
+    CHK_PIXEL = 2u,   // pixel index outside the image
+    CHK_POOL = 4u,    // voxel-block pool slot outside the pool
+    CHK_ITEM = 8u,    // work item outside its level or queue
+};
+#ifdef PS_CHECK
+#define PS_CHECKED 1
+#else
+#define PS_CHECKED 0
+#endif
+namespace {
+__device__ unsigned g_check_bits;  // one per translation unit
+}
+// True when cond holds; in the checked build a failure records `bit`.
+#define PS_DCHECK(cond, bit) \
+    (!PS_CHECKED || (cond) || (atomicOr(&ps::g_check_bits, (unsigned)(bit)), false))
+// Host reader of this translation unit's check word (reads and clears it).
+#define PS_DEFINE_CHECK_READER(fn)                                                \
+    unsigned fn() {                                                               \
+        unsigned v = 0;                                                           \
+        if (!PS_CHECKED) return 0;                                                \
+        if (cudaMemcpyFromSymbol(&v, ps::g_check_bits, sizeof(v)) != cudaSuccess) \
+            return 0xffffffffu;                                                   \
+        const unsigned z = 0;                                                     \
+        cudaMemcpyToSymbol(ps::g_check_bits, &z, sizeof(z));                      \
+        return v;                                                                 \
+    }
+unsigned check_bits_sweep();
+unsigned check_bits_tsdf();
+unsigned check_bits_batch16();
+unsigned check_bits_batch24();
+unsigned check_bits_diff();
+
 // Camera in float for device use (level intrinsics already applied).
 struct CamF {
     float xi, fx, fy, cx, cy, k1, k2, p1, p2, r2_max;

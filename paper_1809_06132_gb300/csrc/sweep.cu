@@ -721,3 +721,7 @@ extern "C" int psweep_frame_host(psweep_t* h, tsdf_t* t, const uint8_t* const* h
     PS_CUDA(cudaStreamSynchronize(s));
     return PS_OK;
 }
+
+namespace ps {
+PS_DEFINE_CHECK_READER(check_bits_sweep)
+}  // namespace ps

@@ -181,6 +181,11 @@ __device__ __forceinline__ float warp_sample(const CamS& c, float X, float Y, fl
     float uc = fminf(fmaxf(u, 0.0f), c.wm1), vc = fminf(fmaxf(v, 0.0f), c.hm1);
     bool ok = (Z > c.lim * n) && (r2 <= c.r2_max) && (uc == u) && (vc == v);
     int x0 = (int)uc, y0 = (int)vc;
+    if (!PS_DCHECK(x0 >= 0 && x0 < c.width && y0 >= 0 && (float)y0 <= c.hm1, CHK_GATHER)) {
+        x0 = 0;
+        y0 = 0;
+        ok = false;
+    }
     float ax = uc - (float)x0, ay = vc - (float)y0;
     float4 q;
     if (HALF) {
@@ -277,6 +282,7 @@ template <int RHO, bool HALF, int TH, int KP>
 __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, unsigned char* smem_raw, int* s_flag) {
     using G = Geo<RHO, TH, KP>;
     constexpr int SEG = G::SEG;
+    if (!PS_DCHECK(item >= 0 && item < L.n_items, CHK_ITEM)) return;  // uniform over the CTA
     const int tile = item / L.n_chunks, chunk = item - tile * L.n_chunks;
     const int k_lo = chunk * L.chunk, k_hi = min(L.n_planes, k_lo + L.chunk);
     constexpr int HH = G::HH, HWL = G::HWL, WS = G::WS, HS = G::HS, NPOS = G::NPOS, N = G::N;

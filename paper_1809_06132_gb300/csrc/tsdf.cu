@@ -274,6 +274,7 @@ __device__ __forceinline__ bool observe_voxel(const FrameP& F, const float* dept
     float pu = floorf(u + 0.5f), pv = floorf(v + 0.5f);
     if (!(pu >= 0.f && pv >= 0.f && pu < (float)c.width && pv < (float)c.height)) return false;
     const size_t pix = (size_t)pv * c.width + (size_t)pu;
+    if (!PS_DCHECK(pix < (size_t)c.width * c.height, CHK_PIXEL)) return false;
     float d = __ldg(&depth[pix]);
     if (!(d > 0.f) || !(d < 3.0e38f)) return false;
     // |X_d| in voxel units: (a + b)^2 = a^2 (exact int) + (2a + b) b
@@ -312,6 +313,7 @@ __global__ void __launch_bounds__(IT) integrate_kernel(const __grid_constant__ F
     int nv = *T.n_vis;
     for (int e = blockIdx.x; e < nv; e += gridDim.x) {
         int bi = T.vis[e];
+        if (!PS_DCHECK(bi >= 0 && bi < T.pool_cap, CHK_POOL)) continue;  // uniform over the CTA
         int4 k = T.pool_keys[bi];
         float4* blk = reinterpret_cast<float4*>(T.vox + (size_t)bi * B3);
         float4 pr = blk[threadIdx.x];
@@ -329,6 +331,7 @@ __global__ void __launch_bounds__(IT) integrate_kernel(const __grid_constant__ F
 __global__ void extract_kernel(TsdfDev T, const int* live, int n, float min_w, int* keys, float* D, float* W) {
     for (int o = blockIdx.x; o < n; o += gridDim.x) {
         const int i = live ? live[o] : o;
+        if (!PS_DCHECK(i >= 0 && i < T.pool_cap, CHK_POOL)) continue;  // uniform over the CTA
         if (threadIdx.x == 0) {
             int4 k = T.pool_keys[i];
             keys[3 * o] = k.x;
@@ -449,6 +452,7 @@ __global__ void load_voxels_kernel(TsdfDev T, const int* keys, const float* D, c
     for (int e = blockIdx.x; e < n; e += gridDim.x) {
         const int i = hash_find(T, keys[3 * e], keys[3 * e + 1], keys[3 * e + 2]);
         if (i < 0) continue;  // no room (capacity already latched)
+        if (!PS_DCHECK(i < T.pool_cap, CHK_POOL)) continue;
         for (int v = threadIdx.x; v < B3; v += blockDim.x)
             T.vox[(size_t)i * B3 + v] = make_float2(D[(size_t)e * B3 + v], W[(size_t)e * B3 + v]);
     }
@@ -1011,3 +1015,7 @@ extern "C" int tsdf_dense_fuse_backward(const float* voxels_in, const int32_t* d
     PS_CUDA(cudaGetLastError());
     return PS_OK;
 }
+
+namespace ps {
+PS_DEFINE_CHECK_READER(check_bits_tsdf)
+}  // namespace ps

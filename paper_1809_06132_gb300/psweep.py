@@ -30,7 +30,7 @@ EXPORTS = ["psweep_create", "psweep_depth", "psweep_destroy", "tsdf_create", "ts
            "psbatch_queue_stats", "psbatch_destroy", "psbatch_autotune", "ps_pipe_create", "ps_pipe_push",
            "ps_pipe_flush", "ps_pipe_destroy", "psdiff_create", "psdiff_forward", "psdiff_backward",
            "psdiff_destroy", "tsdf_dense_fuse_backward",
-           "ps_last_error", "ps_version"]
+           "ps_check_read", "ps_last_error", "ps_version"]
 
 
 class PsError(RuntimeError):
@@ -98,20 +98,26 @@ class ps_tsdf_desc(C.Structure):
 _lib = None
 
 
+def _checked() -> bool:
+    """PSWEEP_CHECKED=1 selects the bounds-checked build of the library."""
+    return os.environ.get("PSWEEP_CHECKED", "") == "1"
+
+
 def lib_path() -> str:
-    return _build.LIB
+    return _build.LIB_CHECK if _checked() else _build.LIB
 
 
 def load(build_if_missing: bool = True):
-    """Load libpsweep.so (building it in-tree first if it is missing)."""
+    """Load libpsweep.so (building it in-tree first if it is missing);
+    libpsweep_check.so when PSWEEP_CHECKED=1."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    path = lib_path()
     if not os.path.exists(path):
         if not build_if_missing:
-            raise ImportError(f"libpsweep.so not built at {path}")
-        _build.build()
+            raise ImportError(f"{os.path.basename(path)} not built at {path}")
+        _build.build(check=_checked())
     L = C.CDLL(path)
     P = C.c_void_p
     L.psweep_create.argtypes = [C.POINTER(ps_sweep_desc), C.POINTER(C.c_void_p)]
@@ -155,6 +161,7 @@ def load(build_if_missing: bool = True):
     L.psdiff_destroy.restype = None
     L.tsdf_dense_fuse_backward.argtypes = [P, P, P, C.c_double, C.c_double, C.c_double, P, C.POINTER(ps_camera),
                                            C.POINTER(ps_pose), P, P, P, P, P]
+    L.ps_check_read.argtypes = [C.POINTER(C.c_uint32)]
     L.ps_last_error.restype = C.c_char_p
     L.ps_version.restype = C.c_char_p
     _lib = L
@@ -548,6 +555,17 @@ def tsdf_integrate_dense_static(voxels: torch.Tensor, dims, origin, voxel_size: 
     _check(load().tsdf_integrate_dense_static(_dev(voxels, torch.float32, "voxels"), d, o, float(voxel_size),
                                               float(mu), float(w_max), _dev(depth, torch.float32, "depth"),
                                               C.byref(cz), C.byref(pz), _stream_ptr(stream)))
+
+
+CHECK_BITS = {1: "image gather outside the image", 2: "pixel index outside the image",
+              4: "pool slot outside the pool", 8: "work item outside its level or queue"}
+
+
+def check_read() -> int:
+    """Bounds-check failures recorded since the last read (always 0 in the normal build)."""
+    b = C.c_uint32()
+    _check(load().ps_check_read(C.byref(b)))
+    return b.value
 
 
 def version() -> str:
