@@ -218,6 +218,14 @@ def boxes_array(boxes):
     return arr, n
 
 
+def _cuda_device(device, name: str):
+    """Output buffers that kernels write must be device memory."""
+    d = torch.device(device)
+    if d.type != "cuda":
+        raise ValueError(f"{name}: outputs are written by kernels and must be on a CUDA device, not {d}")
+    return d
+
+
 def _dev(t: torch.Tensor, dtype, name: str) -> int:
     if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
         raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
@@ -510,6 +518,7 @@ class Tsdf:
 
     def swap_out(self, local_center, capacity: int = None, device="cuda", stream=None):
         """Move the blocks outside the local map out of the map: (keys, D, W) CUDA tensors."""
+        device = _cuda_device(device, "swap_out")
         cap = self.count(stream) if capacity is None else int(capacity)
         keys = torch.empty((max(cap, 1), 3), dtype=torch.int32, device=device)
         D = torch.empty((max(cap, 1), 512), dtype=torch.float32, device=device)
@@ -529,6 +538,7 @@ class Tsdf:
 
     def extract(self, min_weight: float = 0.0, device="cuda", stream=None):
         """(keys (n, 3) int32, D (n, 512), W (n, 512)) as CUDA tensors, in pool order."""
+        device = _cuda_device(device, "extract")
         n = self.count(stream)
         keys = torch.empty((max(n, 1), 3), dtype=torch.int32, device=device)
         D = torch.empty((max(n, 1), 512), dtype=torch.float32, device=device)

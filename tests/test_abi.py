@@ -130,3 +130,11 @@ def test_differentiable_argument_errors_without_gpu():
     assert L.psdiff_backward(None, None, None, None, None, None, None, None, None) == P.PS_ERR_ARG
     assert L.tsdf_dense_fuse_backward(None, None, None, 0.1, 0.3, 100.0, None, None, None, None, None, None, None,
                                       None) == P.PS_ERR_ARG
+
+
+def test_kernel_outputs_must_be_device_memory():
+    # extract and swap_out write through kernels: host tensors are refused before any call
+    from paper_1809_06132_gb300.psweep import _cuda_device
+    with pytest.raises(ValueError):
+        _cuda_device("cpu", "extract")
+    assert _cuda_device("cuda", "extract").type == "cuda"
