@@ -41,7 +41,7 @@ UNIT = "frames/s"
 # warp 64 (plane intersection 4, rigid transform 18, unified projection 12,
 # distortion 18, bilinear sample 12), window statistics 18 (w^2 and r w
 # products, running horizontal + vertical sums of 4 quantities), ZNCC cost 9,
-# camera minimum 1  ("roofline")
+# camera minimum 1
 FLOP_PER_UNIT = 92
 # TSDF integration: each voxel of a listed block is read and written once ({D, w} float32 pairs)
 BYTES_PER_VOXEL = 16
