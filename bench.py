@@ -75,6 +75,20 @@ def workload(args, seed):
     return scenes.street(seed, n_frames=100)
 
 
+def workload_config(args, wl, nf, world):
+    """The `config` object of a street / ring line (the same for both arms)."""
+    street = args.config == "street"
+    return {"workload": wl.name, "ref": f"{wl.rig.ref.width}x{wl.rig.ref.height}",
+            "matching_cams": len(wl.rig.cams),
+            "levels": ("320x256 (64 fronto + 32 ground, 7x7) + 640x512 crop (128 fronto, 9x9)" if street
+                       else "1280x1024 (256 fronto, 9x9)"),
+            "tsdf": ("8^3 blocks, 0.1 m voxels, mu 0.5 m, 60x3x60 m local map" if street
+                     else "8^3 blocks, 0.02 m voxels, mu 0.1 m, 60x3x60 m local map, 2^23-block pool"),
+            "image_storage": "fp16" if getattr(args, "half", False) else "fp32", "frames": nf,
+            "l2": "flushed between steps (256 MB write outside the step events)",
+            "parallelism": f"replicas x{world} (independent sequences)"}
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -259,7 +273,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "frames": nf, "l2": "n/a (CPU)"},
+            "config": workload_config(args, wl, nf, world),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "per step: sweep at 24 random pixels per level extrapolated linearly to the "
                                        "whole frame, plus full-frame TSDF fusion of the frame's range map"},
@@ -405,14 +419,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl.name, "ref": f"{W}x{H}", "matching_cams": len(wl.rig.cams),
-                   "levels": ("320x256 (64 fronto + 32 ground, 7x7) + 640x512 crop (128 fronto, 9x9)"
-                              if args.config == "street" else "1280x1024 (256 fronto, 9x9)"),
-                   "tsdf": ("8^3 blocks, 0.1 m voxels, mu 0.5 m, 60x3x60 m local map" if args.config == "street"
-                            else "8^3 blocks, 0.02 m voxels, mu 0.1 m, 60x3x60 m local map, 2^23-block pool"),
-                   "image_storage": "fp16" if args.half else "fp32", "frames": nf,
-                   "l2": "flushed between steps (256 MB write outside the step events)",
-                   "parallelism": f"replicas x{world} (independent sequences)"},
+        "config": workload_config(args, wl, nf, world),
         "sweep": {"value": pix_planes / (depth_ms * 1e-3) / 1e9, "unit": "Gpix·planes/s",
                   "kernel_only": pix_planes / (k_ms * 1e-3) / 1e9,
                   "gpix_plane_cam_per_s": units / (k_ms * 1e-3) / 1e9,
