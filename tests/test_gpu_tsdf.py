@@ -187,3 +187,23 @@ def test_checkpoint_and_resume():
     a = _sorted(*A.extract())
     b = _sorted(*B.extract())
     assert all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+def test_street_full_size_parity():
+    # the bench's fusion configuration (1280x1024 range maps, 10 cm voxels,
+    # 60 x 3 x 60 m local map), two frames, every voxel against the oracle
+    wl = scenes.street(0, n_frames=2, scale=1.0)
+    src = scenes.FrameSource(wl, device="cuda")
+    T, O, gk, gD, gW = _run(wl, range(2), src)
+    ok, oD, oW, oamb = O.dump()
+    gset = set(map(tuple, gk.tolist()))
+    oset = set(map(tuple, ok.tolist()))
+    maybe = set(map(tuple, O.ever_maybe().tolist()))
+    amb_blocks = {tuple(k) for k, a in zip(ok.tolist(), oamb) if a.all()}
+    assert (oset - amb_blocks) <= gset
+    assert gset <= (oset | maybe)
+    s = tsdf_compare(ok, oD, oW, oamb, gk, gD, gW)
+    print("street full-size fusion", s, "blocks", len(gset), len(oset))
+    assert len(gset) > 1000 and s["n_updated"] > 200000
+    assert s["D_abs_max"] <= TSDF_ABS, s
+    assert s["W_mismatch"] == 0, s
