@@ -111,6 +111,8 @@ def lib():
             L.orc_tsdf_load.argtypes = [_P, C.c_int64, _P, _D, _D]
             L.orc_tsdf_ever_maybe.argtypes = [_P, _P]
             L.orc_tsdf_ever_maybe.restype = C.c_int64
+            L.orc_tsdf_points.argtypes = [C.c_int64, _P, _D, _D, C.c_double, _D, C.c_double, C.c_int64, _D, _P]
+            L.orc_tsdf_points.restype = C.c_int64
             L.orc_project_jacobian.argtypes = [C.POINTER(OrCamera), _D, _D]
             L.orc_soft_argmin.argtypes = [_D, _D, C.c_int32, C.c_double, _D, _D, _D]
             L.orc_soft_depth.argtypes = [C.POINTER(OrCamera), C.c_int32, C.POINTER(OrCamera), C.POINTER(OrPose),
@@ -520,3 +522,19 @@ def dense_fuse_grad(vox, nb, origin, voxel, mu, w_max, depth, cam, w2c, gD):
     lib().orc_dense_fuse_grad(nbv.ctypes.data, _dptr(o), voxel, mu, w_max, _dptr(vin), d.ctypes.data,
                               C.byref(camera(cam)), C.byref(pose(w2c)), _dptr(g), _dptr(gin), _dptr(gd), _dptr(gp))
     return gin, gd, gp
+
+
+def tsdf_points(keys, D, W, min_w, origin, voxel):
+    """Surface points of a block map: (points (m, 3) float64, edges (m, 4) int32: voxel index, axis)."""
+    k = np.ascontiguousarray(keys, dtype=np.int32).reshape(-1, 3)
+    d = np.ascontiguousarray(D, dtype=np.float64).reshape(-1, 512)
+    w = np.ascontiguousarray(W, dtype=np.float64).reshape(-1, 512)
+    o = np.ascontiguousarray(origin, dtype=np.float64)
+    L = lib()
+    m = L.orc_tsdf_points(len(k), k.ctypes.data, _dptr(d), _dptr(w), float(min_w), _dptr(o), float(voxel), 0, None,
+                          None)
+    pts = np.zeros((max(m, 1), 3))
+    edges = np.zeros((max(m, 1), 4), np.int32)
+    L.orc_tsdf_points(len(k), k.ctypes.data, _dptr(d), _dptr(w), float(min_w), _dptr(o), float(voxel), m, _dptr(pts),
+                      edges.ctypes.data)
+    return pts[:m], edges[:m]

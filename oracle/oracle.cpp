@@ -1024,6 +1024,58 @@ void orc_tsdf_dump(void* h, int64_t* keys, double* D, double* W, uint8_t* amb) {
     }
 }
 
+// Surface points of a block map (Sec. III-C, the extracted map): for every
+// voxel a and its +x, +y and +z neighbour b (in the same block or the next
+// block along that axis) that both have w >= max(min_w, 1), a sign change of
+// D (positive on one side, zero or negative on the other) gives the point
+// X_a + t (X_b - X_a), t = D_a / (D_a - D_b), voxel centres at
+// origin + (i + 1/2) voxel.  keys: n x 3 block indices; D, W: n x 512 (voxel
+// x + 8 y + 64 z).  Writes up to cap points (x, y, z) and edges (global voxel
+// index of a, axis); returns the number of points found.
+int64_t orc_tsdf_points(int64_t n, const int32_t* keys, const double* D, const double* W, double min_w,
+                        const double* origin, double voxel, int64_t cap, double* points, int32_t* edges) {
+    std::map<Key, int64_t> index;
+    for (int64_t i = 0; i < n; ++i) index[Key{keys[3 * i], keys[3 * i + 1], keys[3 * i + 2]}] = i;
+    const double wmin = std::max(min_w, 1.0);
+    int64_t found = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t* k = keys + 3 * i;
+        for (int v = 0; v < 512; ++v) {
+            const int x = v % 8, y = (v / 8) % 8, z = v / 64;
+            const double da = D[i * 512 + v];
+            if (!(W[i * 512 + v] >= wmin)) continue;
+            for (int axis = 0; axis < 3; ++axis) {
+                int c[3] = {x, y, z};
+                int32_t kb[3] = {k[0], k[1], k[2]};
+                c[axis] += 1;
+                if (c[axis] == 8) {  // the neighbour lies in the next block along the axis
+                    c[axis] = 0;
+                    kb[axis] += 1;
+                }
+                auto it = index.find(Key{kb[0], kb[1], kb[2]});
+                if (it == index.end()) continue;
+                const int64_t j = it->second;
+                const int vb = c[0] + 8 * c[1] + 64 * c[2];
+                if (!(W[j * 512 + vb] >= wmin)) continue;
+                const double db = D[j * 512 + vb];
+                if ((da > 0.0) == (db > 0.0)) continue;
+                const double t = da / (da - db);
+                const int g[3] = {k[0] * 8 + x, k[1] * 8 + y, k[2] * 8 + z};
+                if (found < cap) {
+                    for (int q = 0; q < 3; ++q) {
+                        double xa = origin[q] + (g[q] + 0.5) * voxel;
+                        points[3 * found + q] = xa + (q == axis ? t * voxel : 0.0);
+                        edges[4 * found + q] = g[q];
+                    }
+                    edges[4 * found + 3] = axis;
+                }
+                ++found;
+            }
+        }
+    }
+    return found;
+}
+
 // Last frame's allocation report: counts of the strict set (blocks any
 // correct implementation allocates) and the ambiguous band.
 void orc_tsdf_alloc_counts(void* h, int64_t* n_strict, int64_t* n_maybe) {
