@@ -230,6 +230,20 @@ int tsdf_extract(tsdf_t* t, float min_weight, int32_t* keys, float* D, float* W,
 /* Synchronises `stream`, returns and clears the latched device status. */
 int tsdf_status(tsdf_t* t, void* stream);
 
+/* Surface points of the map (Sec. III-C; the paper evaluates the map as a
+ * point set): for every voxel a and its +x, +y and +z neighbour b (in the
+ * same block or the next block along that axis) that both have at least
+ * max(min_weight, 1) observations and whose D change sign (positive against
+ * zero or negative), the point X_a + t (X_b - X_a) with t = D_a / (D_a - D_b),
+ * X = origin + (i + 1/2) voxel_size, in world coordinates.
+ *   points  device float32 capacity x 3.
+ *   edges   device int32 capacity x 4 (global voxel index of a, axis) or NULL.
+ * Unspecified order.  *n_out = points found; if that exceeds capacity only
+ * the first `capacity` are written and the call returns PS_ERR_CAPACITY
+ * (capacity 0 counts them).  Synchronises `stream`. */
+int tsdf_extract_points(tsdf_t* t, float min_weight, float* points, int32_t* edges, int64_t capacity,
+                        int64_t* n_out, void* stream);
+
 /* Local-map swap-out (Sec. III-C: blocks that are no longer in the local map
  * are swapped out of GPU memory).  Every allocated block whose centre lies
  * outside the local-map box around local_center (half extents local_half of

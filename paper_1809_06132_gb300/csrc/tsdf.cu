@@ -14,6 +14,7 @@
 //                     block, 256 threads x 2 voxels, 16-byte loads and
 //                     stores of the interleaved {D, w} pairs
 //   extract_kernel    copy-out with the minimum-observation filter
+//   points_kernel     surface points at sign changes between observed neighbour voxels
 //
 // The signed distance eta = d - |X_d| subtracts two ranges of tens of
 // metres; float32 alone would lose ~1e-5 m there.  The kernel therefore
@@ -442,6 +443,64 @@ __device__ int hash_find(const TsdfDev& T, int bx, int by, int bz) {
     return -1;
 }
 
+// Surface points (the extracted map): every voxel a of a listed block and
+// its +x, +y, +z neighbour b (same block, or the next block along the axis:
+// index arithmetic on dense grids, the hash otherwise) with w >= wmin on both
+// and a sign change of D (positive against zero or negative) give the point
+// X_a + t (X_b - X_a), t = D_a / (D_a - D_b).  Points and edges (global voxel
+// index of a, axis) go to slots taken from an atomic counter; slots past
+// `cap` are counted only.
+__global__ void __launch_bounds__(256) points_kernel(TsdfDev T, const int* live, int n, float wmin, int nbx, int nby,
+                                                     int nbz, float vox, float ox, float oy, float oz, int cap,
+                                                     int* counter, float* points, int* edges) {
+    __shared__ int nb_slot[3];
+    for (int o = blockIdx.x; o < n; o += gridDim.x) {
+        const int i = live ? live[o] : o;
+        if (!PS_DCHECK(i >= 0 && i < T.pool_cap, CHK_POOL)) continue;  // uniform over the CTA
+        const int4 k = T.pool_keys[i];
+        __syncthreads();  // the previous block's neighbour slots are no longer read
+        if (threadIdx.x < 3) {
+            const int a = threadIdx.x;
+            const int kx = k.x + (a == 0), ky = k.y + (a == 1), kz = k.z + (a == 2);
+            int slot = -1;
+            if (nbx > 0) {
+                if (kx < nbx && ky < nby && kz < nbz) slot = kx + nbx * (ky + nby * kz);
+            } else {
+                slot = hash_find(T, kx, ky, kz);
+            }
+            nb_slot[a] = (slot >= 0 && slot < T.pool_cap) ? slot : -1;
+        }
+        __syncthreads();
+        for (int v = threadIdx.x; v < B3; v += blockDim.x) {
+            const float2 da = T.vox[(size_t)i * B3 + v];
+            if (!(da.y >= wmin)) continue;
+            const int c[3] = {v & 7, (v >> 3) & 7, v >> 6};
+            for (int axis = 0; axis < 3; ++axis) {
+                int cb[3] = {c[0], c[1], c[2]};
+                int slot = i;
+                if (++cb[axis] == B) {
+                    cb[axis] = 0;
+                    slot = nb_slot[axis];
+                    if (slot < 0) continue;
+                }
+                const float2 db = T.vox[(size_t)slot * B3 + cb[0] + B * cb[1] + B * B * cb[2]];
+                if (!(db.y >= wmin) || ((da.x > 0.f) == (db.x > 0.f))) continue;
+                const float t = da.x / (da.x - db.x);
+                const int g[3] = {k.x * B + c[0], k.y * B + c[1], k.z * B + c[2]};
+                const int e = atomicAdd(counter, 1);
+                if (e >= cap) continue;
+                const float org[3] = {ox, oy, oz};
+                for (int q = 0; q < 3; ++q) {
+                    const float f = (float)g[q] + 0.5f + (q == axis ? t : 0.f);
+                    points[3 * (size_t)e + q] = fmaf(f, vox, org[q]);
+                    if (edges) edges[4 * (size_t)e + q] = g[q];
+                }
+                if (edges) edges[4 * (size_t)e + 3] = axis;
+            }
+        }
+    }
+}
+
 // Load: (1) insert the keys, (2) copy each block's voxels into its slot.
 __global__ void load_keys_kernel(TsdfDev T, const int* keys, int n) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -731,6 +790,46 @@ extern "C" int tsdf_extract(tsdf_t* t, float min_weight, int32_t* keys, float* D
     if (st) return st;
     if (capacity < n) {
         set_error("tsdf_extract: capacity %lld < %lld blocks", (long long)capacity, (long long)n);
+        return PS_ERR_CAPACITY;
+    }
+    return PS_OK;
+}
+
+extern "C" int tsdf_extract_points(tsdf_t* t, float min_weight, float* points, int32_t* edges, int64_t capacity,
+                                   int64_t* n_out, void* stream) {
+    clear_error();
+    PS_ARG(t != nullptr && n_out != nullptr, "tsdf_extract_points: NULL argument");
+    PS_ARG(capacity >= 0 && capacity < (1ll << 31), "tsdf_extract_points: capacity must be in 0 .. 2^31 - 1");
+    PS_ARG(capacity == 0 || points != nullptr, "tsdf_extract_points: points is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t n = 0;
+    int st = tsdf_count(t, &n, stream);
+    int64_t hw = 0;
+    PS_CUDA(cudaMemcpyAsync(&hw, t->T.n_alloc, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PS_CUDA(cudaStreamSynchronize(s));
+    const bool holes = std::min<int64_t>((int)hw, t->T.pool_cap) != n;
+    if (holes) {
+        int e = live_slots(t, s, &n);
+        if (e) return e;
+    }
+    int found = 0;
+    if (n > 0) {
+        PS_CUDA(cudaMemsetAsync(t->n_tmp + 1, 0, sizeof(int), s));
+        const ps_tsdf_desc& d = t->d;
+        const int nbx = t->dense ? d.dense_dim[0] / 8 : 0, nby = t->dense ? d.dense_dim[1] / 8 : 0,
+                  nbz = t->dense ? d.dense_dim[2] / 8 : 0;
+        points_kernel<<<(int)std::min<int64_t>(n, 65535), 256, 0, s>>>(
+            t->T, holes ? t->T.vis : nullptr, (int)n, std::max(min_weight, 1.0f), nbx, nby, nbz, (float)d.voxel_size,
+            (float)d.origin[0], (float)d.origin[1], (float)d.origin[2], (int)capacity, t->n_tmp + 1, points, edges);
+        PS_CUDA(cudaGetLastError());
+        PS_CUDA(cudaMemcpyAsync(&found, t->n_tmp + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PS_CUDA(cudaStreamSynchronize(s));
+    }
+    *n_out = found;
+    if (st) return st;
+    if (found > capacity) {
+        set_error("tsdf_extract_points: %d points, capacity %lld (the first %lld were written)", found,
+                  (long long)capacity, (long long)capacity);
         return PS_ERR_CAPACITY;
     }
     return PS_OK;

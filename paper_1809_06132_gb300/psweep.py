@@ -26,7 +26,7 @@ MAX_SETS, MAX_CAMS, MAX_LEVELS = 4, 4, 2
 EXPORTS = ["psweep_create", "psweep_depth", "psweep_destroy", "tsdf_create", "tsdf_integrate", "tsdf_count",
            "tsdf_extract", "tsdf_status", "tsdf_destroy", "psweep_frame_host", "psweep_profile",
            "psweep_profile_read", "tsdf_profile", "tsdf_profile_read", "tsdf_integrate_dense_static",
-           "tsdf_swap_out", "tsdf_load", "psbatch_create", "psbatch_run", "psbatch_timing", "psbatch_status",
+           "tsdf_swap_out", "tsdf_load", "tsdf_extract_points", "psbatch_create", "psbatch_run", "psbatch_timing", "psbatch_status",
            "psbatch_queue_stats", "psbatch_destroy", "psbatch_autotune", "ps_pipe_create", "ps_pipe_push",
            "ps_pipe_flush", "ps_pipe_destroy", "psdiff_create", "psdiff_forward", "psdiff_backward",
            "psdiff_destroy", "tsdf_dense_fuse_backward",
@@ -138,6 +138,7 @@ def load(build_if_missing: bool = True):
     L.tsdf_profile_read.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int32)]
     L.tsdf_swap_out.argtypes = [P, P, P, P, P, C.c_int64, C.POINTER(C.c_int64), P]
     L.tsdf_load.argtypes = [P, P, P, P, C.c_int64, P]
+    L.tsdf_extract_points.argtypes = [P, C.c_float, P, P, C.c_int64, C.POINTER(C.c_int64), P]
     L.tsdf_integrate_dense_static.argtypes = [P, P, P, C.c_double, C.c_double, C.c_double, P,
                                               C.POINTER(ps_camera), C.POINTER(ps_pose), P]
     L.psbatch_create.argtypes = [P, C.c_int32, C.POINTER(ps_batch_opts), C.POINTER(C.c_void_p)]
@@ -548,6 +549,23 @@ class Tsdf:
                                    C.byref(m), _stream_ptr(stream)))
         return keys[:m.value], D[:m.value], W[:m.value]
 
+
+def _tsdf_points(self, min_weight: float = 3.0, device="cuda", stream=None):
+    """Surface points (m, 3) float32 and edges (m, 4) int32 (voxel index, axis) as CUDA tensors."""
+    device = _cuda_device(device, "points")
+    m = C.c_int64()
+    st = load().tsdf_extract_points(self.h, float(min_weight), None, None, 0, C.byref(m), _stream_ptr(stream))
+    if st not in (PS_OK, PS_ERR_CAPACITY):
+        _check(st)
+    n = m.value
+    pts = torch.empty((max(n, 1), 3), dtype=torch.float32, device=device)
+    edges = torch.empty((max(n, 1), 4), dtype=torch.int32, device=device)
+    _check(load().tsdf_extract_points(self.h, float(min_weight), pts.data_ptr(), edges.data_ptr(), n, C.byref(m),
+                                      _stream_ptr(stream)))
+    return pts[:m.value], edges[:m.value]
+
+
+Tsdf.points = _tsdf_points
 
 STATIC_MAX_BLOCKS = 65536
 

@@ -138,3 +138,9 @@ def test_kernel_outputs_must_be_device_memory():
     with pytest.raises(ValueError):
         _cuda_device("cpu", "extract")
     assert _cuda_device("cuda", "extract").type == "cuda"
+
+
+def test_points_argument_errors_without_gpu():
+    L = P.load()
+    n = C.c_int64()
+    assert L.tsdf_extract_points(None, 3.0, None, None, 0, C.byref(n), None) == P.PS_ERR_ARG

@@ -207,3 +207,39 @@ def test_street_full_size_parity():
     assert len(gset) > 1000 and s["n_updated"] > 200000
     assert s["D_abs_max"] <= TSDF_ABS, s
     assert s["W_mismatch"] == 0, s
+
+
+def _edge_map(pts, edges):
+    return {tuple(e): p for p, e in zip(np.asarray(pts), np.asarray(edges))}
+
+
+@pytest.mark.parametrize("case", ["hashed", "dense"])
+def test_surface_points_follow_the_oracle_rule(case):
+    # the GPU's points against the oracle's rule applied to the GPU's own voxels
+    if case == "hashed":
+        wl = scenes.street(0, n_frames=4, scale=0.25)
+    else:
+        wl = scenes.tiny(0, n_frames=3)
+    src = scenes.FrameSource(wl)
+    T, _, _, _, _ = _run(wl, range(wl.n_frames), src)
+    pts, edges = T.points(min_weight=3)
+    k, D, W = T.extract(min_weight=0)
+    opts, oedges = oracle.tsdf_points(k.cpu().numpy(), D.cpu().numpy(), W.cpu().numpy(), 3.0, wl.tsdf.origin,
+                                      wl.tsdf.voxel_size)
+    g = _edge_map(pts.cpu().numpy(), edges.cpu().numpy())
+    o = _edge_map(opts, oedges)
+    print(case, "surface points", len(g), len(o))
+    assert len(o) > 500 and set(g) == set(o)
+    err = max(np.abs(g[e] - o[e]).max() for e in o)
+    assert err <= 1e-4, err
+    # capacity: a short buffer reports how many there are
+    m = C_count(T)
+    assert m == len(o)
+
+
+def C_count(T):
+    import ctypes as C
+    n = C.c_int64()
+    st = P.load().tsdf_extract_points(T.h, 3.0, None, None, 0, C.byref(n), None)
+    assert st in (P.PS_OK, P.PS_ERR_CAPACITY)
+    return n.value
