@@ -559,6 +559,42 @@ def run_batch(args):
                 h_.copy_(d_, non_blocking=True)
             stream.synchronize()
             e2e.append(time.perf_counter() - ts)
+    # many small sweeps: where one launch pays most
+    small = scenes.batch_mix(rank_seed(args.seed, rank) + 100, n=args.batch_size, sizes=((256, 200), (320, 256)),
+                             planes=(32, 64))
+    s_sweeps, s_imgs, s_boxes = [], [], []
+    for w in small:
+        im, _ = scenes.FrameSource(w, device=f"cuda:{local}").frame(0)
+        s_imgs.append([torch.from_numpy(np.ascontiguousarray(x.numpy())).to(dev) for x in im])
+        s_sweeps.append(P.Sweep(w.rig, w.levels))
+        s_boxes.append(w.boxes[0])
+    s_outs = [torch.empty((w.rig.ref.height, w.rig.ref.width), dtype=torch.float32, device=dev) for w in small]
+    with torch.cuda.stream(stream):
+        Bs = P.Batch(s_sweeps, opts=P.batch_opts(tile_h=o.tile_h, kp=o.kp, plane_chunk=o.plane_chunk, use_graph=True))
+
+        def small_batch():
+            Bs.run(s_imgs, boxes=s_boxes, outs=s_outs, stream=stream)
+
+        def small_singles():
+            for sw_, im_, bx_, out_ in zip(s_sweeps, s_imgs, s_boxes, s_outs):
+                sw_.depth(im_, boxes=bx_, out=out_, stream=stream)
+
+        for _ in range(args.warmup):
+            small_batch()
+            small_singles()
+        sb, sl = [], []
+        for k in range(max(3, args.steps // 2)):
+            for fn, acc in ((small_batch, sb), (small_singles, sl)):
+                flush.zero_()
+                stream.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                stream.synchronize()
+                acc.append(a.elapsed_time(b))
+        small_lat = sorted(Bs.timing()[0])
+    small_pp = sum(w.pix_planes() for w in small)
     clocks.stop()
     clk = clocks.summary(t0, t1)
     if not clk.get("samples"):
@@ -585,6 +621,11 @@ def run_batch(args):
                        "source": "device global timer, kernel start to each sweep's finished depth map"},
         "compare": {"singles_ms": statistics.median(ms_single), "batch_no_graph_ms": statistics.median(ms_nograph),
                     "speedup_vs_singles": statistics.median(ms_single) / batch_ms},
+        "small_mix": {"sweeps": len(small), "sizes": "256x200 / 320x256", "planes": "32 / 64",
+                      "pix_planes_per_batch": small_pp, "batch_ms": statistics.median(sb),
+                      "singles_ms": statistics.median(sl), "speedup_vs_singles": statistics.median(sl) /
+                      statistics.median(sb), "gpix_planes_s": small_pp / (statistics.median(sb) * 1e-3) / 1e9,
+                      "latency_ms": {"p50": small_lat[len(small_lat) // 2], "p99": small_lat[-1]}},
         "autotune": [{"tile_h": c.tile_h, "kp": c.kp, "plane_chunk": c.plane_chunk, "ms": m}
                      for c, m in zip(cands, tune_ms)],
         "roofline": {"kernel": "batch_kernel", "bound": "alu", "achieved": achieved, "peak": peak_tflops,
