@@ -21,6 +21,7 @@
 //   local-map allocation gate ....... Sec. III-C (60 m x 60 m x 3 m)
 //   depth filters ................... Sec. III-A "Depth map filtering"
 //   block swap-out / load ........... Sec. III-C (blocks leaving the local map)
+//   surface points of the map ....... the map as a point set (Sec. IV-C)
 //   differentiable forms (not in the paper): soft-argmin depth over the
 //   plane hypotheses and dense fusion, each with its gradient
 //
