@@ -149,37 +149,32 @@ __device__ __forceinline__ float2 stats_px(const float* ref, int W, int H, int r
 
 // ------------------------------------------------------------- sweep
 
-// ------------------------------------------------------------- sweep
-
 // Matching camera as the sweep reads it (staged in shared memory per tile).
+// The projection constants are kept twice: as scalars, and as (value,
+// value) pairs for the two-plane form of the warp on packed FP32 operations.
 struct CamS {
     float R[9], t[3];
     float xi, fx, fy, cx, cy, k1, k2, p1, p2, r2_max, lim, wm1, hm1;
     int width;
     const void* quad;
+    float2 xi2, fx2, fy2, cx2, cy2, k12, k22, p12, p1x2, p22, p2x2, lim2;  // pairs; p1x2 = 2 p1, p2x2 = 2 p2
 };
 
-// Bilinear sample of a matching camera at the projection of X_j (camera
-// frame), as a centred intensity; NaN when the point does not project
-// (sphere side, distortion range) or lands outside [0, W-1] x [0, H-1].
-// The gather is clamped into the image and always issued, so the warp does
-// not diverge; a clamp that moved the point marks it outside (NaN compares
-// unequal, so a NaN position is rejected too).  HALF: quads stored as FP16.
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Bilinear sample of a matching camera at pixel (u, v), as a centred
+// intensity; NaN when `ok` is false (the point does not project) or (u, v)
+// lies outside [0, W-1] x [0, H-1].  The gather is clamped into the image and
+// always issued, so the warp does not diverge; a clamp that moved the point
+// marks it outside (NaN compares unequal, so a NaN position is rejected
+// too).  HALF: quads stored as FP16.
 template <bool HALF>
-__device__ __forceinline__ float warp_sample(const CamS& c, float X, float Y, float Z) {
-    float n2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
-    float n = n2 * rsqrtf(n2);
-    float inv = __fdividef(1.0f, fmaf(c.xi, n, Z));
-    float mx = X * inv, my = Y * inv;
-    float r2 = fmaf(mx, mx, my * my);
-    float rad = fmaf(r2, fmaf(c.k2, r2, c.k1), 1.0f);
-    float mxy = mx * my;
-    float xd = fmaf(mx, rad, fmaf(2.0f * c.p1, mxy, c.p2 * fmaf(2.0f * mx, mx, r2)));
-    float yd = fmaf(my, rad, fmaf(c.p1, fmaf(2.0f * my, my, r2), 2.0f * c.p2 * mxy));
-    float u = fmaf(c.fx, xd, c.cx);
-    float v = fmaf(c.fy, yd, c.cy);
+__device__ __forceinline__ float sample_at(const CamS& c, float u, float v, bool ok) {
     float uc = fminf(fmaxf(u, 0.0f), c.wm1), vc = fminf(fmaxf(v, 0.0f), c.hm1);
-    bool ok = (Z > c.lim * n) && (r2 <= c.r2_max) && (uc == u) && (vc == v);
+    ok = ok && (uc == u) && (vc == v);
     int x0 = (int)uc, y0 = (int)vc;
     if (!PS_DCHECK(x0 >= 0 && x0 < c.width && y0 >= 0 && (float)y0 <= c.hm1, CHK_GATHER)) {
         x0 = 0;
@@ -200,6 +195,47 @@ __device__ __forceinline__ float warp_sample(const CamS& c, float X, float Y, fl
     float bot = fmaf(ax, q.w - q.z, q.z);
     float w = fmaf(ay, bot - top, top);
     return ok ? w : __int_as_float(0x7fc00000);
+}
+
+// The sample of a matching camera at the projection of X_j (camera frame):
+// unified model, then radial-tangential distortion; NaN when the point does
+// not project (sphere side, distortion range) or lands outside the image.
+template <bool HALF>
+__device__ __forceinline__ float warp_sample(const CamS& c, float X, float Y, float Z) {
+    float n2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
+    float n = n2 * rsqrtf(n2);
+    float inv = __fdividef(1.0f, fmaf(c.xi, n, Z));
+    float mx = X * inv, my = Y * inv;
+    float r2 = fmaf(mx, mx, my * my);
+    float rad = fmaf(r2, fmaf(c.k2, r2, c.k1), 1.0f);
+    float mxy = mx * my;
+    float xd = fmaf(mx, rad, fmaf(2.0f * c.p1, mxy, c.p2 * fmaf(2.0f * mx, mx, r2)));
+    float yd = fmaf(my, rad, fmaf(c.p1, fmaf(2.0f * my, my, r2), 2.0f * c.p2 * mxy));
+    float u = fmaf(c.fx, xd, c.cx);
+    float v = fmaf(c.fy, yd, c.cy);
+    return sample_at<HALF>(c, u, v, (Z > c.lim * n) && (r2 <= c.r2_max));
+}
+
+// warp_sample for two points at once (lane x: the first plane, lane y: the
+// second).  The projection runs on packed FP32 pairs; per lane every
+// operation and its rounding are those of warp_sample (2 m = m + m exactly),
+// so each result is bit-identical to a warp_sample call.
+template <bool HALF>
+__device__ __forceinline__ float2 warp_sample2(const CamS& c, float2 X, float2 Y, float2 Z) {
+    float2 n2 = fma2(X, X, fma2(Y, Y, mul2(Z, Z)));
+    float2 n = mul2(n2, make_float2(rsqrtf(n2.x), rsqrtf(n2.y)));
+    float2 den = fma2(c.xi2, n, Z);
+    float2 inv = make_float2(__fdividef(1.0f, den.x), __fdividef(1.0f, den.y));
+    float2 mx = mul2(X, inv), my = mul2(Y, inv);
+    float2 r2 = fma2(mx, mx, mul2(my, my));
+    float2 rad = fma2(r2, fma2(c.k22, r2, c.k12), dup2(1.0f));
+    float2 mxy = mul2(mx, my);
+    float2 xd = fma2(mx, rad, fma2(c.p1x2, mxy, mul2(c.p22, fma2(add2(mx, mx), mx, r2))));
+    float2 yd = fma2(my, rad, fma2(c.p12, fma2(add2(my, my), my, r2), mul2(c.p2x2, mxy)));
+    float2 u = fma2(c.fx2, xd, c.cx2), v = fma2(c.fy2, yd, c.cy2);
+    float2 ln = mul2(c.lim2, n);
+    return make_float2(sample_at<HALF>(c, u.x, v.x, (Z.x > ln.x) && (r2.x <= c.r2_max)),
+                       sample_at<HALF>(c, u.y, v.y, (Z.y > ln.y) && (r2.y <= c.r2_max)));
 }
 
 // Tile geometry.  A CTA owns TW x TH output pixels of one level plus a halo of
@@ -226,15 +262,159 @@ struct Geo {
     static constexpr int NRUNPOS = RUN + 2 * RHO;     // positions one horizontal run reads
     static constexpr int NV = (NRUNPOS + 3) / 4;      // float4 loads per run
     static constexpr int N = (2 * RHO + 1) * (2 * RHO + 1);
-    // n_cams direction tables, H, KP W (one per plane of the group) and R
+    // two planes per pass: W holds (plane 0, plane 1) pairs with a row stride
+    // of 74 pairs (148 = 20 mod 32 words, so the 16-byte loads of the lanes
+    // of phase H, one halo row each, hit distinct bank groups)
+    static constexpr int WS2 = 74;
+    static constexpr int NV2 = (NRUNPOS + 1) / 2;     // 16-byte loads (two pairs) per run
+    // KP H buffers, W, R and n_cams direction tables (three floats per position)
     static constexpr size_t smem(int n_cams) {
-        return sizeof(float4) * ((size_t)n_cams * NPOS + HH * HS) + sizeof(float) * (KP + 1) * HH * WS;
+        return sizeof(float4) * KP * HH * HS + sizeof(float) * ((KP == 2 ? 2 * HH * WS2 : HH * WS) + HH * WS) +
+               sizeof(float) * 3 * (size_t)n_cams * NPOS;
     }
     static_assert(NT == TW * (TH / SEG) && TH % 8 == 0, "phase V: one thread per column and row segment");
     static_assert(KP == 1 || KP == 2, "one or two planes per pass");
     static_assert(HH <= 32, "phase H maps one warp lane per halo row");
     static_assert(HWL <= WS && 4 * NV + TW - RUN <= WS, "row stride covers the runs' loads");
+    static_assert(HWL <= WS2 && 2 * NV2 + TW - RUN <= WS2, "pair row stride covers the runs' loads");
 };
+
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// Phases A, H and V of one matching camera for two planes at once (planes
+// at offsets d0 and d1 of the current set), on packed FP32 pairs: lane x is
+// the first plane, lane y the second.  Per lane every sum and every rounding
+// is that of the one-plane path, so the costs are bit-identical to it.
+// W2 holds (plane 0, plane 1) sample pairs; H holds, per halo row and output
+// column, (sw0, sw1, sww0, sww1) in the first buffer and (srw0, srw1, m0, m1)
+// in the second (m: invalid samples in the run).  On return cmin0 / cmin1
+// hold the running minimum over cameras of the two planes' costs.
+template <int RHO, bool HALF, int TH>
+__device__ __forceinline__ void pair_pass(const CamS& C, const float* Aj, float d0, float d1, float2* W2,
+                                          const float* Rs, float4* Hs, const float2 (&st)[TH / 8], int base_v,
+                                          float (&cmin0)[TH / 8], float (&cmin1)[TH / 8]) {
+    using G = Geo<RHO, TH, 2>;
+    constexpr int SEG = G::SEG, HH = G::HH, HWL = G::HWL, WS = G::WS, WS2 = G::WS2, HS = G::HS;
+    constexpr int NPOS = G::NPOS, N = G::N;
+    const int tid = threadIdx.x;
+    float4* Ha = Hs;
+    float4* Hb = Hs + HH * HS;
+    // phase A: warped sample pairs of the tile + halo
+    int bad = 0;
+#pragma unroll 3
+    for (int i = 0; i < G::PPT; ++i) {
+        int p = tid + i * NT;
+        if (p < NPOS) {
+            const float4 a = make_float4(Aj[p], Aj[NPOS + p], Aj[2 * NPOS + p], 0.f);
+            float2 w = warp_sample2<HALF>(C, make_float2(fmaf(d0, a.x, C.t[0]), fmaf(d1, a.x, C.t[0])),
+                                          make_float2(fmaf(d0, a.y, C.t[1]), fmaf(d1, a.y, C.t[1])),
+                                          make_float2(fmaf(d0, a.z, C.t[2]), fmaf(d1, a.z, C.t[2])));
+            bad |= isnan(w.x) | isnan(w.y);
+            int hy = p / HWL, hx = p - hy * HWL;
+            W2[hy * WS2 + hx] = w;
+        }
+    }
+    bad = __syncthreads_or(bad);
+    // phase H: sliding horizontal sums of both planes along a run of one halo row
+    const int hrow = tid & 31, hrun = tid >> 5;
+    if (hrow < HH && hrun < TW / RUN) {
+        const float2* wr = W2 + hrow * WS2 + RUN * hrun;
+        const float* rr = Rs + hrow * WS + RUN * hrun;
+        float2 w[2 * G::NV2];
+        float r[4 * G::NV];
+#pragma unroll
+        for (int qq = 0; qq < G::NV2; ++qq) {
+            float4 a = *reinterpret_cast<const float4*>(wr + 2 * qq);
+            w[2 * qq] = make_float2(a.x, a.y);
+            w[2 * qq + 1] = make_float2(a.z, a.w);
+        }
+#pragma unroll
+        for (int qq = 0; qq < G::NV; ++qq) {
+            float4 b = *reinterpret_cast<const float4*>(rr + 4 * qq);
+            r[4 * qq] = b.x; r[4 * qq + 1] = b.y; r[4 * qq + 2] = b.z; r[4 * qq + 3] = b.w;
+        }
+        float4* ha = Ha + hrow * HS + RUN * hrun;
+        float4* hb = Hb + hrow * HS + RUN * hrun;
+        float2 sw = dup2(0.f), sww = dup2(0.f), srw = dup2(0.f), sm = dup2(0.f);
+        if (!bad) {  // every sample of the tile is valid (the common case)
+#pragma unroll
+            for (int t = 0; t <= 2 * RHO; ++t) {
+                sw = add2(sw, w[t]);
+                sww = fma2(w[t], w[t], sww);
+                srw = fma2(dup2(r[t]), w[t], srw);
+            }
+            ha[0] = make_float4(sw.x, sw.y, sww.x, sww.y);
+            hb[0] = make_float4(srw.x, srw.y, 0.f, 0.f);
+#pragma unroll
+            for (int o = 1; o < RUN; ++o) {
+                const int a = o + 2 * RHO, b = o - 1;
+                sw = add2(sw, add2(w[a], neg2(w[b])));
+                sww = add2(sww, fma2(w[a], w[a], mul2(neg2(w[b]), w[b])));
+                srw = add2(srw, fma2(dup2(r[a]), w[a], mul2(dup2(-r[b]), w[b])));
+                ha[o] = make_float4(sw.x, sw.y, sww.x, sww.y);
+                hb[o] = make_float4(srw.x, srw.y, 0.f, 0.f);
+            }
+        } else {  // invalid samples: excluded from the sums and counted
+#pragma unroll
+            for (int t = 0; t <= 2 * RHO; ++t) {
+                const bool bx = isnan(w[t].x), by = isnan(w[t].y);
+                const float2 wt = make_float2(bx ? 0.0f : w[t].x, by ? 0.0f : w[t].y);
+                sw = add2(sw, wt);
+                sww = fma2(wt, wt, sww);
+                srw = fma2(dup2(r[t]), wt, srw);
+                sm = add2(sm, make_float2(bx ? 1.0f : 0.0f, by ? 1.0f : 0.0f));
+            }
+            ha[0] = make_float4(sw.x, sw.y, sww.x, sww.y);
+            hb[0] = make_float4(srw.x, srw.y, sm.x, sm.y);
+#pragma unroll
+            for (int o = 1; o < RUN; ++o) {
+                const int a = o + 2 * RHO, b = o - 1;
+                const bool ax = isnan(w[a].x), ay = isnan(w[a].y), bx = isnan(w[b].x), by = isnan(w[b].y);
+                const float2 wa = make_float2(ax ? 0.0f : w[a].x, ay ? 0.0f : w[a].y);
+                const float2 wb = make_float2(bx ? 0.0f : w[b].x, by ? 0.0f : w[b].y);
+                sw = add2(sw, add2(wa, neg2(wb)));
+                sww = add2(sww, fma2(wa, wa, mul2(neg2(wb), wb)));
+                srw = add2(srw, fma2(dup2(r[a]), wa, mul2(dup2(-r[b]), wb)));
+                sm = add2(sm, add2(make_float2(ax ? 1.0f : 0.0f, ay ? 1.0f : 0.0f),
+                                   neg2(make_float2(bx ? 1.0f : 0.0f, by ? 1.0f : 0.0f))));
+                ha[o] = make_float4(sw.x, sw.y, sww.x, sww.y);
+                hb[o] = make_float4(srw.x, srw.y, sm.x, sm.y);
+            }
+        }
+    }
+    __syncthreads();
+    // phase V: sliding vertical sums of both planes down SEG rows, ZNCC, minimum over cameras
+    float2 vs = dup2(0.f), vss = dup2(0.f), vrs = dup2(0.f), vm = dup2(0.f);
+#pragma unroll
+    for (int dy = 0; dy <= 2 * RHO; ++dy) {
+        const float4 a = Ha[base_v + dy * HS], b = Hb[base_v + dy * HS];
+        vs = add2(vs, make_float2(a.x, a.y));
+        vss = add2(vss, make_float2(a.z, a.w));
+        vrs = add2(vrs, make_float2(b.x, b.y));
+        vm = add2(vm, make_float2(b.z, b.w));
+    }
+#pragma unroll
+    for (int i = 0; i < SEG; ++i) {
+        if (i > 0) {
+            const float4 a = Ha[base_v + (i + 2 * RHO) * HS], b = Hb[base_v + (i + 2 * RHO) * HS];
+            const float4 c = Ha[base_v + (i - 1) * HS], d = Hb[base_v + (i - 1) * HS];
+            vs = add2(vs, add2(make_float2(a.x, a.y), make_float2(-c.x, -c.y)));
+            vss = add2(vss, add2(make_float2(a.z, a.w), make_float2(-c.z, -c.w)));
+            vrs = add2(vrs, add2(make_float2(b.x, b.y), make_float2(-d.x, -d.y)));
+            vm = add2(vm, add2(make_float2(b.z, b.w), make_float2(-d.z, -d.w)));
+        }
+        const float2 var_w = fma2(mul2(neg2(vs), dup2(1.0f / (float)N)), vs, vss);
+        const float2 cov = fma2(dup2(-st[i].x), vs, vrs);
+        const float2 zr = mul2(mul2(cov, dup2(st[i].y)), make_float2(rsqrtf(var_w.x), rsqrtf(var_w.y)));
+        const float2 z = make_float2(fminf(1.0f, fmaxf(-1.0f, zr.x)), fminf(1.0f, fmaxf(-1.0f, zr.y)));  // |ZNCC| <= 1
+        const float2 cost = fma2(dup2(-0.5f), z, dup2(0.5f));
+        const bool ref_ok = !isnan(st[i].y);
+        const bool ok0 = vm.x == 0.0f && var_w.x >= (float)N * 1e-8f && ref_ok;
+        const bool ok1 = vm.y == 0.0f && var_w.y >= (float)N * 1e-8f && ref_ok;
+        cmin0[i] = ok0 ? fminf(cmin0[i], cost.x) : cmin0[i];
+        cmin1[i] = ok1 ? fminf(cmin1[i], cost.y) : cmin1[i];
+    }
+}
 
 // Parabola through the winner and its neighbours in the same plane set, and
 // the range along the pixel's ray; writes the level outputs of one pixel.
@@ -286,10 +466,11 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
     const int tile = item / L.n_chunks, chunk = item - tile * L.n_chunks;
     const int k_lo = chunk * L.chunk, k_hi = min(L.n_planes, k_lo + L.chunk);
     constexpr int HH = G::HH, HWL = G::HWL, WS = G::WS, HS = G::HS, NPOS = G::NPOS, N = G::N;
-    float4* Hs = reinterpret_cast<float4*>(smem_raw);            // [HH][HS] window sums
-    float4* A = Hs + HH * HS;                                     // [n_cams][NPOS] (R_j r / n.r); NaN = none
-    float* Ws = reinterpret_cast<float*>(A + L.n_cams * NPOS);    // [KP][HH][WS] warped samples of the group (NaN = invalid)
-    float* Rs = Ws + KP * HH * WS;                                // [HH][WS] reference intensities
+    float4* Hs = reinterpret_cast<float4*>(smem_raw);            // [KP][HH][HS] window sums
+    float* Ws = reinterpret_cast<float*>(Hs + KP * HH * HS);      // warped samples (NaN = invalid): KP = 1 [HH][WS],
+    float2* W2 = reinterpret_cast<float2*>(Ws);                   //   KP = 2 [HH][WS2] pairs (plane k0, plane k0 + 1)
+    float* Rs = Ws + (KP == 2 ? 2 * HH * G::WS2 : HH * WS);       // [HH][WS] reference intensities
+    float* A = Rs + HH * WS;                                      // [n_cams][3][NPOS] R_j r / (n . r); NaN = none
     const int tid = threadIdx.x;
     const int tx = tile % L.tiles_x, ty = tile / L.tiles_x;
     const int gx0 = tx * TW - RHO, gy0 = ty * TH - RHO;
@@ -339,9 +520,10 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
             float inv = nr > 0.0f ? 1.0f / nr : nan;
             for (int j = 0; j < L.n_cams; ++j) {
                 const CamS& C = cams[j];
-                A[j * NPOS + p] = make_float4(inv * fmaf(C.R[0], r.x, fmaf(C.R[1], r.y, C.R[2] * r.z)),
-                                              inv * fmaf(C.R[3], r.x, fmaf(C.R[4], r.y, C.R[5] * r.z)),
-                                              inv * fmaf(C.R[6], r.x, fmaf(C.R[7], r.y, C.R[8] * r.z)), 0.f);
+                float* Aj = A + j * 3 * NPOS;
+                Aj[p] = inv * fmaf(C.R[0], r.x, fmaf(C.R[1], r.y, C.R[2] * r.z));
+                Aj[NPOS + p] = inv * fmaf(C.R[3], r.x, fmaf(C.R[4], r.y, C.R[5] * r.z));
+                Aj[2 * NPOS + p] = inv * fmaf(C.R[6], r.x, fmaf(C.R[7], r.y, C.R[8] * r.z));
             }
         }
         __syncthreads();
@@ -357,39 +539,29 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
                 for (int i = 0; i < SEG; ++i) cmin[q][i] = inf;
             for (int j = 0; j < L.n_cams; ++j) {
                 const CamS& C = cams[j];
-                const float4* Aj = A + j * NPOS;
-                // phase A: warped samples of the tile + halo for the group's planes
+                const float* Aj = A + j * 3 * NPOS;
                 const float d0 = __ldg(&L.planes[k0].d);
                 const float d1 = __ldg(&L.planes[k0 + np - 1].d);
-                int bad = 0;
+                if constexpr (KP == 2) {
+                    pair_pass<RHO, HALF, TH>(C, Aj, d0, d1, W2, Rs, Hs, st, base_v, cmin[0], cmin[1]);
+                } else {
+                    // phase A: warped samples of the tile + halo for the plane
+                    int bad = 0;
 #pragma unroll 3
-                for (int i = 0; i < G::PPT; ++i) {
-                    int p = tid + i * NT;
-                    if (p < NPOS) {
-                        float4 a = Aj[p];
-                        float w0 = warp_sample<HALF>(C, fmaf(d0, a.x, C.t[0]), fmaf(d0, a.y, C.t[1]), fmaf(d0, a.z, C.t[2]));
-                        if constexpr (KP == 2) {  // both gathers in flight before the stores
-                            float w1 = warp_sample<HALF>(C, fmaf(d1, a.x, C.t[0]), fmaf(d1, a.y, C.t[1]),
-                                                         fmaf(d1, a.z, C.t[2]));
-                            bad |= isnan(w0) | isnan(w1);
-                            int hy = p / HWL, hx = p - hy * HWL;
-                            Ws[hy * WS + hx] = w0;
-                            Ws[HH * WS + hy * WS + hx] = w1;
-                        } else {
+                    for (int i = 0; i < G::PPT; ++i) {
+                        int p = tid + i * NT;
+                        if (p < NPOS) {
+                            const float4 a = make_float4(Aj[p], Aj[NPOS + p], Aj[2 * NPOS + p], 0.f);
+                            float w0 = warp_sample<HALF>(C, fmaf(d0, a.x, C.t[0]), fmaf(d0, a.y, C.t[1]), fmaf(d0, a.z, C.t[2]));
                             bad |= isnan(w0);
                             int hy = p / HWL, hx = p - hy * HWL;
                             Ws[hy * WS + hx] = w0;
                         }
                     }
-                }
-                bad = __syncthreads_or(bad);
-#pragma unroll
-                for (int q = 0; q < KP; ++q) {
-                    if (q >= np) break;
-                    if (q > 0) __syncthreads();  // the previous plane's vertical pass is done with H
+                    bad = __syncthreads_or(bad);
                     // phase H: sliding horizontal sums along a run of one halo row
                     if (hrow < HH && hrun < TW / RUN) {
-                        const float* wr = Ws + q * HH * WS + hrow * WS + RUN * hrun;
+                        const float* wr = Ws + hrow * WS + RUN * hrun;
                         const float* rr = Rs + hrow * WS + RUN * hrun;
                         float w[4 * G::NV], r[4 * G::NV];
 #pragma unroll
@@ -460,7 +632,7 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
                         bool ok = v.w == 0.0f && var_w >= (float)N * 1e-8f && !isnan(st[i].y);
                         float z = fminf(1.0f, fmaxf(-1.0f, cov * st[i].y * rsqrtf(var_w)));  // |ZNCC| <= 1
                         float cost = fmaf(-0.5f, z, 0.5f);
-                        cmin[q][i] = ok ? fminf(cmin[q][i], cost) : cmin[q][i];
+                        cmin[0][i] = ok ? fminf(cmin[0][i], cost) : cmin[0][i];
                     }
                 }
             }
@@ -575,6 +747,9 @@ __device__ __forceinline__ void sweep_item(const LevelD& L, int half, int item, 
         c.hm1 = (float)(J.cam.height - 1);
         c.width = J.cam.width;
         c.quad = J.quad;
+        c.xi2 = dup2(c.xi); c.fx2 = dup2(c.fx); c.fy2 = dup2(c.fy); c.cx2 = dup2(c.cx); c.cy2 = dup2(c.cy);
+        c.k12 = dup2(c.k1); c.k22 = dup2(c.k2); c.p12 = dup2(c.p1); c.p1x2 = dup2(2.0f * c.p1);
+        c.p22 = dup2(c.p2); c.p2x2 = dup2(2.0f * c.p2); c.lim2 = dup2(c.lim);
     }
     __syncthreads();
     if (half) {
