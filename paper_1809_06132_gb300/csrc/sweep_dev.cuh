@@ -301,7 +301,7 @@ __device__ __forceinline__ void pair_pass(const CamS& C, const float* Aj, float 
     float4* Hb = Hs + HH * HS;
     // phase A: warped sample pairs of the tile + halo
     int bad = 0;
-#pragma unroll 3
+#pragma unroll
     for (int i = 0; i < G::PPT; ++i) {
         int p = tid + i * NT;
         if (p < NPOS) {
