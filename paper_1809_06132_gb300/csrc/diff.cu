@@ -13,13 +13,14 @@
 //   soft_fwd_kernel  per plane and camera, warp the tile + window halo into
 //                    shared memory; two-pass window ZNCC per pixel; minimum
 //                    over cameras; online softmax over planes.
-//   soft_bwd_kernel  recomputes the same costs (bit-identical), forms
-//                    dL/dC_k, spreads dL/dZNCC over both windows with shared
-//                    atomics, then per warped halo sample scatters dL/dI to
-//                    the 4 bilinear texels and chains dL/dw through the
-//                    bilinear slope and the projection Jacobian to a left
-//                    perturbation (w, v) of each ref_to_cam pose (CTA
-//                    reduction, FP64 atomics).
+//   soft_bwd_kernel  recomputes the same costs (bit-identical) while keeping
+//                    each warped sample's bilinear cell and pose derivative,
+//                    forms dL/dC_k, spreads dL/dZNCC over both windows as
+//                    separable box sums of per-pixel coefficients, then per
+//                    warped halo sample scatters dL/dI to the 4 bilinear
+//                    texels and adds dL/dw times the sample's pose
+//                    derivative to a left perturbation (w, v) of each
+//                    ref_to_cam pose (CTA reduction, FP64 atomics).
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -233,17 +234,110 @@ struct GradOut {
     float* cam[PS_MAX_CAMS];
 };
 
+// Shared-memory layout of the backward kernel (floats), for window radius
+// RHO and nc matching cameras.  nf = 4 nc + 3 coefficient fields.
+template <int RHO>
+struct BwdLayout {
+    static constexpr int HW = DT + 2 * RHO, NPOS = HW * HW, BUF = HW * DS;
+    static constexpr int FS = DT + 1;  // field row stride
+    __host__ __device__ static constexpr int nf(int nc) { return 4 * nc + 3; }
+    // Rs, gR, nc x (Ws, gW), chain data (8 floats + 1 cell per sample and
+    // camera), horizontal box sums [nf][DT][HW], fields / vertical box sums
+    // [nf][NPOS] (the fields [nf][DT][FS] are dead once the horizontal sums exist)
+    __host__ __device__ static constexpr size_t floats(int nc) {
+        return (size_t)(2 + 2 * nc) * BUF + (size_t)nc * NPOS * 9 + (size_t)nf(nc) * DT * HW +
+               (size_t)nf(nc) * NPOS;
+    }
+    static_assert(NPOS >= DT * FS, "the vertical sums reuse the field storage");
+};
+
+// The sample of halo position (gx, gy) through plane P in camera C, with
+// what the chain rule needs later: the bilinear cell (y0 << 16 | x0, -1 when
+// invalid), its weights (ax, ay) and m = (X x g, g), g = J^T (dw/du, dw/dv),
+// J the 2 x 3 projection Jacobian at X (camera frame); gw m is then the
+// sample's contribution to the gradient of a left perturbation (w, v) of
+// ref_to_cam.  w is computed exactly as in the forward (warp_at).
+struct WarpJ {
+    float w;
+    int cell;
+    float ax, ay;
+    float m[6];
+};
+
+__device__ __forceinline__ WarpJ warp_jac(const DiffP& P, const DiffCam& C, const PlaneD& pl, int gx, int gy) {
+    WarpJ o;
+    const Warp wp = warp_at(P, C, pl, gx, gy);
+    o.w = wp.w;
+    o.cell = -1;
+    o.ax = o.ay = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) o.m[i] = 0.f;
+    if (isnan(wp.w)) return o;
+    const int Wc = C.c.width;
+    const int xa = (int)floorf(wp.u), ya = (int)floorf(wp.v);
+    const int xb = min(xa + 1, Wc - 1), yb = min(ya + 1, C.c.height - 1);
+    const float ax = wp.u - (float)xa, ay = wp.v - (float)ya;
+    const float* I = C.img;
+    const float i00 = I[(size_t)ya * Wc + xa], i10 = I[(size_t)ya * Wc + xb];
+    const float i01 = I[(size_t)yb * Wc + xa], i11 = I[(size_t)yb * Wc + xb];
+    const float dwdu = (1.f - ay) * (i10 - i00) + ay * (i11 - i01);
+    const float dwdv = (1.f - ax) * (i01 - i00) + ax * (i11 - i10);
+    float J[6];
+    project_jac_f(C.c, wp.X, wp.Y, wp.Z, J);
+    float g[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) g[i] = dwdu * J[i] + dwdv * J[3 + i];
+    o.cell = (ya << 16) | xa;
+    o.ax = ax;
+    o.ay = ay;
+    o.m[0] = wp.Y * g[2] - wp.Z * g[1];
+    o.m[1] = wp.Z * g[0] - wp.X * g[2];
+    o.m[2] = wp.X * g[1] - wp.Y * g[0];
+    o.m[3] = g[0];
+    o.m[4] = g[1];
+    o.m[5] = g[2];
+    return o;
+}
+
+// Backward of the soft sweep for one 16 x 16 tile.  Per plane:
+//  1. warp the halo for every camera (samples + chain data, warp_jac);
+//  2. per pixel, the plane's cost and winning camera jb as in the forward,
+//     dL/dC, and the ZNCC gradient coefficients ka = gz / sqrt(va vb),
+//     kz_a = gz z / va, kz_b = gz z / vb (gz = dL/dZNCC);
+//  3. window gradients as box sums.  For a window sample q of pixel p,
+//       dZNCC/da_q = (b_q - mb) / sqrt(va vb) - z (a_q - ma) / va   (a: ref)
+//       dZNCC/db_q = (a_q - ma) / sqrt(va vb) - z (b_q - mb) / vb   (b: camera jb)
+//     so, summed over the pixels whose window holds q,
+//       gW_j(q) = a_q A1_j - A2_j - b_q A3_j + A4_j
+//       gR(q)  += sum_j b_j(q) A1_j - B1 - a_q B2 + B3
+//     with A1_j..A4_j the (2 RHO + 1)^2 box sums of ka, ka ma, kz_b, kz_b mb
+//     over pixels with jb = j, and B1..B3 those of ka mb, kz_a, kz_a ma.
+//     Intensities are taken relative to a per-tile centre (a) and a
+//     per-plane, per-camera centre (b), which leaves every difference
+//     unchanged and keeps the products small.  The box sums are separable
+//     (rows, then columns) in shared memory: no atomics;
+//  4. chain every sample with dL/dw != 0: dL/dI to its four texels (global
+//     atomics) and gw m to the pose accumulators.
+// After the planes: dL/dref of the halo (global atomics) and the CTA's pose
+// gradient (FP64 atomics).
 template <int RHO>
 __global__ void __launch_bounds__(DNT) soft_bwd_kernel(const __grid_constant__ DiffP P, const float* aux,
                                                       const float* g_range, const float* g_cost, float* g_ref,
                                                       const __grid_constant__ GradOut G, double* g_pose) {
-    constexpr int HW = DT + 2 * RHO, NPOS = HW * HW, BUF = HW * DS;
+    using BL = BwdLayout<RHO>;
+    constexpr int HW = BL::HW, NPOS = BL::NPOS, BUF = BL::BUF, FS = BL::FS;
+    const int nc = P.n_cams, nf = BL::nf(nc);
     extern __shared__ float sm[];
-    float* Rs = sm;                   // reference
-    float* gR = Rs + BUF;             // dL/dref, summed over planes
-    float* Ws = gR + BUF;             // [n_cams] warped samples of the current plane
-    float* gW = Ws + P.n_cams * BUF;  // [n_cams] dL/dw of the current plane
+    float* Rs = sm;                                   // reference
+    float* gR = Rs + BUF;                             // dL/dref, summed over planes
+    float* Ws = gR + BUF;                             // [nc] warped samples of the current plane
+    float* gW = Ws + nc * BUF;                        // [nc] dL/dw of the current plane
+    float* Cm = gW + nc * BUF;                        // [nc][8][NPOS] m[0..5], ax, ay
+    int* Cc = reinterpret_cast<int*>(Cm + nc * 8 * NPOS);  // [nc][NPOS] bilinear cell
+    float* Hx = reinterpret_cast<float*>(Cc + nc * NPOS);  // [nf][DT][HW] horizontal box sums
+    float* FV = Hx + nf * DT * HW;                    // [nf][DT][FS] fields, then [nf][NPOS] box sums
     __shared__ float red[DNT / 32][6 * PS_MAX_CAMS];
+    __shared__ float cb[PS_MAX_CAMS];
     const int tid = threadIdx.x, lx = tid % DT, ly = tid / DT;
     const int x0 = blockIdx.x * DT - RHO, y0 = blockIdx.y * DT - RHO;
     const int gx = blockIdx.x * DT + lx, gy = blockIdx.y * DT + ly;
@@ -270,22 +364,36 @@ __global__ void __launch_bounds__(DNT) soft_bwd_kernel(const __grid_constant__ D
     float pose_acc[6 * PS_MAX_CAMS];
 #pragma unroll
     for (int i = 0; i < 6 * PS_MAX_CAMS; ++i) pose_acc[i] = 0.f;
+    __syncthreads();
+    const int qc = (RHO + DT / 2) * DS + RHO + DT / 2;  // centre of the tile
+    const float ca = Rs[qc];
     for (int k = 0; k < P.K; ++k) {
         const PlaneD pl = P.planes[k];
-        __syncthreads();
+        __syncthreads();  // the previous plane's chain is done with gW and the chain data
+        // 1. samples and chain data of the halo
         for (int p = tid; p < NPOS; p += DNT) {
             const int hx = p % HW, hy = p / HW;
-            for (int j = 0; j < P.n_cams; ++j) {
-                Ws[j * BUF + hy * DS + hx] = warp_at(P, P.cams[j], pl, x0 + hx, y0 + hy).w;
-                gW[j * BUF + hy * DS + hx] = 0.f;
+            for (int j = 0; j < nc; ++j) {
+                const WarpJ wj = warp_jac(P, P.cams[j], pl, x0 + hx, y0 + hy);
+                Ws[j * BUF + hy * DS + hx] = wj.w;
+                float* cm = Cm + j * 8 * NPOS + p;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) cm[i * NPOS] = wj.m[i];
+                cm[6 * NPOS] = wj.ax;
+                cm[7 * NPOS] = wj.ay;
+                Cc[j * NPOS + p] = wj.cell;
             }
         }
         __syncthreads();
-        // the pixel's cost for this plane (as in the forward) and its camera
+        if (tid < nc) {
+            const float c = Ws[tid * BUF + qc];
+            cb[tid] = isnan(c) ? 0.f : c;
+        }
+        // 2. the pixel's cost for this plane (as in the forward), its camera and coefficients
         float best = inf;
         int jb = -1;
         Zn zb;
-        for (int j = 0; use && j < P.n_cams; ++j) {
+        for (int j = 0; use && j < nc; ++j) {
             Zn zn;
             if (window_zncc<RHO>(Rs, Ws + j * BUF, lx, ly, &zn)) {
                 float c = 0.5f * (1.0f - zn.z);
@@ -296,63 +404,114 @@ __global__ void __launch_bounds__(DNT) soft_bwd_kernel(const __grid_constant__ D
                 }
             }
         }
+        __syncthreads();  // cb
+        float ka = 0.f, kza = 0.f, kzb = 0.f, mac = 0.f, mbc = 0.f;
         if (jb >= 0) {
             const float s = __expf(-(best - cmin) / P.T) / Z;
             const float rho_k = (pl.nx * ray.x + pl.ny * ray.y + pl.nz * ray.z) / pl.d;
             const float gC = gE * (-s * (rho_k - E) / P.T) + gs * s;
             const float gz = -0.5f * gC;
-            const float* Wj = Ws + jb * BUF;
-            float* gWj = gW + jb * BUF;
-            const float ka = gz / zb.sab, kz_a = gz * zb.z / zb.va, kz_b = gz * zb.z / zb.vb;
-#pragma unroll
-            for (int dy = 0; dy <= 2 * RHO; ++dy)
-#pragma unroll
-                for (int dx = 0; dx <= 2 * RHO; ++dx) {
-                    const int q = (ly + dy) * DS + lx + dx;
-                    float ea = Rs[q] - zb.ma, eb = Wj[q] - zb.mb;
-                    atomicAdd(&gR[q], fmaf(ka, eb, -kz_a * ea));
-                    atomicAdd(&gWj[q], fmaf(ka, ea, -kz_b * eb));
-                }
+            ka = gz / zb.sab;
+            kza = gz * zb.z / zb.va;
+            kzb = gz * zb.z / zb.vb;
+            mac = zb.ma - ca;
+            mbc = zb.mb - cb[jb];
+        }
+        {
+            float* F = FV + ly * FS + lx;
+            for (int j = 0; j < nc; ++j) {
+                const bool mine = j == jb;
+                F[(4 * j + 0) * DT * FS] = mine ? ka : 0.f;
+                F[(4 * j + 1) * DT * FS] = mine ? ka * mac : 0.f;
+                F[(4 * j + 2) * DT * FS] = mine ? kzb : 0.f;
+                F[(4 * j + 3) * DT * FS] = mine ? kzb * mbc : 0.f;
+            }
+            F[(4 * nc + 0) * DT * FS] = ka * mbc;
+            F[(4 * nc + 1) * DT * FS] = kza;
+            F[(4 * nc + 2) * DT * FS] = kza * mac;
         }
         __syncthreads();
-        // chain dL/dw of every warped halo sample to the image and the pose
+        // 3a. horizontal box sums: halo column c collects pixels c - 2 RHO .. c of the row.
+        // Direct sums, not running ones: coefficients of low-texture windows are
+        // large, and a running sum would leave their rounding residue where the
+        // exact sum is zero
+        for (int it = tid; it < nf * DT; it += DNT) {
+            const float* fr = FV + it * FS;
+            float* hr = Hx + it * HW;
+            float v[DT];
+#pragma unroll
+            for (int x = 0; x < DT; ++x) v[x] = fr[x];
+#pragma unroll
+            for (int c = 0; c < HW; ++c) {
+                float acc = 0.f;
+#pragma unroll
+                for (int x = (c - 2 * RHO > 0 ? c - 2 * RHO : 0); x <= (c < DT - 1 ? c : DT - 1); ++x) acc += v[x];
+                hr[c] = acc;
+            }
+        }
+        __syncthreads();
+        // 3b. vertical box sums: halo row r collects rows r - 2 RHO .. r
+        for (int it = tid; it < nf * HW; it += DNT) {
+            const int f = it / HW, c = it - f * HW;
+            const float* hc = Hx + f * DT * HW + c;
+            float* vc = FV + f * NPOS + c;
+            float v[DT];
+#pragma unroll
+            for (int y = 0; y < DT; ++y) v[y] = hc[y * HW];
+#pragma unroll
+            for (int r = 0; r < HW; ++r) {
+                float acc = 0.f;
+#pragma unroll
+                for (int y = (r - 2 * RHO > 0 ? r - 2 * RHO : 0); y <= (r < DT - 1 ? r : DT - 1); ++y) acc += v[y];
+                vc[r * HW] = acc;
+            }
+        }
+        __syncthreads();
+        // 3c. per halo sample: dL/dw of every camera and this plane's part of dL/dref
+        for (int p = tid; p < NPOS; p += DNT) {
+            const int hx = p % HW, hy = p / HW, q = hy * DS + hx;
+            const float* V = FV + p;
+            const float a = Rs[q] - ca;
+            float g = -V[(4 * nc + 0) * NPOS] - a * V[(4 * nc + 1) * NPOS] + V[(4 * nc + 2) * NPOS];
+            for (int j = 0; j < nc; ++j) {
+                const float A1 = V[(4 * j + 0) * NPOS], A2 = V[(4 * j + 1) * NPOS];
+                const float A3 = V[(4 * j + 2) * NPOS], A4 = V[(4 * j + 3) * NPOS];
+                const float bw = Ws[j * BUF + q];
+                float gw = 0.f;
+                if (!isnan(bw)) {  // an invalid sample is in no used window: all its sums are zero
+                    const float b = bw - cb[j];
+                    gw = a * A1 - A2 - b * A3 + A4;
+                    g += b * A1;
+                }
+                gW[j * BUF + q] = gw;
+            }
+            gR[q] += g;
+        }
+        __syncthreads();
+        // 4. chain dL/dw of every warped halo sample to the image and the pose
         for (int p = tid; p < NPOS; p += DNT) {
             const int hx = p % HW, hy = p / HW;
 #pragma unroll
             for (int j = 0; j < PS_MAX_CAMS; ++j) {
-                if (j >= P.n_cams) break;
+                if (j >= nc) break;
                 const float gw = gW[j * BUF + hy * DS + hx];
-                if (gw == 0.f) continue;
-                const DiffCam& C = P.cams[j];
-                Warp wp = warp_at(P, C, pl, x0 + hx, y0 + hy);
-                int xa = (int)floorf(wp.u), ya = (int)floorf(wp.v);
-                int xb = min(xa + 1, C.c.width - 1), yb = min(ya + 1, C.c.height - 1);
-                if (!PS_DCHECK(xa >= 0 && ya >= 0 && xa < C.c.width && ya < C.c.height, CHK_GATHER)) continue;
-                float ax = wp.u - (float)xa, ay = wp.v - (float)ya;
-                const float* I = C.img;
-                const int Wc = C.c.width;
-                float i00 = I[(size_t)ya * Wc + xa], i10 = I[(size_t)ya * Wc + xb];
-                float i01 = I[(size_t)yb * Wc + xa], i11 = I[(size_t)yb * Wc + xb];
+                const int cell = Cc[j * NPOS + p];
+                if (gw == 0.f || cell < 0) continue;
+                const float* cm = Cm + j * 8 * NPOS + p;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) pose_acc[6 * j + i] = fmaf(gw, cm[i * NPOS], pose_acc[6 * j + i]);
                 if (G.cam[j]) {
+                    const DiffCam& C = P.cams[j];
+                    const int Wc = C.c.width, xa = cell & 0xffff, ya = cell >> 16;
+                    if (!PS_DCHECK(xa < Wc && ya < C.c.height, CHK_GATHER)) continue;
+                    const int xb = min(xa + 1, Wc - 1), yb = min(ya + 1, C.c.height - 1);
+                    const float ax = cm[6 * NPOS], ay = cm[7 * NPOS];
                     float* Gj = G.cam[j];
                     atomicAdd(&Gj[(size_t)ya * Wc + xa], gw * (1.f - ax) * (1.f - ay));
                     atomicAdd(&Gj[(size_t)ya * Wc + xb], gw * ax * (1.f - ay));
                     atomicAdd(&Gj[(size_t)yb * Wc + xa], gw * (1.f - ax) * ay);
                     atomicAdd(&Gj[(size_t)yb * Wc + xb], gw * ax * ay);
                 }
-                float dwdu = (1.f - ay) * (i10 - i00) + ay * (i11 - i01);
-                float dwdv = (1.f - ax) * (i01 - i00) + ax * (i11 - i10);
-                float J[6];
-                project_jac_f(C.c, wp.X, wp.Y, wp.Z, J);
-                float gx3[3];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) gx3[i] = gw * (dwdu * J[i] + dwdv * J[3 + i]);
-                pose_acc[6 * j + 0] += wp.Y * gx3[2] - wp.Z * gx3[1];
-                pose_acc[6 * j + 1] += wp.Z * gx3[0] - wp.X * gx3[2];
-                pose_acc[6 * j + 2] += wp.X * gx3[1] - wp.Y * gx3[0];
-                pose_acc[6 * j + 3] += gx3[0];
-                pose_acc[6 * j + 4] += gx3[1];
-                pose_acc[6 * j + 5] += gx3[2];
             }
         }
     }
@@ -525,16 +684,22 @@ extern "C" int psdiff_backward(psdiff_t* h, const float* const* images, const ps
     float* g_ref = g_images ? g_images[0] : nullptr;
     GradOut G;
     for (int j = 0; j < PS_MAX_CAMS; ++j) G.cam[j] = (g_images && j < h->n_cams) ? g_images[1 + j] : nullptr;
-    const int hw = 16 + 2 * P.rho;
-    const size_t smem = sizeof(float) * (size_t)hw * 48 * (2 + 2 * P.n_cams);  // at most 46 KB
+    // at most 202 KB (window 9, 4 cameras)
+    const size_t smem = sizeof(float) * (P.rho == 2   ? BwdLayout<2>::floats(P.n_cams)
+                                         : P.rho == 3 ? BwdLayout<3>::floats(P.n_cams)
+                                                      : BwdLayout<4>::floats(P.n_cams));
     dim3 grid((P.W + 15) / 16, (P.H + 15) / 16);
     cudaStream_t s = (cudaStream_t)stream;
-    if (P.rho == 2)
+    if (P.rho == 2) {
+        PS_CUDA(cudaFuncSetAttribute(soft_bwd_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         soft_bwd_kernel<2><<<grid, DNT, smem, s>>>(P, aux, g_range, g_cost, g_ref, G, g_pose);
-    else if (P.rho == 3)
+    } else if (P.rho == 3) {
+        PS_CUDA(cudaFuncSetAttribute(soft_bwd_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         soft_bwd_kernel<3><<<grid, DNT, smem, s>>>(P, aux, g_range, g_cost, g_ref, G, g_pose);
-    else
+    } else {
+        PS_CUDA(cudaFuncSetAttribute(soft_bwd_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         soft_bwd_kernel<4><<<grid, DNT, smem, s>>>(P, aux, g_range, g_cost, g_ref, G, g_pose);
+    }
     PS_CUDA(cudaGetLastError());
     return PS_OK;
 }
