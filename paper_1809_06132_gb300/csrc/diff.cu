@@ -240,12 +240,13 @@ template <int RHO>
 struct BwdLayout {
     static constexpr int HW = DT + 2 * RHO, NPOS = HW * HW, BUF = HW * DS;
     static constexpr int FS = DT + 1;  // field row stride
+    static constexpr int HS = HW + 1;  // horizontal-sum row stride (odd: the row-per-thread writes are conflict-free)
     __host__ __device__ static constexpr int nf(int nc) { return 4 * nc + 3; }
     // Rs, gR, nc x (Ws, gW), chain data (8 floats + 1 cell per sample and
-    // camera), horizontal box sums [nf][DT][HW], fields / vertical box sums
+    // camera), horizontal box sums [nf][DT][HS], fields / vertical box sums
     // [nf][NPOS] (the fields [nf][DT][FS] are dead once the horizontal sums exist)
     __host__ __device__ static constexpr size_t floats(int nc) {
-        return (size_t)(2 + 2 * nc) * BUF + (size_t)nc * NPOS * 9 + (size_t)nf(nc) * DT * HW +
+        return (size_t)(2 + 2 * nc) * BUF + (size_t)nc * NPOS * 9 + (size_t)nf(nc) * DT * HS +
                (size_t)nf(nc) * NPOS;
     }
     static_assert(NPOS >= DT * FS, "the vertical sums reuse the field storage");
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(DNT) soft_bwd_kernel(const __grid_constant__ D
                                                       const float* g_range, const float* g_cost, float* g_ref,
                                                       const __grid_constant__ GradOut G, double* g_pose) {
     using BL = BwdLayout<RHO>;
-    constexpr int HW = BL::HW, NPOS = BL::NPOS, BUF = BL::BUF, FS = BL::FS;
+    constexpr int HW = BL::HW, NPOS = BL::NPOS, BUF = BL::BUF, FS = BL::FS, HS = BL::HS;
     const int nc = P.n_cams, nf = BL::nf(nc);
     extern __shared__ float sm[];
     float* Rs = sm;                                   // reference
@@ -334,10 +335,9 @@ __global__ void __launch_bounds__(DNT) soft_bwd_kernel(const __grid_constant__ D
     float* gW = Ws + nc * BUF;                        // [nc] dL/dw of the current plane
     float* Cm = gW + nc * BUF;                        // [nc][8][NPOS] m[0..5], ax, ay
     int* Cc = reinterpret_cast<int*>(Cm + nc * 8 * NPOS);  // [nc][NPOS] bilinear cell
-    float* Hx = reinterpret_cast<float*>(Cc + nc * NPOS);  // [nf][DT][HW] horizontal box sums
-    float* FV = Hx + nf * DT * HW;                    // [nf][DT][FS] fields, then [nf][NPOS] box sums
+    float* Hx = reinterpret_cast<float*>(Cc + nc * NPOS);  // [nf][DT][HS] horizontal box sums
+    float* FV = Hx + nf * DT * HS;                    // [nf][DT][FS] fields, then [nf][NPOS] box sums
     __shared__ float red[DNT / 32][6 * PS_MAX_CAMS];
-    __shared__ float cb[PS_MAX_CAMS];
     const int tid = threadIdx.x, lx = tid % DT, ly = tid / DT;
     const int x0 = blockIdx.x * DT - RHO, y0 = blockIdx.y * DT - RHO;
     const int gx = blockIdx.x * DT + lx, gy = blockIdx.y * DT + ly;
@@ -385,10 +385,11 @@ __global__ void __launch_bounds__(DNT) soft_bwd_kernel(const __grid_constant__ D
             }
         }
         __syncthreads();
-        if (tid < nc) {
-            const float c = Ws[tid * BUF + qc];
-            cb[tid] = isnan(c) ? 0.f : c;
-        }
+        // the per-camera centre of this plane's warped samples (a broadcast read)
+        auto centre = [&](int j) {
+            const float c = Ws[j * BUF + qc];
+            return isnan(c) ? 0.f : c;
+        };
         // 2. the pixel's cost for this plane (as in the forward), its camera and coefficients
         float best = inf;
         int jb = -1;
@@ -404,7 +405,6 @@ __global__ void __launch_bounds__(DNT) soft_bwd_kernel(const __grid_constant__ D
                 }
             }
         }
-        __syncthreads();  // cb
         float ka = 0.f, kza = 0.f, kzb = 0.f, mac = 0.f, mbc = 0.f;
         if (jb >= 0) {
             const float s = __expf(-(best - cmin) / P.T) / Z;
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(DNT) soft_bwd_kernel(const __grid_constant__ D
             kza = gz * zb.z / zb.va;
             kzb = gz * zb.z / zb.vb;
             mac = zb.ma - ca;
-            mbc = zb.mb - cb[jb];
+            mbc = zb.mb - centre(jb);
         }
         {
             float* F = FV + ly * FS + lx;
@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(DNT) soft_bwd_kernel(const __grid_constant__ D
         // exact sum is zero
         for (int it = tid; it < nf * DT; it += DNT) {
             const float* fr = FV + it * FS;
-            float* hr = Hx + it * HW;
+            float* hr = Hx + it * HS;
             float v[DT];
 #pragma unroll
             for (int x = 0; x < DT; ++x) v[x] = fr[x];
@@ -453,11 +453,11 @@ __global__ void __launch_bounds__(DNT) soft_bwd_kernel(const __grid_constant__ D
         // 3b. vertical box sums: halo row r collects rows r - 2 RHO .. r
         for (int it = tid; it < nf * HW; it += DNT) {
             const int f = it / HW, c = it - f * HW;
-            const float* hc = Hx + f * DT * HW + c;
+            const float* hc = Hx + f * DT * HS + c;
             float* vc = FV + f * NPOS + c;
             float v[DT];
 #pragma unroll
-            for (int y = 0; y < DT; ++y) v[y] = hc[y * HW];
+            for (int y = 0; y < DT; ++y) v[y] = hc[y * HS];
 #pragma unroll
             for (int r = 0; r < HW; ++r) {
                 float acc = 0.f;
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(DNT) soft_bwd_kernel(const __grid_constant__ D
                 const float bw = Ws[j * BUF + q];
                 float gw = 0.f;
                 if (!isnan(bw)) {  // an invalid sample is in no used window: all its sums are zero
-                    const float b = bw - cb[j];
+                    const float b = bw - centre(j);
                     gw = a * A1 - A2 - b * A3 + A4;
                     g += b * A1;
                 }
