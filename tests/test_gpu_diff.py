@@ -132,6 +132,45 @@ def test_autograd_images_and_pose(case):
         assert b.abs().max().item() > 0
 
 
+@pytest.mark.parametrize("window,n_cams", [(7, 3), (9, 4)])
+def test_wider_windows_and_more_cameras(window, n_cams):
+    # the other kernel instantiations (window radius 3 and 4) and shared-memory
+    # layouts (3 and 4 cameras) against the oracle: forward maps and gradients
+    import dataclasses
+    wl = scenes.diff(5, width=64, height=48, n_planes=8)
+    cams, poses = list(wl.rig.cams), list(wl.rig.ref_to_cam)
+    for k, dy in enumerate((-0.3, 0.3)[:n_cams - 2]):
+        R = rot_xyz(math.radians(0.5 * (k + 1)), math.radians(-0.4), 0.0)
+        poses.append(Pose(R.T, -R.T @ np.array([0.1, dy, 0.0])))
+        cams.append(cams[k])
+    wl.rig = dataclasses.replace(wl.rig, cams=cams, ref_to_cam=poses)
+    wl.levels = [dataclasses.replace(wl.levels[0], window=window)]
+    imgs, _ = scenes.FrameSource(wl).frame(0)
+    dev = [torch.from_numpy((i.numpy().astype(np.float64) / 255.0).astype(np.float32)).cuda() for i in imgs]
+    ims = [d.double().cpu().numpy() for d in dev]
+    sw = P.SoftSweep(wl.rig, wl.levels[0], temperature=0.05)
+    r, S, aux = sw.forward(dev)
+    orr = oracle.soft_depth(wl.rig, wl.levels[0], ims, T=0.05)
+    rc = r.cpu().numpy()
+    both = (rc > 0) & (orr > 0)
+    assert both.mean() > 0.3 and ((rc > 0) == (orr > 0)).mean() >= 0.99
+    assert np.median(np.abs(rc[both] - orr[both]) / orr[both]) <= 1e-5
+    tied = oracle.soft_depth_ties(wl.rig, wl.levels[0], ims, tau=1e-5, tau_px=3e-5)
+    valid = (rc > 0) & ~tied
+    rng = np.random.default_rng(2)
+    g = (rng.normal(size=valid.shape) * valid).astype(np.float32)
+    gs = (rng.normal(size=valid.shape) * valid).astype(np.float32)
+    gi, gp = sw.backward(dev, None, aux, torch.from_numpy(g).cuda(), torch.from_numpy(gs).cuda())
+    torch.cuda.synchronize()
+    ogi, ogp = oracle.soft_depth_grad(wl.rig, wl.levels[0], ims, g.astype(np.float64), T=0.05,
+                                      g_cost=gs.astype(np.float64))
+    e_pose = [_rel_err(gp[j].cpu().numpy(), ogp[j]) for j in range(n_cams) if np.abs(ogp[j]).max() > 0]
+    e_img = [_rel_err(gi[m].cpu().numpy(), ogi[m]) for m in range(1 + n_cams) if np.abs(ogi[m]).max() > 0]
+    print(f"window {window}, {n_cams} cameras: tied", int(tied.sum()), "pose", e_pose, "image", e_img)
+    assert len(e_pose) >= 2 and len(e_img) >= 3
+    assert max(e_pose) <= 1e-4 and max(e_img) <= 1e-4
+
+
 def _sphere_case():
     cam = scenes.Camera(xi=1.0, fx=40.0, fy=40.0, cx=24.0, cy=20.0, width=48, height=40)
     from scenes.configs import TsdfParams
