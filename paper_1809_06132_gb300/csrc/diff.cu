@@ -10,9 +10,10 @@
 // on a tie), exactly the sweep's cost but on real-valued images.
 //
 // Kernels (one CTA per 16 x 16 output tile, one thread per output pixel):
-//   soft_fwd_kernel  per plane and camera, warp the tile + window halo into
-//                    shared memory; two-pass window ZNCC per pixel; minimum
-//                    over cameras; online softmax over planes.
+//   soft_fwd_kernel  per pair of planes and camera, warp the tile + window
+//                    halo into shared memory; two-pass window ZNCC per pixel
+//                    (both planes on packed FP32 pairs); minimum over
+//                    cameras; online softmax over planes.
 //   soft_bwd_kernel  recomputes the same costs (bit-identical) while keeping
 //                    each warped sample's bilinear cell and pose derivative,
 //                    forms dL/dC_k, spreads dL/dZNCC over both windows as
@@ -97,12 +98,39 @@ struct Warp {
     float X, Y, Z, u, v, w;
 };
 
+// n . r of a plane and a ray.  The plane's offset along the ray, and the
+// bilinear blend below, are written with explicit roundings so that every
+// kernel computes the same samples (the costs decide integers: a camera, a
+// plane) whatever contractions the compiler would choose in each.
+__device__ __forceinline__ float plane_dot(const PlaneD& pl, const float4& r) {
+    return __fmaf_rn(pl.nz, r.z, __fmaf_rn(pl.ny, r.y, __fmul_rn(pl.nx, r.x)));
+}
+
+__device__ __forceinline__ float bilerp(float ax, float ay, float i00, float i10, float i01, float i11) {
+    const float bx = __fsub_rn(1.0f, ax), by = __fsub_rn(1.0f, ay);
+    const float top = __fmaf_rn(ax, i10, __fmul_rn(bx, i00));
+    const float bot = __fmaf_rn(ax, i11, __fmul_rn(bx, i01));
+    return __fmaf_rn(ay, bot, __fmul_rn(by, top));
+}
+
+// Bilinear sample of camera C at (u, v), NaN outside [0, W-1] x [0, H-1].
+__device__ __forceinline__ float sample_uv(const DiffCam& C, float u, float v) {
+    if (!(u >= 0.0f && u <= (float)(C.c.width - 1) && v >= 0.0f && v <= (float)(C.c.height - 1)))
+        return __int_as_float(0x7fc00000);
+    int x0 = (int)floorf(u), y0 = (int)floorf(v);
+    int x1 = min(x0 + 1, C.c.width - 1), y1 = min(y0 + 1, C.c.height - 1);
+    float ax = u - (float)x0, ay = v - (float)y0;
+    const float* I = C.img;
+    return bilerp(ax, ay, I[(size_t)y0 * C.c.width + x0], I[(size_t)y0 * C.c.width + x1],
+                  I[(size_t)y1 * C.c.width + x0], I[(size_t)y1 * C.c.width + x1]);
+}
+
 __device__ __forceinline__ Warp warp_at(const DiffP& P, const DiffCam& C, const PlaneD& pl, int gx, int gy) {
     const float nan = __int_as_float(0x7fc00000);
     Warp o{0.f, 0.f, 0.f, 0.f, 0.f, nan};
     if (gx < 0 || gy < 0 || gx >= P.W || gy >= P.H) return o;
     float4 r = P.rays[(size_t)gy * P.W + gx];
-    float nr = pl.nx * r.x + pl.ny * r.y + pl.nz * r.z;
+    float nr = plane_dot(pl, r);
     if (!(nr > 0.0f)) return o;
     float lam = pl.d / nr;
     float x = lam * r.x, y = lam * r.y, z = lam * r.z;
@@ -111,15 +139,42 @@ __device__ __forceinline__ Warp warp_at(const DiffP& P, const DiffCam& C, const 
     o.Z = fmaf(C.R[6], x, fmaf(C.R[7], y, fmaf(C.R[8], z, C.t[2])));
     float n;
     if (!project_f(C.c, o.X, o.Y, o.Z, &o.u, &o.v, &n)) return o;
-    if (!(o.u >= 0.0f && o.u <= (float)(C.c.width - 1) && o.v >= 0.0f && o.v <= (float)(C.c.height - 1))) return o;
-    int x0 = (int)floorf(o.u), y0 = (int)floorf(o.v);
-    int x1 = min(x0 + 1, C.c.width - 1), y1 = min(y0 + 1, C.c.height - 1);
-    float ax = o.u - (float)x0, ay = o.v - (float)y0;
-    const float* I = C.img;
-    float i00 = I[(size_t)y0 * C.c.width + x0], i10 = I[(size_t)y0 * C.c.width + x1];
-    float i01 = I[(size_t)y1 * C.c.width + x0], i11 = I[(size_t)y1 * C.c.width + x1];
-    o.w = (1.0f - ay) * ((1.0f - ax) * i00 + ax * i10) + ay * ((1.0f - ax) * i01 + ax * i11);
+    o.w = sample_uv(C, o.u, o.v);
     return o;
+}
+
+// warp_at for two planes at once (lane x: p0, lane y: p1): the samples only,
+// with the transform and the projection on packed FP32 pairs.  Per lane
+// every operation and rounding is that of warp_at (2 m = m + m exactly), so
+// each sample is bit-identical to warp_at's.
+__device__ __forceinline__ float2 warp_pair(const DiffP& P, const DiffCam& C, const PlaneD& p0, const PlaneD& p1,
+                                            int gx, int gy) {
+    const float nan = __int_as_float(0x7fc00000);
+    if (gx < 0 || gy < 0 || gx >= P.W || gy >= P.H) return make_float2(nan, nan);
+    const float4 r = P.rays[(size_t)gy * P.W + gx];
+    const float nr0 = plane_dot(p0, r), nr1 = plane_dot(p1, r);
+    const bool f0 = nr0 > 0.0f, f1 = nr1 > 0.0f;
+    if (!(f0 || f1)) return make_float2(nan, nan);
+    const float2 lam = make_float2(p0.d / nr0, p1.d / nr1);
+    const float2 x = mul2(lam, dup2(r.x)), y = mul2(lam, dup2(r.y)), z = mul2(lam, dup2(r.z));
+    const float2 X = fma2(dup2(C.R[0]), x, fma2(dup2(C.R[1]), y, fma2(dup2(C.R[2]), z, dup2(C.t[0]))));
+    const float2 Y = fma2(dup2(C.R[3]), x, fma2(dup2(C.R[4]), y, fma2(dup2(C.R[5]), z, dup2(C.t[1]))));
+    const float2 Z = fma2(dup2(C.R[6]), x, fma2(dup2(C.R[7]), y, fma2(dup2(C.R[8]), z, dup2(C.t[2]))));
+    const CamF& c = C.c;
+    const float2 n2 = fma2(X, X, fma2(Y, Y, mul2(Z, Z)));
+    const float2 n = make_float2(sqrtf(n2.x), sqrtf(n2.y));
+    const float2 den = fma2(dup2(c.xi), n, Z);
+    const float2 inv = make_float2(1.0f / den.x, 1.0f / den.y);
+    const float2 mx = mul2(X, inv), my = mul2(Y, inv);
+    const float2 r2 = fma2(mx, mx, mul2(my, my));
+    const float2 rad = fma2(r2, fma2(dup2(c.k2), r2, dup2(c.k1)), dup2(1.0f));
+    const float2 mxy = mul2(mx, my);
+    const float2 xd = fma2(mx, rad, fma2(dup2(2.0f * c.p1), mxy, mul2(dup2(c.p2), fma2(add2(mx, mx), mx, r2))));
+    const float2 yd = fma2(my, rad, fma2(dup2(c.p1), fma2(add2(my, my), my, r2), mul2(dup2(2.0f * c.p2), mxy)));
+    const float2 u = fma2(dup2(c.fx), xd, dup2(c.cx)), v = fma2(dup2(c.fy), yd, dup2(c.cy));
+    const float2 ln = mul2(dup2(c.lim), n);
+    const bool g0 = f0 && (Z.x > ln.x) && (r2.x <= c.r2_max), g1 = f1 && (Z.y > ln.y) && (r2.y <= c.r2_max);
+    return make_float2(g0 ? sample_uv(C, u.x, v.x) : nan, g1 ? sample_uv(C, u.y, v.y) : nan);
 }
 
 // Two-pass ZNCC of the pixel's window: reference samples R and warped
@@ -171,12 +226,58 @@ __device__ __forceinline__ bool window_zncc(const float* R, const float* Wv, int
     return true;
 }
 
+// window_zncc for two planes at once: warped pairs Wv (lane x: the first
+// plane, lane y: the second), one reference window.  The reference sums are
+// shared; per lane every sum and rounding is window_zncc's, so z is
+// bit-identical to it.  ok0 / ok1: the lanes' validity.
 template <int RHO>
-__global__ void __launch_bounds__(DNT) soft_fwd_kernel(const __grid_constant__ DiffP P, float* range, float* cost,
+__device__ __forceinline__ float2 window_zncc2(const float* R, const float2* Wv, int lx, int ly, bool* ok0, bool* ok1) {
+    constexpr int N = (2 * RHO + 1) * (2 * RHO + 1);
+    float sa = 0.f;
+    float2 sb = dup2(0.f);
+    bool v0 = true, v1 = true;
+#pragma unroll
+    for (int dy = 0; dy <= 2 * RHO; ++dy)
+#pragma unroll
+        for (int dx = 0; dx <= 2 * RHO; ++dx) {
+            const int q = (ly + dy) * DS + lx + dx;
+            const float2 b = Wv[q];
+            v0 &= !isnan(b.x);
+            v1 &= !isnan(b.y);
+            sa += R[q];
+            sb = add2(sb, b);
+        }
+    *ok0 = *ok1 = false;
+    if (!(v0 || v1)) return dup2(0.f);
+    const float ma = sa / (float)N;
+    const float2 nmb = make_float2(-(sb.x / (float)N), -(sb.y / (float)N));
+    float va = 0.f;
+    float2 cov = dup2(0.f), vb = dup2(0.f);
+#pragma unroll
+    for (int dy = 0; dy <= 2 * RHO; ++dy)
+#pragma unroll
+        for (int dx = 0; dx <= 2 * RHO; ++dx) {
+            const int q = (ly + dy) * DS + lx + dx;
+            const float ea = R[q] - ma;
+            const float2 eb = add2(Wv[q], nmb);
+            cov = fma2(dup2(ea), eb, cov);
+            va = fmaf(ea, ea, va);
+            vb = fma2(eb, eb, vb);
+        }
+    const float lim = (float)N * 1e-8f;
+    *ok0 = v0 && !(va < lim || vb.x < lim);
+    *ok1 = v1 && !(va < lim || vb.y < lim);
+    return make_float2(cov.x / sqrtf(va * vb.x), cov.y / sqrtf(va * vb.y));
+}
+
+// Window 5: three CTAs per SM (80 registers, a small spill) measured faster
+// than two without the limit.
+template <int RHO>
+__global__ void __launch_bounds__(DNT, RHO == 2 ? 3 : 1) soft_fwd_kernel(const __grid_constant__ DiffP P, float* range, float* cost,
                                                       float* aux) {
     constexpr int HW = DT + 2 * RHO, NPOS = HW * HW;
     __shared__ float Rs[HW * DS];
-    __shared__ float Ws[HW * DS];
+    __shared__ float2 W2[HW * DS];  // warped samples of a pair of planes
     const int tid = threadIdx.x, lx = tid % DT, ly = tid / DT;
     const int x0 = blockIdx.x * DT - RHO, y0 = blockIdx.y * DT - RHO;
     const int gx = blockIdx.x * DT + lx, gy = blockIdx.y * DT + ly;
@@ -189,31 +290,39 @@ __global__ void __launch_bounds__(DNT) soft_fwd_kernel(const __grid_constant__ D
     const bool use = in && gx >= RHO && gy >= RHO && gx < P.W - RHO && gy < P.H - RHO && !isnan(ray.x);
     const float inf = __int_as_float(0x7f800000);
     float cmin = inf, Z = 0.f, Nr = 0.f;
-    for (int k = 0; k < P.K; ++k) {
-        const PlaneD pl = P.planes[k];
-        float best = inf;
+    // planes in pairs (k, k + 1), warped and matched together on packed FP32
+    for (int k = 0; k < P.K; k += 2) {
+        const int np = min(2, P.K - k);
+        const PlaneD pl0 = P.planes[k], pl1 = P.planes[k + np - 1];
+        float best[2] = {inf, inf};
         for (int j = 0; j < P.n_cams; ++j) {
             __syncthreads();
             for (int p = tid; p < NPOS; p += DNT) {
                 const int hx = p % HW, hy = p / HW;
-                Ws[hy * DS + hx] = warp_at(P, P.cams[j], pl, x0 + hx, y0 + hy).w;
+                W2[hy * DS + hx] = warp_pair(P, P.cams[j], pl0, pl1, x0 + hx, y0 + hy);
             }
             __syncthreads();
-            Zn zn;
-            if (use && window_zncc<RHO>(Rs, Ws, lx, ly, &zn)) {
-                float c = 0.5f * (1.0f - zn.z);
-                if (c < best) best = c;
+            if (use) {
+                bool ok0, ok1;
+                const float2 z = window_zncc2<RHO>(Rs, W2, lx, ly, &ok0, &ok1);
+                const float c0 = 0.5f * (1.0f - z.x), c1 = 0.5f * (1.0f - z.y);
+                if (ok0 && c0 < best[0]) best[0] = c0;
+                if (ok1 && c1 < best[1]) best[1] = c1;
             }
         }
-        if (best < inf) {
-            float rho_k = (pl.nx * ray.x + pl.ny * ray.y + pl.nz * ray.z) / pl.d;
-            if (best < cmin) {  // rescale the running sums to the new minimum
-                float f = cmin < inf ? __expf(-(cmin - best) / P.T) : 0.f;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            if (q >= np || !(best[q] < inf)) continue;
+            const PlaneD& pl = q == 0 ? pl0 : pl1;
+            const float bq = best[q];
+            float rho_k = plane_dot(pl, ray) / pl.d;
+            if (bq < cmin) {  // rescale the running sums to the new minimum
+                float f = cmin < inf ? __expf(-(cmin - bq) / P.T) : 0.f;
                 Z *= f;
                 Nr *= f;
-                cmin = best;
+                cmin = bq;
             }
-            float e = __expf(-(best - cmin) / P.T);
+            float e = __expf(-(bq - cmin) / P.T);
             Z += e;
             Nr = fmaf(e, rho_k, Nr);
         }
@@ -408,7 +517,7 @@ __global__ void __launch_bounds__(DNT) soft_bwd_kernel(const __grid_constant__ D
         float ka = 0.f, kza = 0.f, kzb = 0.f, mac = 0.f, mbc = 0.f;
         if (jb >= 0) {
             const float s = __expf(-(best - cmin) / P.T) / Z;
-            const float rho_k = (pl.nx * ray.x + pl.ny * ray.y + pl.nz * ray.z) / pl.d;
+            const float rho_k = plane_dot(pl, ray) / pl.d;
             const float gC = gE * (-s * (rho_k - E) / P.T) + gs * s;
             const float gz = -0.5f * gC;
             ka = gz / zb.sab;
