@@ -132,12 +132,13 @@ def test_autograd_images_and_pose(case):
         assert b.abs().max().item() > 0
 
 
-@pytest.mark.parametrize("window,n_cams", [(7, 3), (9, 4)])
-def test_wider_windows_and_more_cameras(window, n_cams):
-    # the other kernel instantiations (window radius 3 and 4) and shared-memory
-    # layouts (3 and 4 cameras) against the oracle: forward maps and gradients
+@pytest.mark.parametrize("window,n_cams,n_planes", [(7, 3, 8), (9, 4, 8), (5, 2, 7)])
+def test_wider_windows_and_more_cameras(window, n_cams, n_planes):
+    # the other kernel instantiations (window radius 3 and 4), shared-memory
+    # layouts (3 and 4 cameras) and an odd plane count (the forward takes
+    # planes in pairs) against the oracle: forward maps and gradients
     import dataclasses
-    wl = scenes.diff(5, width=64, height=48, n_planes=8)
+    wl = scenes.diff(5, width=64, height=48, n_planes=n_planes)
     cams, poses = list(wl.rig.cams), list(wl.rig.ref_to_cam)
     for k, dy in enumerate((-0.3, 0.3)[:n_cams - 2]):
         R = rot_xyz(math.radians(0.5 * (k + 1)), math.radians(-0.4), 0.0)
@@ -166,7 +167,8 @@ def test_wider_windows_and_more_cameras(window, n_cams):
                                       g_cost=gs.astype(np.float64))
     e_pose = [_rel_err(gp[j].cpu().numpy(), ogp[j]) for j in range(n_cams) if np.abs(ogp[j]).max() > 0]
     e_img = [_rel_err(gi[m].cpu().numpy(), ogi[m]) for m in range(1 + n_cams) if np.abs(ogi[m]).max() > 0]
-    print(f"window {window}, {n_cams} cameras: tied", int(tied.sum()), "pose", e_pose, "image", e_img)
+    print(f"window {window}, {n_cams} cameras, {n_planes} planes: tied", int(tied.sum()), "pose", e_pose,
+          "image", e_img)
     assert len(e_pose) >= 2 and len(e_img) >= 3
     assert max(e_pose) <= 1e-4 and max(e_img) <= 1e-4
 

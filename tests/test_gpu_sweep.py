@@ -53,6 +53,22 @@ def test_tiny_more_seeds(seed):
     assert_sweep_parity(o, g[0], min_gated=2000)
 
 
+def test_odd_plane_sets_and_chunk_boundaries(tiny_frame):
+    # planes go through the tile routine in pairs: sets of odd size end on a
+    # half-empty pair, and the 50 planes split into two 25-plane work items,
+    # one of which starts inside the first set
+    import dataclasses
+    from scenes.configs import FRONTO, GROUND, PlaneSet
+    wl, imgs = tiny_frame
+    sets = [PlaneSet(FRONTO, 33, 0.5, 20.0), PlaneSet(GROUND, 17, 1.0, 2.0, n=(0.0, 1.0, 0.0))]
+    wl = dataclasses.replace(wl, levels=[dataclasses.replace(wl.levels[0], sets=sets)])
+    o = oracle.sweep_level(wl.rig, wl.levels[0], imgs)
+    _, g = _gpu_levels(P.Sweep(wl.rig, wl.levels), imgs)
+    s = assert_sweep_parity(o, g[0], min_gated=2000)
+    print("odd sets", s)
+    assert (g[0]["kstar"] >= 33).any() and (g[0]["kstar"][g[0]["kstar"] >= 0] < 33).any()
+
+
 @pytest.fixture(scope="module")
 def street_small():
     wl = scenes.street(0, n_frames=1, scale=0.25)
