@@ -69,26 +69,28 @@ __device__ __forceinline__ bool project_f(const CamF& c, float X, float Y, float
     return (Z > c.lim * n) && (r2 <= c.r2_max);
 }
 
-// d(u, v)/dX of project_f (row-major 2 x 3).
-__device__ __forceinline__ void project_jac_f(const CamF& c, float X, float Y, float Z, float J[6]) {
-    float n = sqrtf(fmaf(X, X, fmaf(Y, Y, Z * Z)));
-    float den = fmaf(c.xi, n, Z), id = 1.0f / den;
-    float dden[3] = {c.xi * X / n, c.xi * Y / n, 1.0f + c.xi * Z / n};
-    float mx = X * id, my = Y * id;
-    float dmx[3], dmy[3];
-    for (int i = 0; i < 3; ++i) {
-        dmx[i] = (i == 0 ? id : 0.0f) - mx * dden[i] * id;
-        dmy[i] = (i == 1 ? id : 0.0f) - my * dden[i] * id;
-    }
-    float r2 = fmaf(mx, mx, my * my);
-    float rad = fmaf(r2, fmaf(c.k2, r2, c.k1), 1.0f), drad = fmaf(2.0f * c.k2, r2, c.k1);
-    float a = rad + 2.0f * mx * mx * drad + 2.0f * c.p1 * my + 6.0f * c.p2 * mx;
-    float b = 2.0f * mx * my * drad + 2.0f * c.p1 * mx + 2.0f * c.p2 * my;
-    float d = rad + 2.0f * my * my * drad + 6.0f * c.p1 * my + 2.0f * c.p2 * mx;
-    for (int i = 0; i < 3; ++i) {
-        J[i] = c.fx * (a * dmx[i] + b * dmy[i]);
-        J[3 + i] = c.fy * (b * dmx[i] + d * dmy[i]);
-    }
+// g = J^T (gu, gv) for the projection Jacobian J = d(u, v)/dX at X (camera
+// frame), by reverse-mode differentiation of project_f instead of forming J:
+// the adjoints of the distorted point, of the normalised point (mx, my),
+// then of X through mx = X / den, my = Y / den, den = xi |X| + Z.
+__device__ __forceinline__ void project_vjp_f(const CamF& c, float X, float Y, float Z, float gu, float gv,
+                                              float g[3]) {
+    const float n = sqrtf(fmaf(X, X, fmaf(Y, Y, Z * Z)));
+    const float id = 1.0f / fmaf(c.xi, n, Z);
+    const float mx = X * id, my = Y * id;
+    const float r2 = fmaf(mx, mx, my * my);
+    const float rad = fmaf(r2, fmaf(c.k2, r2, c.k1), 1.0f), drad = fmaf(2.0f * c.k2, r2, c.k1);
+    // d(xd, yd)/d(mx, my) = [[a, b], [b, d]]
+    const float a = rad + 2.0f * mx * mx * drad + 2.0f * c.p1 * my + 6.0f * c.p2 * mx;
+    const float b = 2.0f * mx * my * drad + 2.0f * c.p1 * mx + 2.0f * c.p2 * my;
+    const float d = rad + 2.0f * my * my * drad + 6.0f * c.p1 * my + 2.0f * c.p2 * mx;
+    const float gxd = gu * c.fx, gyd = gv * c.fy;
+    const float gmx = fmaf(gxd, a, gyd * b), gmy = fmaf(gxd, b, gyd * d);
+    const float sden = fmaf(gmx, mx, gmy * my) * id;  // -dL/dden
+    const float xn = c.xi / n;                        // d(xi n)/dX = xi X / n
+    g[0] = fmaf(gmx, id, -sden * xn * X);
+    g[1] = fmaf(gmy, id, -sden * xn * Y);
+    g[2] = -sden * fmaf(xn, Z, 1.0f);
 }
 
 // The warp of halo position (gx, gy) through plane P into camera C: the
@@ -392,11 +394,8 @@ __device__ __forceinline__ WarpJ warp_jac(const DiffP& P, const DiffCam& C, cons
     const float i01 = I[(size_t)yb * Wc + xa], i11 = I[(size_t)yb * Wc + xb];
     const float dwdu = (1.f - ay) * (i10 - i00) + ay * (i11 - i01);
     const float dwdv = (1.f - ax) * (i01 - i00) + ax * (i11 - i10);
-    float J[6];
-    project_jac_f(C.c, wp.X, wp.Y, wp.Z, J);
     float g[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) g[i] = dwdu * J[i] + dwdv * J[3 + i];
+    project_vjp_f(C.c, wp.X, wp.Y, wp.Z, dwdu, dwdv, g);
     o.cell = (ya << 16) | xa;
     o.ax = ax;
     o.ay = ay;
