@@ -248,8 +248,9 @@ __device__ __forceinline__ float2 warp_sample2(const CamS& c, float2 X, float2 Y
 // (column, segment) slides down SEG output rows, forms ZNCC and keeps the
 // minimum over cameras.  Strides make every phase's shared-memory accesses
 // free of bank conflicts.  KP planes are warped per camera before the
-// window sums of each run, so consecutive gathers hit overlapping
-// footprints of the same image.
+// window sums, so consecutive gathers hit overlapping footprints of the same
+// image; with KP = 2 the three phases handle both planes at once on packed
+// FP32 pairs (pair_pass) and H holds both planes' sums.
 template <int RHO, int TH, int KP>
 struct Geo {
     static constexpr int SEG = TH / 8;                // output rows per vertical segment (phase V)
