@@ -437,8 +437,8 @@ def run_ours(args):
         "e2e": {"value": world * args.steps / (pipe_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "api": "ps_pipe_push x K + ps_pipe_flush (two frames in flight)",
                 "serial": world * args.steps / (e2e_ms / 1e3), "serial_api": "psweep_frame_host per frame"},
-        # per level: reference image + statistics, quads of all cameras; the sweep and the merge; 4 TSDF stages
-        "gpu_launches": args.steps * (2 * len(wl.levels) + 2 + 4),
+        # one prep launch for every level (reference images, statistics, quads), the sweep, the merge; 4 TSDF stages
+        "gpu_launches": args.steps * (1 + 2 + 4),
         "clocks": clk,
         "render_s": render_s,
     }

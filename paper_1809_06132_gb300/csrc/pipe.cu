@@ -1,8 +1,10 @@
-// Frame pipeline: host frames through three CUDA streams (copy in, sweep,
-// fuse + copy out) with two frames in flight, so that the sweep of frame
-// n + 1 and the host<->device copies overlap the fusion of frame n.  The
-// paper runs depth estimation and fusion on separate computers at the same
-// time (Sec. IV-A); on one GPU the same overlap comes from streams.
+// Frame pipeline: host frames through three CUDA streams (copy in; sweep
+// and fusion; copy out) with two frames in flight, so that the host<->device
+// copies and the host-side staging of frames n + 1 and n - 1 overlap the
+// GPU work of frame n.  The paper runs depth estimation and fusion on
+// separate computers at the same time (Sec. IV-A); on one GPU the sweep
+// fills every SM, so fusion follows each sweep on the compute stream and the
+// overlap that remains is the copies'.
 #include <cstring>
 
 #include "sweep_dev.cuh"
@@ -120,17 +122,21 @@ extern "C" int ps_pipe_push(ps_pipe_t* p, const uint8_t* const* host_images, con
         dev[i] = p->dev_img[slot][i];
     }
     PS_CUDA(cudaEventRecord(p->ev_in[slot], p->s_in));
-    // sweep (frames in order on one stream: the handle's level buffers are reused)
+    // sweep, then fusion, in frame order on the compute stream (the handles'
+    // buffers are reused and the volume is updated in order).  Fusion is
+    // short and runs right behind its sweep: on a stream of its own it could
+    // be held behind the next frame's persistent sweep launch, delaying the
+    // slot's release and so the next frame's input copy.
     PS_CUDA(cudaStreamWaitEvent(p->s_sweep, p->ev_in[slot], 0));
     st = psweep_depth(p->h, dev, boxes, n_boxes, p->dev_depth[slot], nullptr, p->s_sweep);
     if (st) return st;
-    PS_CUDA(cudaEventRecord(p->ev_depth[slot], p->s_sweep));
-    // fuse and copy out (frames in order on one stream: the volume is updated in order)
-    PS_CUDA(cudaStreamWaitEvent(p->s_out, p->ev_depth[slot], 0));
     if (p->t) {
-        st = tsdf_integrate(p->t, p->dev_depth[slot], world_to_ref, local_center, p->s_out);
+        st = tsdf_integrate(p->t, p->dev_depth[slot], world_to_ref, local_center, p->s_sweep);
         if (st) return st;
     }
+    PS_CUDA(cudaEventRecord(p->ev_depth[slot], p->s_sweep));
+    // copy out on the output stream
+    PS_CUDA(cudaStreamWaitEvent(p->s_out, p->ev_depth[slot], 0));
     if (host_depth_out)
         PS_CUDA(cudaMemcpyAsync(p->host_depth[slot], p->dev_depth[slot], p->depth_bytes, cudaMemcpyDeviceToHost,
                                 p->s_out));

@@ -4,12 +4,14 @@
 //   ray_table_kernel   Eq. 1 back-projection of every reference pixel of a
 //                      level, in double precision, stored as float4 (once
 //                      per rig, at psweep_create).
-//   ref_stats_kernel   reference image of a level (s x s box mean, or the
-//                      centred crop), centred intensities I/255 - 1/2, and
-//                      its window mean and sum of squared deviations.
-//   quad_level_kernel  matching images of a level in "quad" layout: entry
-//                      (x, y) holds the 2 x 2 neighbourhood used by one
-//                      bilinear sample, so a sample is one 16-byte gather.
+//   prep_kernel        per frame, in one launch for every level: the
+//                      reference image of the level (s x s box mean, or the
+//                      centred crop), centred intensities I/255 - 1/2, with
+//                      its window mean and sum of squared deviations; the
+//                      matching images in "quad" layout: entry (x, y) holds
+//                      the 2 x 2 neighbourhood used by one bilinear sample,
+//                      so a sample is one 16-byte gather; and the zeroing of
+//                      the sweep's work counters.
 //   sweep_kernel       the hot loop.  One CTA owns a 64 x 24 tile of output
 //                      pixels of one level and walks every plane and every
 //                      matching camera: warp the tile + window halo through
@@ -122,29 +124,29 @@ __global__ void view_angle_kernel(ps_camera c, int W, int H, unsigned* out) {
 // tile of level pixels plus a window halo is formed in shared memory, the
 // tile is written out and each pixel's statistics come from shared memory.
 constexpr int RS_TX = 32, RS_TY = 8, RS_MAXH = 4;
-__global__ void __launch_bounds__(RS_TX * RS_TY) ref_stats_kernel(const uint8_t* img, int W, int s, int x0, int y0,
-                                                                  int Wl, int Hl, int rho, float* ref, float2* stats) {
-    __shared__ float tile[(RS_TY + 2 * RS_MAXH) * (RS_TX + 2 * RS_MAXH)];
+constexpr int PREP_T = RS_TX * RS_TY;  // threads of a prep block
+__device__ __forceinline__ void ref_stats_tile(const uint8_t* img, int W, int s, int x0, int y0, int Wl, int Hl,
+                                               int rho, float* ref, float2* stats, int tbx, int tby, float* tile) {
     const int hw = RS_TX + 2 * rho, hh = RS_TY + 2 * rho;
-    const int bx = blockIdx.x * RS_TX - rho, by = blockIdx.y * RS_TY - rho;
-    const int tid = threadIdx.y * RS_TX + threadIdx.x;
-    for (int p = tid; p < hw * hh; p += RS_TX * RS_TY) {
+    const int bx = tbx * RS_TX - rho, by = tby * RS_TY - rho;
+    const int tid = threadIdx.x, tx = tid % RS_TX, ty = tid / RS_TX;
+    for (int p = tid; p < hw * hh; p += PREP_T) {
         int x = bx + p % hw, y = by + p / hw;
         tile[p] = (x >= 0 && y >= 0 && x < Wl && y < Hl) ? ref_px(img, W, s, x0, y0, Wl, Hl, x, y) : 0.0f;
     }
     __syncthreads();
-    const int x = blockIdx.x * RS_TX + threadIdx.x, y = blockIdx.y * RS_TY + threadIdx.y;
+    const int x = tbx * RS_TX + tx, y = tby * RS_TY + ty;
     if (x >= Wl || y >= Hl) return;
-    const float* c = tile + (threadIdx.y + rho) * hw + threadIdx.x + rho;
+    const float* c = tile + (ty + rho) * hw + tx + rho;
     ref[(size_t)y * Wl + x] = *c;
     stats[(size_t)y * Wl + x] = (x >= rho && y >= rho && x < Wl - rho && y < Hl - rho) ? window_stats(c, hw, rho)
                                                                                       : make_float2(0.f, -1.f);
 }
 
-// Quad images of every matching camera of a level (blockIdx.z = camera).
-// Each thread forms the level pixels (x, y) and (x, y + 1) and takes the
-// (x + 1) column from its lane neighbour, so every level pixel is computed
-// about twice instead of four times.
+// Quad images of the matching cameras of a level.  Each thread forms the
+// level pixels (x, y) and (x, y + 1) and takes the (x + 1) column from its
+// lane neighbour, so every level pixel is computed about twice instead of
+// four times.
 struct QuadJobs {
     const uint8_t* img[PS_MAX_CAMS];
     void* out[PS_MAX_CAMS];
@@ -152,11 +154,10 @@ struct QuadJobs {
     int s, half;
 };
 
-__global__ void __launch_bounds__(128) quad_level_kernel(const __grid_constant__ QuadJobs Q) {
-    const int j = blockIdx.z;
+__device__ __forceinline__ void quad_row(const QuadJobs& Q, int j, int xb, int y) {
     const int Wl = Q.Wl[j], Hl = Q.Hl[j];
-    if ((int)(blockIdx.x * blockDim.x) >= Wl || (int)blockIdx.y >= Hl) return;  // whole block outside this camera
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (xb * PREP_T >= Wl || y >= Hl) return;  // whole block outside this camera
+    const int x = xb * PREP_T + threadIdx.x;
     const uint8_t* img = Q.img[j];
     const int W = Q.W[j], s = Q.s;
     float a = level_px(img, W, Wl, Hl, s, x, y), b = level_px(img, W, Wl, Hl, s, x, y + 1);
@@ -172,6 +173,53 @@ __global__ void __launch_bounds__(128) quad_level_kernel(const __grid_constant__
         static_cast<uint2*>(Q.out[j])[o] = make_uint2(*reinterpret_cast<unsigned*>(&p), *reinterpret_cast<unsigned*>(&q));
     } else {
         static_cast<float4*>(Q.out[j])[o] = make_float4(a, a1, b, b1);
+    }
+}
+
+// Everything a frame's sweep reads, in one launch: per level the reference
+// tiles and the quad rows of every matching camera, and the zeroing of the
+// sweep's work counters.  Block b takes the role of the range it falls in;
+// roles are uniform over a block.
+struct PrepLevel {
+    int W, s, x0, y0, Wl, Hl, rho;  // reference image and level
+    float* ref;
+    float2* stats;
+    int rs_tiles_x, rs_blocks;      // reference tiles
+    QuadJobs Q;
+    int n_cams, q_xblocks, q_rows, q_blocks;  // quad blocks: rows of PREP_T pixels x rows x cameras
+    int* done;                      // per-tile chunk counters to zero
+    int n_done;
+};
+
+struct PrepP {
+    const uint8_t* ref_img;
+    int n_levels;
+    PrepLevel L[PS_MAX_LEVELS];
+    int* tile_counter;
+};
+
+__global__ void __launch_bounds__(PREP_T) prep_kernel(const __grid_constant__ PrepP P) {
+    __shared__ float tile[(RS_TY + 2 * RS_MAXH) * (RS_TX + 2 * RS_MAXH)];
+    int b = blockIdx.x;
+    if (b == 0) {
+        if (threadIdx.x == 0) *P.tile_counter = 0;
+        for (int l = 0; l < P.n_levels; ++l)
+            for (int i = threadIdx.x; i < P.L[l].n_done; i += PREP_T) P.L[l].done[i] = 0;
+    }
+    for (int l = 0; l < P.n_levels; ++l) {
+        const PrepLevel& L = P.L[l];
+        if (b < L.rs_blocks) {
+            ref_stats_tile(P.ref_img, L.W, L.s, L.x0, L.y0, L.Wl, L.Hl, L.rho, L.ref, L.stats, b % L.rs_tiles_x,
+                           b / L.rs_tiles_x, tile);
+            return;
+        }
+        b -= L.rs_blocks;
+        if (b < L.q_blocks) {
+            const int per_cam = L.q_xblocks * L.q_rows, j = b / per_cam, r = b - j * per_cam;
+            quad_row(L.Q, j, r % L.q_xblocks, r / L.q_xblocks);
+            return;
+        }
+        b -= L.q_blocks;
     }
 }
 
@@ -600,17 +648,30 @@ extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_
         };
         if (cost(1) > cost(0)) std::swap(order[0], order[1]);
     }
+    PrepP prep;
+    std::memset(&prep, 0, sizeof(prep));
+    prep.ref_img = images[0];
+    prep.n_levels = h->n_levels;
+    int prep_blocks = 0;
     for (int oi = 0; oi < h->n_levels; ++oi) {
         const int l = order[oi];
         const ps_level& L = h->levels[l];
         const int W = h->lW[l], H = h->lH[l];
         const bool down = L.kind == PS_LEVEL_DOWNSAMPLE;
-        ref_stats_kernel<<<dim3((W + RS_TX - 1) / RS_TX, (H + RS_TY - 1) / RS_TY), dim3(RS_TX, RS_TY), 0, s>>>(
-            images[0], h->ref.width, down ? L.factor : 0, down ? 0 : h->cx0[l], down ? 0 : h->cy0[l], W, H,
-            L.window / 2, h->ref_img[l], h->stats[l]);
+        PrepLevel& R = prep.L[oi];
+        R.W = h->ref.width;
+        R.s = down ? L.factor : 0;
+        R.x0 = down ? 0 : h->cx0[l];
+        R.y0 = down ? 0 : h->cy0[l];
+        R.Wl = W;
+        R.Hl = H;
+        R.rho = L.window / 2;
+        R.ref = h->ref_img[l];
+        R.stats = h->stats[l];
+        R.rs_tiles_x = (W + RS_TX - 1) / RS_TX;
+        R.rs_blocks = R.rs_tiles_x * ((H + RS_TY - 1) / RS_TY);
         {
-            QuadJobs Q;
-            std::memset(&Q, 0, sizeof(Q));
+            QuadJobs& Q = R.Q;
             int wmax = 0, hmax = 0;
             for (int j = 0; j < h->n_cams; ++j) {
                 const ps_camera& cj = h->lcam[l][j];
@@ -624,13 +685,18 @@ extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_
             }
             Q.s = down ? L.factor : 1;
             Q.half = h->image_half;
-            quad_level_kernel<<<dim3((wmax + 127) / 128, hmax, h->n_cams), 128, 0, s>>>(Q);
+            R.n_cams = h->n_cams;
+            R.q_xblocks = (wmax + PREP_T - 1) / PREP_T;
+            R.q_rows = hmax;
+            R.q_blocks = R.q_xblocks * R.q_rows * h->n_cams;
         }
+        prep_blocks += R.rs_blocks + R.q_blocks;
         LevelD& D = P.lv[oi];
         fill_level(h, l, TH_SINGLE, h->chunk[l], D);
         D.partial = h->partial[l];
         D.done = h->done[l];
-        PS_CUDA(cudaMemsetAsync(D.done, 0, sizeof(int) * D.n_tiles, s));
+        R.done = D.done;  // zeroed by the prep launch
+        R.n_done = D.n_tiles;
         const ps_level_out* lo = level_out ? &level_out[l] : nullptr;
         if (lo && lo->depth) D.depth = lo->depth;
         if (lo && lo->best_cost) D.c1 = lo->best_cost;
@@ -646,7 +712,9 @@ extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_
         smem = std::max(smem, sweep_smem<TH_SINGLE, KP_SINGLE>(r, nc));
         tiles += P.lv[l].n_items;
     }
-    PS_CUDA(cudaMemsetAsync(h->tile_counter, 0, sizeof(int), s));
+    prep.tile_counter = h->tile_counter;
+    prep_kernel<<<prep_blocks, PREP_T, 0, s>>>(prep);
+    PS_CUDA(cudaGetLastError());
     h->prof.mark(1, s);
     sweep_kernel<<<std::min(tiles, h->grid), NT, smem, s>>>(P, h->tile_counter);
     PS_CUDA(cudaGetLastError());
