@@ -277,12 +277,13 @@ int psweep_frame_host(psweep_t* h, tsdf_t* t, const uint8_t* const* host_images,
 
 /* Frame pipeline.  The paper ran depth estimation and fusion on separate
  * computers at the same time, each on a different frame (Sec. IV-A).  On
- * one GPU the same overlap comes from CUDA streams: frames from host memory
- * go through a copy-in stream (host images -> pinned staging -> device), a
- * sweep stream (psweep_depth) and a fuse stream (tsdf_integrate, then the
- * depth map back to pinned staging), with two frames in flight, so the
- * sweep of frame n + 1 and both copies overlap the fusion of frame n.
- * Every frame gets exactly what psweep_frame_host gives it.
+ * one GPU the sweep fills every SM, so the overlap comes from the copies:
+ * frames from host memory go through a copy-in stream (host images ->
+ * pinned staging -> device), a compute stream (psweep_depth, then
+ * tsdf_integrate) and a copy-out stream (the depth map back to pinned
+ * staging), with two frames in flight, so the copies and the host-side
+ * staging of the neighbouring frames overlap the GPU work of the current
+ * one.  Every frame gets exactly what psweep_frame_host gives it.
  *   ps_pipe_create  t may be NULL (no fusion); allocates two sets of device
  *                   and pinned staging buffers, three streams, six events.
  *   ps_pipe_push    enqueues one frame (arguments as psweep_frame_host) and

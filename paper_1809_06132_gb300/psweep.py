@@ -330,8 +330,8 @@ class Sweep:
 
 
 class Pipeline:
-    """Host frames through copy-in / sweep / fuse+copy-out streams, two frames
-    in flight (ps_pipe_*).  push() returns at once; the depth map of a frame
+    """Host frames through copy-in / compute (sweep, then fusion) / copy-out
+    streams, two frames in flight (ps_pipe_*).  push() returns at once; the depth map of a frame
     lands in its host buffer by the time the push two calls later, or
     flush(), returns."""
 
