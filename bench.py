@@ -371,8 +371,8 @@ def run_ours(args):
         ts = time.perf_counter()
         step_host(args.warmup + k)
         e2e_ms += (time.perf_counter() - ts) * 1e3
-    # the same through the frame pipeline (copy-in / sweep / fuse+copy-out streams,
-    # two frames in flight): K pushes and the final flush, host images in, depth maps out
+    # the same through the frame pipeline (copy-in / compute: sweep then fusion / copy-out
+    # streams, two frames in flight): K pushes and the final flush, host images in, depth maps out
     T3 = P.Tsdf(wl.tsdf, wl.rig.ref)
     pipe = P.Pipeline(sw, T3)
     host_outs = [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in range(2)]
