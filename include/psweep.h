@@ -30,7 +30,9 @@
  *     ps_last_error() gives a message for the calling thread.  Device-side
  *     failures (hash table or block pool full, bounded probe gave up) are
  *     latched in the handle and reported by the next synchronising call
- *     (tsdf_status, tsdf_extract, tsdf_count).  No call traps the device.
+ *     (ps_sync_status for any handle; tsdf_status, tsdf_extract,
+ *     tsdf_count for a TSDF; psbatch_status for a batch).  No call traps
+ *     the device.
  */
 #ifndef PSWEEP_H
 #define PSWEEP_H
@@ -47,6 +49,8 @@ extern "C" {
 #define PS_ERR_CAPACITY 3   /* TSDF hash table or voxel-block pool is full */
 #define PS_ERR_CUDA 4       /* a CUDA runtime call failed */
 #define PS_ERR_TIMEOUT 5    /* a bounded device loop (hash probing) gave up */
+#define PS_ERR_STATE 6      /* a device-side invariant failed: one handle's work counters were
+                               advanced by overlapping calls (e.g. two streams at once) */
 
 /* Unified omnidirectional camera (Sec. III-C, Eq. 1, after Mei) with
  * radial-tangential distortion of the normalised coordinates:
@@ -319,10 +323,11 @@ int tsdf_profile_read(tsdf_t* t, double* stage_ms, int32_t* n_calls);
 
 /* Allocation-free fusion into a caller-owned dense grid (the paper has no
  * counterpart; this is a convenience of the library).  Some callers cannot
- * allocate GPU memory while they run: code recording a CUDA graph (an
- * allocation breaks the capture), real-time loops whose memory is planned
- * once up front, and hosts whose device memory belongs to another
- * allocator.  This call fuses one depth map exactly like tsdf_integrate on
+ * allocate GPU memory while they run: real-time loops whose memory is
+ * planned once up front (an allocation there can stall or fail at an
+ * unplanned moment), and hosts whose device memory belongs to another
+ * allocator (memory taken behind its back is memory it cannot account
+ * for).  This call fuses one depth map exactly like tsdf_integrate on
  * a dense grid, but the voxels are the caller's and the library's working
  * memory (block list, counters, depth maximum) is one fixed static device
  * array of PS_STATIC_SCRATCH_BYTES (about 1.3 MB), which every GPU that
@@ -333,13 +338,17 @@ int tsdf_profile_read(tsdf_t* t, double* stage_ms, int32_t* n_calls);
  *                 map).  Zero it to start an empty map.
  *   dims          host int32[3]: voxels per axis, multiples of 8, at most
  *                 PS_STATIC_MAX_BLOCKS blocks in all (larger grids get
- *                 PS_ERR_ARG and a message naming the limit).
+ *                 PS_ERR_ARG and a message naming the limit).  The library
+ *                 sees only pointers: voxels must hold dims' blocks and
+ *                 depth cam's H x W values (the Python binding checks both).
  *   origin        host double[3]; voxel_size, mu, w_max as in ps_tsdf_desc.
  *   depth         device float32 H x W range map of cam (0 = no depth).
  *   cam           host, the depth map's camera; world_to_cam host pose.
- * Asynchronous on `stream`.  The first call on each device looks up the
- * static array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call
+ * Asynchronous on `stream`; a device-side failure has no handle to be
+ * latched in, and none can occur on a dense grid (argument errors are
+ * returned at once).  The first call on each device looks up the static
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call
  * reuses the same array (it keeps the last call's contents; the call clears
  * what must start at zero), so calls that overlap on the GPU, from other
  * streams or host threads, race on it: serialise them. */
@@ -512,6 +521,18 @@ int ps_check_read(uint32_t* bits);
 
 /* Message for the calling thread's last non-zero status ("" if none). */
 const char* ps_last_error(void);
+
+/* Synchronises `stream` and returns the device status latched in a handle
+ * since the last read (then clears it), for any handle the library made:
+ * psweep_t (a plane-chunk completion counted more often than the tile has
+ * chunks: PS_ERR_STATE, which overlapping calls on one handle cause),
+ * tsdf_t (full hash table or pool: PS_ERR_CAPACITY; probing gave up:
+ * PS_ERR_TIMEOUT) or psbatch_t (a wait gave up: PS_ERR_TIMEOUT;
+ * PS_ERR_STATE as for a sweep).  The handle's type is read from its first
+ * word; a pointer that is no live handle of this library is undefined
+ * behaviour (PS_ERR_ARG when the word does not match a handle type).
+ * Paper: Sec. III (the per-frame pipeline needs each stage's outcome). */
+int ps_sync_status(void* handle, void* stream);
 
 /* Library version string. */
 const char* ps_version(void);

@@ -28,14 +28,25 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so (plain g++ -O2, IEEE double arithmetic)."""
+    """Compile liboracle.so (plain g++ -O2, IEEE double arithmetic), with
+    OpenMP when the compiler has it (the per-pixel arithmetic is the same
+    either way; only independent loops are shared among threads)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-fno-fast-math",
-                               _SRC, "-o", tmp])
+        base = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-fno-fast-math", _SRC, "-o", tmp]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's independent loops (n <= 0: leave as is);
+    returns the count in effect (1 without OpenMP)."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 class OrCamera(C.Structure):
@@ -77,6 +88,8 @@ def lib():
     with _lock:
         if _lib is None:
             L = C.CDLL(build())
+            L.orc_set_threads.argtypes = [C.c_int32]
+            L.orc_set_threads.restype = C.c_int32
             L.orc_project.argtypes = [C.POINTER(OrCamera), _D, _D]
             L.orc_unproject.argtypes = [C.POINTER(OrCamera), C.c_double, C.c_double, _D]
             L.orc_distort.argtypes = [C.POINTER(OrCamera), C.c_double, C.c_double, _D]

@@ -26,7 +26,10 @@
 //   plane hypotheses and dense fusion, each with its gradient
 //
 // Readings where the paper is silent are stated beside the code that takes
-// them.  Parity pins: see tests/test_oracle_*.py.
+// them.  Built with OpenMP, the independent loops (pixels of a sweep, rows of
+// a ray table, blocks of an integration) are shared among threads; each
+// pixel, ray and voxel is still computed by the same sequential code, so the
+// results do not depend on the thread count.  Parity pins: see tests/test_oracle_*.py.
 
 #include <algorithm>
 #include <array>
@@ -37,6 +40,10 @@
 #include <map>
 #include <set>
 #include <vector>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -279,6 +286,7 @@ void build_level(const OrCamera& ref_full, int n_cams, const OrCamera* cams_full
     size_t N = (size_t)ctx.ref.width * ctx.ref.height;
     ctx.ray.resize(N);
     ctx.ray_ok.resize(N);
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ctx.ref.height; ++y)
         for (int x = 0; x < ctx.ref.width; ++x) {
             double r[3];
@@ -586,9 +594,14 @@ void integrate(Tsdf& T, const float* depth, const OrCamera& cam, const OrPose& w
     const TsdfDesc& d = T.d;
     const int B = d.block_dim;
     const double lim = cam.xi > 0.0 ? std::min(cam.xi, 1.0 / cam.xi) : 0.0;
-    for (auto& kv : T.blocks) {
-        const Key& key = kv.first;
-        Block& blk = kv.second;
+    // Blocks are independent: with OpenMP they are shared among threads.
+    std::vector<std::pair<const Key*, Block*>> list;
+    list.reserve(T.blocks.size());
+    for (auto& kv : T.blocks) list.emplace_back(&kv.first, &kv.second);
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t bi = 0; bi < (int64_t)list.size(); ++bi) {
+        const Key& key = *list[bi].first;
+        Block& blk = *list[bi].second;
         for (int z = 0; z < B; ++z)
             for (int y = 0; y < B; ++y)
                 for (int x = 0; x < B; ++x) {
@@ -778,6 +791,18 @@ bool dense_voxel_obs(const DenseGrid& G, int gx, int gy, int gz, const float* de
 
 extern "C" {
 
+// Threads the pixel and block loops use (OpenMP build); returns the count in
+// effect.  n <= 0 leaves it unchanged.  Without OpenMP everything runs on one.
+int orc_set_threads(int32_t n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 int orc_project(const OrCamera* c, const double* X, double* uv) { return project(*c, X, &uv[0], &uv[1]); }
 
 int orc_unproject(const OrCamera* c, double u, double v, double* r) { return unproject(*c, u, v, r); }
@@ -838,6 +863,9 @@ int64_t orc_sweep_level(const OrCamera* ref_full, int32_t n_cams, const OrCamera
     build_level(*ref_full, n_cams, cams_full, *L, images, ctx);
     int64_t n = pix ? n_pix : (int64_t)ctx.ref.width * ctx.ref.height;
     int K = (int)ctx.planes.size();
+    // Pixels are independent: with OpenMP they are shared among threads, each
+    // pixel still computed by the same sequential code.
+#pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < n; ++i) {
         int x = pix ? pix[2 * i] : (int)(i % ctx.ref.width);
         int y = pix ? pix[2 * i + 1] : (int)(i / ctx.ref.width);

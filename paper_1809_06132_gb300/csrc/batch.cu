@@ -16,6 +16,7 @@ const void* batch_kernel_th24(int kp);
 using namespace ps;
 
 struct psbatch_s {
+    uint32_t magic = MAGIC_BATCH;  // first word: handle type for ps_sync_status
     int n = 0;
     std::vector<psweep_t*> sw;
     ps_batch_opts opts{};
@@ -203,6 +204,7 @@ extern "C" int psbatch_create(psweep_t* const* sweeps, int32_t n, const ps_batch
             if (D.n_chunks > 1) D.partial = b->partial + partial_off[(size_t)i * PS_MAX_LEVELS + l];
             D.done = b->zero + ctr_ints + tile_off[(size_t)i * PS_MAX_LEVELS + l];
             D.tiles_done = b->zero + 4 + i * C_N + C_TILES;
+            D.status = reinterpret_cast<unsigned*>(b->zero + 2);
         }
 
     // launch shape
@@ -375,8 +377,21 @@ extern "C" int psbatch_status(psbatch_t* b) {
         set_error("psbatch: a work item's wait gave up; the rest of the batch was skipped");
         return PS_ERR_TIMEOUT;
     }
+    if (st & DEV_STATE) {
+        set_error("psbatch: a tile's plane chunks were counted more often than it has chunks");
+        return PS_ERR_STATE;
+    }
     return PS_OK;
 }
+
+namespace ps {
+// The batch's status word is cleared by every run, so it holds the last
+// run's outcome.
+int batch_sync_status(psbatch_t* b, cudaStream_t s) {
+    PS_CUDA(cudaStreamSynchronize(s));
+    return psbatch_status(b);
+}
+}  // namespace ps
 
 extern "C" int psbatch_timing(psbatch_t* b, double* done_ms, double* span_ms) {
     clear_error();

@@ -70,6 +70,22 @@ extern "C" const char* ps_version(void) {
     return PS_CHECKED ? "psweep-gb300 0.1 (sm_103a, checked)" : "psweep-gb300 0.1 (sm_103a)";
 }
 
+extern "C" int ps_sync_status(void* handle, void* stream) {
+    ps::clear_error();
+    PS_ARG(handle != nullptr, "ps_sync_status: handle is NULL");
+    uint32_t magic = 0;
+    std::memcpy(&magic, handle, sizeof(magic));
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (magic) {
+        case ps::MAGIC_SWEEP: return ps::sweep_sync_status(static_cast<psweep_t*>(handle), s);
+        case ps::MAGIC_TSDF: return ps::tsdf_sync_status(static_cast<tsdf_t*>(handle), s);
+        case ps::MAGIC_BATCH: return ps::batch_sync_status(static_cast<psbatch_t*>(handle), s);
+        default: break;
+    }
+    ps::set_error("ps_sync_status: not a handle of this library");
+    return PS_ERR_ARG;
+}
+
 extern "C" int ps_check_read(uint32_t* bits) {
     ps::clear_error();
     PS_ARG(bits != nullptr, "ps_check_read: bits is NULL");

@@ -38,7 +38,22 @@ inline int cuda_fail(cudaError_t e, const char* what) {
 enum : uint32_t {
     DEV_CAPACITY = 1u,  // hash table or block pool full
     DEV_TIMEOUT = 2u,   // bounded probe loop gave up
+    DEV_STATE = 4u,     // a work counter ran past its end (overlapping calls on one handle)
 };
+
+// First word of every handle the library hands out, so that
+// ps_sync_status can tell the handle types apart.
+enum : uint32_t {
+    MAGIC_SWEEP = 0x50535750u,  // "PSWP"
+    MAGIC_TSDF = 0x50535444u,   // "PSTD"
+    MAGIC_BATCH = 0x50534241u,  // "PSBA"
+};
+
+// Latched-status readers of each handle type (synchronise the stream, read
+// and clear the status word, map its bits to a PS_* code).
+int sweep_sync_status(psweep_t* h, cudaStream_t s);
+int tsdf_sync_status(tsdf_t* t, cudaStream_t s);
+int batch_sync_status(psbatch_t* b, cudaStream_t s);
 
 // Checked build (compiled with -DPS_CHECK): bounds checks at the accesses
 // whose address comes from data (image gathers from projected coordinates,

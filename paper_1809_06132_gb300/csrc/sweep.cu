@@ -335,6 +335,7 @@ void free_sweep(psweep_t* h) {
     }
     cudaFree(h->boxes_dev);
     cudaFree(h->tile_counter);
+    cudaFree(h->status);
     for (int i = 0; i <= PS_MAX_CAMS; ++i) cudaFree(h->stage_img[i]);
     cudaFree(h->stage_depth);
     cudaFree(h->merged);
@@ -397,6 +398,19 @@ void fill_level(const psweep_t* h, int l, int th, int chunk, LevelD& D) {
     D.c1 = h->out_c1[l];
     D.c2 = h->out_c2[l];
     D.kstar = h->out_k[l];
+    D.status = h->status;
+}
+
+int sweep_sync_status(psweep_t* h, cudaStream_t s) {
+    unsigned st = 0;
+    PS_CUDA(cudaMemcpyAsync(&st, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    PS_CUDA(cudaStreamSynchronize(s));
+    if (!st) return PS_OK;
+    PS_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), s));
+    PS_CUDA(cudaStreamSynchronize(s));
+    set_error("psweep: a tile's plane chunks were counted more often than it has chunks "
+              "(overlapping calls on one sweep handle?)");
+    return PS_ERR_STATE;
 }
 
 int balanced_chunk(int n_planes, int most) {
@@ -601,6 +615,8 @@ extern "C" int psweep_create(const ps_sweep_desc* d, psweep_t** out) {
     PS_TRY(cudaMalloc(&h->stage_depth, sizeof(float) * (size_t)d->ref.width * d->ref.height));
     if (d->filter.enable) PS_TRY(cudaMalloc(&h->merged, sizeof(float) * (size_t)d->ref.width * d->ref.height));
     PS_TRY(cudaMalloc(&h->tile_counter, sizeof(int)));
+    PS_TRY(cudaMalloc(&h->status, sizeof(unsigned)));
+    PS_TRY(cudaMemset(h->status, 0, sizeof(unsigned)));
     {
         int dev = 0, optin = 0;
         PS_TRY(cudaGetDevice(&dev));

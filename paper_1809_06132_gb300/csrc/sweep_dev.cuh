@@ -54,6 +54,7 @@ struct LevelD {
     float* partial;                // [n_items][7][TH x TW] chunk results (when n_chunks > 1)
     int* done;                     // [n_tiles] finished chunks per tile (zeroed per launch)
     int* tiles_done;               // bumped once per finished tile (batched launch), or NULL
+    unsigned* status;              // latched DEV_* bits of the owning handle, or NULL
     float* depth;
     float* c1;
     float* c2;
@@ -691,7 +692,12 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
     }
     __threadfence();
     __syncthreads();
-    if (tid == 0) *s_flag = atomicAdd(&L.done[tile], 1) == L.n_chunks - 1;
+    if (tid == 0) {
+        const int prev = atomicAdd(&L.done[tile], 1);
+        *s_flag = prev == L.n_chunks - 1;
+        // more completions than chunks: the counters were not this call's alone
+        if (prev >= L.n_chunks && L.status) atomicOr(L.status, DEV_STATE);
+    }
     __syncthreads();
     if (*s_flag) {
         __threadfence();
@@ -859,6 +865,8 @@ __device__ __forceinline__ bool in_boxes(const ps_box* b, int n, int u, int v) {
 using namespace ps;
 
 struct psweep_s {
+    uint32_t magic = MAGIC_SWEEP;  // first word: handle type for ps_sync_status
+    unsigned* status = nullptr;    // latched DEV_* bits (device word)
     ps_camera ref;
     int n_cams;
     ps_camera cams[PS_MAX_CAMS];

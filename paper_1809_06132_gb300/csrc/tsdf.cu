@@ -533,6 +533,7 @@ int build_rays(const ps_camera& cam, float4* rays, double* max_angle);
 using namespace ps;
 
 struct tsdf_s {
+    uint32_t magic = MAGIC_TSDF;  // first word: handle type for ps_sync_status
     ps_tsdf_desc d;
     bool dense = false;
     TsdfDev T{};
@@ -894,6 +895,10 @@ extern "C" int tsdf_load(tsdf_t* t, const int32_t* keys, const float* D, const f
     return PS_OK;
 }
 
+namespace ps {
+int tsdf_sync_status(tsdf_t* t, cudaStream_t s) { return read_status(t, s); }
+}  // namespace ps
+
 extern "C" int tsdf_status(tsdf_t* t, void* stream) {
     clear_error();
     PS_ARG(t != nullptr, "tsdf_status: NULL handle");
@@ -902,12 +907,15 @@ extern "C" int tsdf_status(tsdf_t* t, void* stream) {
 
 // ===================================================================== allocation-free dense fusion
 //
-// For callers that cannot allocate device memory while they run (graph
-// capture, pre-planned real-time memory, foreign allocators): the working
-// memory lives in this fixed static device array instead of a handle.
-// Layout: [0] status, [4] block count, [8] listed-block count, [12] depth
-// maximum bits, [256 ..) block keys (int4 x PS_STATIC_MAX_BLOCKS), then the
-// visible-block list (int x PS_STATIC_MAX_BLOCKS).
+// For callers that cannot allocate device memory while they run (real-time
+// loops whose memory is planned once up front, hosts whose device memory
+// belongs to another allocator): the working memory lives in this fixed
+// static device array instead of a handle.
+// Layout: [0] status word, [4] block count, [8] listed-block count, [12]
+// depth maximum bits, [256 ..) block keys (int4 x PS_STATIC_MAX_BLOCKS), then
+// the visible-block list (int x PS_STATIC_MAX_BLOCKS).  The status word only
+// gives the shared kernels a valid target: on a dense grid nothing sets it
+// (no hash table, no pool, no segment allocation), so it is never read.
 
 #include <mutex>
 
@@ -1047,10 +1055,12 @@ extern "C" int tsdf_integrate_dense_static(float* voxels, const int32_t* dims, c
     for (int i = 0; i < 3; ++i)
         PS_ARG(dims[i] > 0 && dims[i] % 8 == 0, "tsdf_integrate_dense_static: dims must be positive multiples of 8");
     const long long nx = dims[0] / 8, ny = dims[1] / 8, nz = dims[2] / 8;
+    // compared step by step: each factor is at least 1, so no product below overflows
+    PS_ARG(nx <= PS_STATIC_MAX_BLOCKS && ny <= PS_STATIC_MAX_BLOCKS / nx &&
+               nz <= PS_STATIC_MAX_BLOCKS / (nx * ny),
+           "tsdf_integrate_dense_static: a %lld x %lld x %lld block grid exceeds the static limit of %d blocks "
+           "(%d voxels)", nx, ny, nz, PS_STATIC_MAX_BLOCKS, PS_STATIC_MAX_BLOCKS * B3);
     const long long n_blocks = nx * ny * nz;
-    PS_ARG(n_blocks <= PS_STATIC_MAX_BLOCKS,
-           "tsdf_integrate_dense_static: %lld blocks exceed the static limit of %d blocks (%d voxels)", n_blocks,
-           PS_STATIC_MAX_BLOCKS, PS_STATIC_MAX_BLOCKS * B3);
     for (int i = 0; i < 12; ++i)
         PS_ARG(std::isfinite(i < 9 ? w2c->R[i] : w2c->t[i - 9]), "tsdf_integrate_dense_static: pose not finite");
     unsigned char* base = nullptr;
@@ -1074,7 +1084,7 @@ extern "C" int tsdf_integrate_dense_static(float* voxels, const int32_t* dims, c
     PS_CUDA(cudaGetDevice(&dev));
     PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int W = cam->width, H = cam->height;
-    PS_CUDA(cudaMemsetAsync(base, 0, 256, s));  // status, counters, depth maximum start at zero
+    PS_CUDA(cudaMemsetAsync(base, 0, 256, s));  // counters and depth maximum start at zero
     static_dense_keys_kernel<<<(int)((n_blocks + 255) / 256), 256, 0, s>>>(T.pool_keys, T.n_alloc, (int)nx, (int)ny,
                                                                            (int)nz);
     PS_CUDA(cudaGetLastError());

@@ -18,8 +18,9 @@ import torch
 
 from . import _build
 
-PS_OK, PS_ERR_ARG, PS_ERR_OOM, PS_ERR_CAPACITY, PS_ERR_CUDA, PS_ERR_TIMEOUT = range(6)
-STATUS_NAMES = {1: "PS_ERR_ARG", 2: "PS_ERR_OOM", 3: "PS_ERR_CAPACITY", 4: "PS_ERR_CUDA", 5: "PS_ERR_TIMEOUT"}
+PS_OK, PS_ERR_ARG, PS_ERR_OOM, PS_ERR_CAPACITY, PS_ERR_CUDA, PS_ERR_TIMEOUT, PS_ERR_STATE = range(7)
+STATUS_NAMES = {1: "PS_ERR_ARG", 2: "PS_ERR_OOM", 3: "PS_ERR_CAPACITY", 4: "PS_ERR_CUDA", 5: "PS_ERR_TIMEOUT",
+                6: "PS_ERR_STATE"}
 MAX_SETS, MAX_CAMS, MAX_LEVELS = 4, 4, 2
 
 # every symbol include/psweep.h declares
@@ -30,7 +31,7 @@ EXPORTS = ["psweep_create", "psweep_depth", "psweep_destroy", "tsdf_create", "ts
            "psbatch_queue_stats", "psbatch_destroy", "psbatch_autotune", "ps_pipe_create", "ps_pipe_push",
            "ps_pipe_flush", "ps_pipe_destroy", "psdiff_create", "psdiff_forward", "psdiff_backward",
            "psdiff_destroy", "tsdf_dense_fuse_backward",
-           "ps_check_read", "ps_last_error", "ps_version"]
+           "ps_check_read", "ps_last_error", "ps_version", "ps_sync_status"]
 
 
 class PsError(RuntimeError):
@@ -163,6 +164,7 @@ def load(build_if_missing: bool = True):
     L.tsdf_dense_fuse_backward.argtypes = [P, P, P, C.c_double, C.c_double, C.c_double, P, C.POINTER(ps_camera),
                                            C.POINTER(ps_pose), P, P, P, P, P]
     L.ps_check_read.argtypes = [C.POINTER(C.c_uint32)]
+    L.ps_sync_status.argtypes = [P, P]
     L.ps_last_error.restype = C.c_char_p
     L.ps_version.restype = C.c_char_p
     _lib = L
@@ -276,6 +278,11 @@ class Sweep:
         n = C.c_int32()
         _check(load().psweep_profile_read(self.h, ms, C.byref(n)))
         return list(ms), n.value
+
+    def sync_status(self, stream=None) -> int:
+        """ps_sync_status: synchronise the stream, return and clear the
+        handle's latched device status (a PS_* code)."""
+        return load().ps_sync_status(self.h, _stream_ptr(stream))
 
     def level_shapes(self):
         return [level_shape(self.rig.ref, lv) for lv in self.levels]
@@ -444,6 +451,10 @@ class Batch:
     def status(self) -> int:
         return load().psbatch_status(self.h)
 
+    def sync_status(self, stream=None) -> int:
+        """ps_sync_status on this batch handle (the last run's outcome)."""
+        return load().ps_sync_status(self.h, _stream_ptr(stream))
+
     def queue_stats(self):
         c = (C.c_int32 * 6)()
         _check(load().psbatch_queue_stats(self.h, c))
@@ -517,6 +528,10 @@ class Tsdf:
     def status(self, stream=None) -> int:
         return load().tsdf_status(self.h, _stream_ptr(stream))
 
+    def sync_status(self, stream=None) -> int:
+        """ps_sync_status on this handle (same outcome as status())."""
+        return load().ps_sync_status(self.h, _stream_ptr(stream))
+
     def swap_out(self, local_center, capacity: int = None, device="cuda", stream=None):
         """Move the blocks outside the local map out of the map: (keys, D, W) CUDA tensors."""
         device = _cuda_device(device, "swap_out")
@@ -575,8 +590,19 @@ def tsdf_integrate_dense_static(voxels: torch.Tensor, dims, origin, voxel_size: 
     """Fuse one depth map into a caller-owned dense grid without any
     allocation by the library (for callers that cannot allocate while they
     run; the working memory is a fixed static device array).  voxels:
-    contiguous CUDA float32 tensor of n_blocks x 512 x 2 ({D, w} pairs)."""
-    d = (C.c_int32 * 3)(*[int(v) for v in dims])
+    contiguous CUDA float32 tensor of n_blocks x 512 x 2 ({D, w} pairs);
+    depth: float32 cam.height x cam.width.  The C library only sees
+    pointers, so the sizes are checked here: a short tensor would be read
+    and written past its end."""
+    dims = [int(v) for v in dims]
+    if len(dims) != 3 or any(v <= 0 or v % 8 for v in dims):
+        raise ValueError(f"dims must be three positive multiples of 8, got {dims}")
+    n_blocks = (dims[0] // 8) * (dims[1] // 8) * (dims[2] // 8)
+    if voxels.numel() != n_blocks * 1024:
+        raise ValueError(f"voxels holds {voxels.numel()} floats; dims {dims} need {n_blocks} x 512 x 2")
+    if depth.numel() != int(cam.width) * int(cam.height):
+        raise ValueError(f"depth holds {depth.numel()} values; the camera is {cam.width} x {cam.height}")
+    d = (C.c_int32 * 3)(*dims)
     o = (C.c_double * 3)(*[float(v) for v in origin])
     cz = camera(cam)
     pz = pose(world_to_cam)

@@ -3,8 +3,11 @@
 Criteria (all computed on the same seeded inputs):
   * winning plane: identical on >= 99.9% of pixels whose oracle margin
     (second-best minus best cost) exceeds 1e-3;
-  * depth: |gpu - oracle| <= 1e-4 * oracle on >= 99.9% of those pixels
-    where the plane agrees (the rest is bounded by one plane spacing);
+  * depth: |gpu - oracle| <= 1e-4 * oracle on every one of those pixels
+    where the plane agrees, except where the oracle's own costs show that
+    the sub-plane fit turns a cost rounding into a larger depth change (see
+    fit_sensitivity); such pixels are counted and bounded, never silently
+    dropped;
   * validity (a depth at all): identical on >= 99.9% of pixels; a
     mismatch needs a warped sample or a window variance within float
     rounding of a validity threshold;
@@ -17,6 +20,9 @@ MARGIN = 1e-3
 DEPTH_REL = 1e-4
 FRAC = 0.999
 TSDF_ABS = 1e-5
+# Pixels whose sub-plane fit is rounding-sensitive may be at most this
+# fraction of the margin-gated pixels.
+SENSITIVE_FRAC = 1e-3
 
 
 def sweep_stats(o, g):
@@ -24,32 +30,134 @@ def sweep_stats(o, g):
     ok, gk = o["kstar"], g["kstar"]
     ov, gv = ok >= 0, gk >= 0
     n = ok.size
-    gated = ov & gv & ((o["c2"] - o["c1"]) > MARGIN)
+    margin = np.where(ov, o["c2"], 0.0) - np.where(ov, o["c1"], 0.0)  # c2 = +inf when only one plane is valid
+    gated = ov & gv & (margin > MARGIN)
     agree = gated & (ok == gk)
     od = o["depth"][agree]
     rel = np.abs(g["depth"][agree] - od) / np.maximum(od, 1e-30)
     c1err = np.abs(g["c1"][agree] - o["c1"][agree])
+    q = (lambda p: float(np.quantile(rel, p)) if rel.size else 0.0)
     return dict(
         n=int(n),
         n_valid_oracle=int(ov.sum()),
         valid_mismatch=float((ov != gv).mean()),
+        n_valid_mismatch=int((ov != gv).sum()),
         n_gated=int(gated.sum()),
         index_agree=float(agree.sum() / max(1, gated.sum())),
+        n_index_disagree=int(gated.sum() - agree.sum()),
         depth_ok=float((rel <= DEPTH_REL).mean()) if rel.size else 1.0,
-        depth_rel_p50=float(np.median(rel)) if rel.size else 0.0,
-        depth_rel_p999=float(np.quantile(rel, 0.999)) if rel.size else 0.0,
+        n_depth_over=int((rel > DEPTH_REL).sum()),
+        depth_rel_p50=q(0.5),
+        depth_rel_p90=q(0.9),
+        depth_rel_p99=q(0.99),
+        depth_rel_p999=q(0.999),
         depth_rel_max=float(rel.max()) if rel.size else 0.0,
         c1_abs_max=float(c1err.max()) if c1err.size else 0.0,
         c1_abs_p50=float(np.median(c1err)) if c1err.size else 0.0,
     )
 
 
-def assert_sweep_parity(o, g, min_gated=50):
+def depth_over(o, g):
+    """Flat indices of margin-gated pixels with the same plane whose relative
+    depth error exceeds DEPTH_REL, and their errors."""
+    ok, gk = o["kstar"].reshape(-1), g["kstar"].reshape(-1)
+    ov, gv = ok >= 0, gk >= 0
+    c1, c2 = o["c1"].reshape(-1), o["c2"].reshape(-1)
+    margin = np.where(ov, c2, 0.0) - np.where(ov, c1, 0.0)
+    agree = ov & gv & (margin > MARGIN) & (ok == gk)
+    od, gd = o["depth"].reshape(-1), g["depth"].reshape(-1)
+    rel = np.zeros(ok.size)
+    rel[agree] = np.abs(gd[agree] - od[agree]) / od[agree]
+    idx = np.nonzero(agree & (rel > DEPTH_REL))[0]
+    return idx, rel[idx]
+
+
+def fit_sensitivity(costs, kstar, lv, planes, eps):
+    """Upper bound on the relative depth change that a perturbation of at
+    most eps in each aggregated cost causes through the sub-plane fit, per
+    pixel (costs: (n, K) oracle costs, kstar: (n,)).
+
+    The fit is delta = (c- - c+) / (2 (c- - 2 c0 + c+)) over the winner c0
+    and its neighbours c-, c+ in the same plane set.  With den = c- - 2 c0 +
+    c+, its partial derivatives are (c+ - c0) / den^2, num / den^2 and
+    (c0 - c-) / den^2 (num = c- - c+), so |d delta| <= eps (|c+ - c0| +
+    |num| + |c- - c0|) / den^2.  A step of delta moves the plane parameter
+    by one plane spacing: for fronto planes the inverse depth moves by
+    (1/a - 1/b) / (count - 1), a relative depth change of that over the
+    inverse depth; for ground planes the offset moves by (b - a) / (count
+    - 1), relative to the offset.  A clamped or absent fit gives 0."""
+    _, d, s_of, loc = planes
+    out = np.zeros(len(kstar))
+    for i, (row, k) in enumerate(zip(costs, kstar)):
+        if k < 0:
+            continue
+        S = lv.sets[int(s_of[k])]
+        li = int(loc[k])
+        if not (0 < li < S.count - 1):
+            continue
+        cm, c0, cp = row[k - 1], row[k], row[k + 1]
+        if not (np.isfinite(cm) and np.isfinite(cp)):
+            continue
+        den = cm - 2 * c0 + cp
+        if den <= 0:
+            continue
+        delta = (cm - cp) / (2 * den)
+        grad = (abs(cp - c0) + abs(cm - cp) + abs(c0 - cm)) / den ** 2
+        if abs(delta) > 0.5 + eps * grad:  # clamped, and stays clamped under the perturbation
+            continue
+        t = (li + delta) / (S.count - 1)
+        if S.family == 0:
+            inv = 1.0 / S.b + t * (1.0 / S.a - 1.0 / S.b)
+            step = (1.0 / S.a - 1.0 / S.b) / (S.count - 1) / inv
+        else:
+            param = S.a + t * (S.b - S.a)
+            step = (S.b - S.a) / (S.count - 1) / abs(param)
+        out[i] = eps * grad * abs(step)
+    return out
+
+
+def oracle_costs_at(rig, lv, imgs, pix=None):
+    """Function of flat indices into a level (pix None) or into a pixel list
+    (pix: (n, 2) x, y) giving the oracle's (n, K) aggregated costs there."""
+    import oracle
+    from oracle import level_shape
+    W = level_shape(rig, lv)[1]
+
+    def f(idx):
+        p = np.stack([idx % W, idx // W], axis=1) if pix is None else np.asarray(pix)[idx]
+        return oracle.sweep_level(rig, lv, imgs, pix=p, want_costs=True)["costs"]
+    return f
+
+
+def assert_sweep_parity(o, g, min_gated=50, src=None):
+    """North-star parity of one level's outputs.  Every margin-gated pixel
+    whose plane agrees must have its depth within DEPTH_REL, except pixels
+    the oracle's costs show to be rounding-sensitive.  src = (rig, level,
+    images[, pix]) names the oracle's inputs (pix: the sampled pixels when o
+    and g hold a pixel list); a pixel over DEPTH_REL is accepted when
+    fit_sensitivity, with eps = the largest best-cost difference measured
+    over the level's agreeing pixels (the FP32 cost error seen), reaches
+    its error.  Accepted pixels are at most SENSITIVE_FRAC of the gated
+    ones."""
     s = sweep_stats(o, g)
     assert s["n_gated"] >= min_gated, s
     assert s["valid_mismatch"] <= 1 - FRAC, s
     assert s["index_agree"] >= FRAC, s
-    assert s["depth_ok"] >= FRAC, s
+    idx, rel = depth_over(o, g)
+    s["n_fit_sensitive"] = 0
+    if idx.size:
+        assert src is not None, ("depth beyond 1e-4 with no oracle inputs to explain it", s)
+        import oracle
+        rig, lv, imgs = src[:3]
+        pix = src[3] if len(src) > 3 else None
+        eps = max(s["c1_abs_max"], 1e-7)
+        C = oracle_costs_at(rig, lv, imgs, pix)(idx)
+        sens = fit_sensitivity(C, o["kstar"].reshape(-1)[idx], lv, oracle.level_planes(lv), eps)
+        unexplained = rel > DEPTH_REL + sens
+        assert not unexplained.any(), dict(s, unexplained=int(unexplained.sum()),
+                                           worst=float(rel[unexplained].max()), eps=eps)
+        s["n_fit_sensitive"] = int(idx.size)
+        assert idx.size <= SENSITIVE_FRAC * s["n_gated"], s
     return s
 
 
@@ -66,5 +174,6 @@ def tsdf_compare(o_keys, o_D, o_W, o_amb, g_keys, g_D, g_W):
     dD = np.abs(g_D[gj] - o_D[oi])[clean]
     wW = (g_W[gj] != o_W[oi])[clean]
     return dict(n_common=len(common), n_voxels=int(clean.sum()), n_amb=int(amb.sum()),
+                amb_frac=float(amb.mean()),
                 D_abs_max=float(dD.max()) if dD.size else 0.0, W_mismatch=int(wW.sum()),
                 n_updated=int((o_W[oi][clean] > 0).sum()))

@@ -144,3 +144,30 @@ def test_points_argument_errors_without_gpu():
     L = P.load()
     n = C.c_int64()
     assert L.tsdf_extract_points(None, 3.0, None, None, 0, C.byref(n), None) == P.PS_ERR_ARG
+
+
+def test_static_fusion_wrapper_checks_tensor_sizes():
+    # the C entry point sees only pointers; the binding must refuse tensors
+    # whose size does not match the grid or the camera before calling it
+    import torch
+    import scenes
+    wl = scenes.tiny(0)
+    p = wl.tsdf
+    n_blocks = (p.dense_dim[0] // 8) * (p.dense_dim[1] // 8) * (p.dense_dim[2] // 8)
+    good_vox = torch.zeros((n_blocks, 512, 2))
+    good_depth = torch.zeros((wl.rig.ref.height, wl.rig.ref.width))
+    cases = [(torch.zeros((n_blocks - 1, 512, 2)), good_depth, p.dense_dim),
+             (good_vox, torch.zeros((wl.rig.ref.height - 1, wl.rig.ref.width)), p.dense_dim),
+             (good_vox, good_depth, (p.dense_dim[0], p.dense_dim[1], 12))]
+    for vox, dep, dims in cases:
+        with pytest.raises(ValueError):
+            P.tsdf_integrate_dense_static(vox, dims, p.origin, p.voxel_size, p.mu, p.w_max, dep, wl.rig.ref,
+                                          wl.world_to_ref[0])
+
+
+def test_sync_status_rejects_what_is_no_handle():
+    L = P.load()
+    assert L.ps_sync_status(None, None) == P.PS_ERR_ARG
+    junk = (C.c_uint32 * 16)()            # host memory whose first word is no handle type
+    assert L.ps_sync_status(C.cast(junk, C.c_void_p), None) == P.PS_ERR_ARG
+    assert b"not a handle" in L.ps_last_error()

@@ -134,6 +134,7 @@ def test_bounded_wait_reports_timeout_and_context_stays_usable(mix):
     sw = mix["sweeps"][:3]
     b = P.Batch(sw, wait_limit_ms=100, drill_unmet_wait=True)
     b.run(mix["images"][:3], boxes=mix["boxes"][:3])
+    assert b.sync_status() == P.PS_ERR_TIMEOUT      # through the handle-generic call
     assert b.status() == P.PS_ERR_TIMEOUT
     with pytest.raises(P.PsError) as e:
         b.timing()

@@ -104,7 +104,9 @@ def test_pool_capacity_is_reported():
     assert T.count() == 8
     # the map stays usable: another frame runs and the overflow is reported again
     T.integrate(d, wl.world_to_ref[0], wl.local_center(0))
-    assert T.status() == P.PS_ERR_CAPACITY
+    # the same latched status through the handle-generic ps_sync_status
+    assert T.sync_status() == P.PS_ERR_CAPACITY
+    assert T.sync_status() == P.PS_OK
 
 
 def test_local_center_required():
@@ -203,8 +205,15 @@ def test_street_full_size_parity():
     assert (oset - amb_blocks) <= gset
     assert gset <= (oset | maybe)
     s = tsdf_compare(ok, oD, oW, oamb, gk, gD, gW)
-    print("street full-size fusion", s, "blocks", len(gset), len(oset))
+    n_amb_blocks = len(amb_blocks)
+    print("street full-size fusion", s, "blocks", len(gset), len(oset), "fully marked blocks", n_amb_blocks)
     assert len(gset) > 1000 and s["n_updated"] > 200000
+    # the rounding marks exempt few voxels and few whole blocks (measured:
+    # 3.4% of the voxels, most of them in the 2.1% of blocks whose first
+    # allocation frame is rounding-sensitive): a drift in the band logic
+    # that widened them would fail here
+    assert s["n_amb"] < 0.05 * (s["n_amb"] + s["n_voxels"]), s
+    assert n_amb_blocks < 0.03 * len(oset), (n_amb_blocks, len(oset))
     assert s["D_abs_max"] <= TSDF_ABS, s
     assert s["W_mismatch"] == 0, s
 
