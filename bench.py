@@ -58,8 +58,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", choices=["street", "ring", "ringloop", "batch", "diff"], default="street",
-                    help="street: the paper-shaped frame (default); ring: 4 cameras, 256 full-resolution planes, "
+    ap.add_argument("--config", choices=["street", "tiny", "ring", "ringloop", "batch", "diff"], default="street",
+                    help="street: the paper-shaped frame (default); tiny: 160x128, 1 matching camera, 32 planes, "
+                         "dense 64^3 TSDF; ring: 4 cameras, 256 full-resolution planes, "
                          "2 cm voxels on a 500 m loop; batch: 64 uneven sweeps in one persistent launch; "
                          "diff: soft-argmin forward/backward and extrinsic refinement; ringloop: fusion of the "
                          "whole 1000-frame ring at 2 cm")
@@ -72,18 +73,22 @@ def workload(args, seed):
     import scenes
     if args.config == "ring":
         return scenes.ring(seed, n_frames=1000)
+    if args.config == "tiny":
+        return scenes.tiny(seed, n_frames=100)
     return scenes.street(seed, n_frames=100)
 
 
 def workload_config(args, wl, nf, world):
     """The `config` object of a street / ring line (the same for both arms)."""
-    street = args.config == "street"
+    levels = {"street": "320x256 (64 fronto + 32 ground, 7x7) + 640x512 crop (128 fronto, 9x9)",
+              "tiny": "160x128 (32 fronto on 0.5-20 m, 5x5)"}
+    tsdf = {"street": "8^3 blocks, 0.1 m voxels, mu 0.5 m, 60x3x60 m local map",
+            "tiny": "dense 64^3 grid, 0.05 m voxels, mu 0.2 m"}
     return {"workload": wl.name, "ref": f"{wl.rig.ref.width}x{wl.rig.ref.height}",
             "matching_cams": len(wl.rig.cams),
-            "levels": ("320x256 (64 fronto + 32 ground, 7x7) + 640x512 crop (128 fronto, 9x9)" if street
-                       else "1280x1024 (256 fronto, 9x9)"),
-            "tsdf": ("8^3 blocks, 0.1 m voxels, mu 0.5 m, 60x3x60 m local map" if street
-                     else "8^3 blocks, 0.02 m voxels, mu 0.1 m, 60x3x60 m local map, 2^23-block pool"),
+            "levels": levels.get(args.config, "1280x1024 (256 fronto, 9x9)"),
+            "tsdf": tsdf.get(args.config, "8^3 blocks, 0.02 m voxels, mu 0.1 m, 60x3x60 m local map, "
+                                          "2^23-block pool"),
             "image_storage": "fp16" if getattr(args, "half", False) else "fp32", "frames": nf,
             "l2": "flushed between steps (256 MB write outside the step events)",
             "parallelism": f"replicas x{world} (independent sequences)"}
@@ -183,46 +188,94 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- CPU oracle leg
 
-def oracle_step(wl, imgs, f, rng, n_pix_per_level):
-    """Oracle sweep of one frame on a bounded sample: n random pixels per
-    level, timed and extrapolated linearly to every pixel of the level (the
-    sweep's cost is the same for every pixel).  Returns (estimated seconds
-    for the whole frame's sweep, wall seconds spent)."""
+def oracle_band(wl, imgs, band: int, n_bands: int, outs):
+    """Oracle sweep of the rows y = band (mod n_bands) of every level of one
+    frame (every pixel of those rows; interleaved, so that each band holds a
+    like share of sky, ground and facades), written into outs[level]
+    (dicts of full level arrays)."""
     import oracle
-    t0 = time.perf_counter()
-    est = 0.0
+    for lv, o in zip(wl.levels, outs):
+        H, W = oracle.level_shape(wl.rig, lv)
+        rows = np.arange(band, H, n_bands)
+        yy, xx = np.meshgrid(rows, np.arange(W), indexing="ij")
+        pix = np.stack([xx.ravel(), yy.ravel()], axis=1).astype(np.int32)
+        r = oracle.sweep_level(wl.rig, lv, imgs, pix=pix)
+        for k in ("depth", "c1", "c2", "kstar"):
+            o[k][rows] = r[k].reshape(len(rows), W)
+
+
+def oracle_level_outs(wl):
+    import oracle
+    outs = []
     for lv in wl.levels:
         H, W = oracle.level_shape(wl.rig, lv)
-        rho = lv.window // 2
-        pix = np.stack([rng.integers(rho, W - rho, n_pix_per_level), rng.integers(rho, H - rho, n_pix_per_level)],
-                       axis=1)
-        ts = time.perf_counter()
-        oracle.sweep_level(wl.rig, lv, imgs, pix=pix)
-        est += (time.perf_counter() - ts) * (W * H) / n_pix_per_level
-    return est, time.perf_counter() - t0
+        outs.append({"depth": np.zeros((H, W)), "c1": np.zeros((H, W)), "c2": np.zeros((H, W)),
+                     "kstar": np.zeros((H, W), np.int32)})
+    return outs
 
 
-def cpu_baseline(wl, frames, n_steps=3, n_pix=1500):
-    """Frames/s of the FP64 oracle (single thread) on a bounded sample."""
+def oracle_finish_frame(wl, f, outs, T):
+    """Merge of the oracle's level maps, boxes, and fusion of the merged map."""
     import oracle
-    rng = np.random.default_rng(11)
+    low = crop = None
+    s, cw, ch = 1, 0, 0
+    for lv, o in zip(wl.levels, outs):
+        if lv.kind == 0:
+            low, s = o["depth"], lv.factor
+        else:
+            crop, cw, ch = o["depth"], lv.crop_w, lv.crop_h
+    D = oracle.merge(wl.rig.ref.width, wl.rig.ref.height, low, s, crop, cw, ch, wl.boxes[f])
+    T.integrate(D.astype(np.float32), wl.rig.ref, wl.world_to_ref[f], wl.local_center(f))
+
+
+def oracle_frame_s(wl, imgs, f, threads, n_bands=1, bands=None):
+    """Seconds of the oracle's whole path for frame f on `threads` threads:
+    the sweep of both levels at every pixel (or only `bands` of n_bands
+    interleaved row bands, then scaled by n_bands / len(bands)), the merge,
+    the boxes and the fusion of the frame's merged map into a fresh map."""
+    import oracle
+    oracle.set_threads(threads)
+    outs = oracle_level_outs(wl)
+    bands = list(range(n_bands)) if bands is None else list(bands)
+    t0 = time.perf_counter()
+    for b in bands:
+        oracle_band(wl, imgs, b, n_bands, outs)
+    t_sweep = (time.perf_counter() - t0) * n_bands / len(bands)
     T = oracle.Tsdf(wl.tsdf)
-    sweep_est, wall = [], 0.0
-    tsdf_t = []
-    for i in range(n_steps):
-        imgs, depth = frames[i]
-        est, w = oracle_step(wl, imgs, i, rng, n_pix)
-        sweep_est.append(est)
-        wall += w
-        ts = time.perf_counter()
-        T.integrate(depth, wl.rig.ref, wl.world_to_ref[i], wl.local_center(i))
-        tsdf_t.append(time.perf_counter() - ts)
-        wall += tsdf_t[-1]
-    per_frame = statistics.mean(sweep_est) + statistics.mean(tsdf_t)
-    return {"value": 1.0 / per_frame, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n_steps} frames: sweep at {n_pix} random pixels per level (extrapolated linearly to the "
-                      f"whole frame), TSDF fusion of the full frame's depth map; {wall:.1f} s of CPU work",
-            "sweep_s_per_frame": statistics.mean(sweep_est), "tsdf_s_per_frame": statistics.mean(tsdf_t)}
+    t1 = time.perf_counter()
+    oracle_finish_frame(wl, f, outs, T)
+    return t_sweep + time.perf_counter() - t1, t_sweep
+
+
+def cpu_baseline(wl, frames, tiny_wl=None):
+    """Frames/s of the FP64 oracle on the host cores, measured: frame 0 of the
+    workload through the whole path on every core (nproc threads), the same
+    frame on one thread over every 16th row of each level (scaled to the
+    frame) plus its full fusion, and, with tiny_wl, the tiny workload's
+    frame on one thread and on every core."""
+    import oracle
+    n = os.cpu_count() or 1
+    imgs = frames[0][0]
+    t_all, sw_all = oracle_frame_s(wl, imgs, 0, n)
+    t_one, sw_one = oracle_frame_s(wl, imgs, 0, 1, n_bands=16, bands=[7])
+    out = {"value": 1.0 / t_all, "unit": UNIT, "cores": n, "threads": oracle.set_threads(n), "kind": "oracle",
+           "sample": f"frame 0 of {wl.name}: both levels swept at every pixel, merge, boxes and fusion of the "
+                     f"merged map, on {n} threads ({t_all:.1f} s)",
+           "sweep_s_per_frame": sw_all,
+           "single_thread": {"value": 1.0 / t_one, "unit": UNIT, "threads": 1,
+                             "sample": "frame 0, every 16th row of each level (rows 7 mod 16) swept on one thread "
+                                       "and scaled x16, plus the frame's merge and fusion",
+                             "sweep_s_per_frame": sw_one}}
+    if tiny_wl is not None:
+        import scenes
+        timgs, _ = scenes.FrameSource(tiny_wl).frame(0)
+        timgs = [i.numpy() for i in timgs]
+        a, _ = oracle_frame_s(tiny_wl, timgs, 0, 1)
+        b, _ = oracle_frame_s(tiny_wl, timgs, 0, n)
+        out["tiny"] = {"workload": tiny_wl.name, "frames": tiny_wl.n_frames, "single_thread": 1.0 / a,
+                       f"threads_{n}": 1.0 / b, "unit": UNIT}
+    oracle.set_threads(n)
+    return out
 
 
 # ----------------------------------------------------------------- main
@@ -242,41 +295,51 @@ def render_frames(wl, n, device):
 
 
 def run_reference(args):
+    """The FP64 oracle as it stands, on every host core, through the whole
+    path: each step sweeps one interleaved row band (every 4th row of both
+    levels) of the current frame at every pixel; the step that completes a
+    frame also merges its levels, applies the boxes and fuses the merged
+    map.  Four steps make a frame, so the K timed steps measure K/4 whole
+    frames; value = frames / seconds, ms_per_step = the measured mean step."""
     import scenes
+    import oracle
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    wl = scenes.street(args.seed, n_frames=100)
+    n_bands = 4
+    wl = workload(args, args.seed)
     n = args.warmup + args.steps
-    nf = min(n, 10)
+    nf = (n + n_bands - 1) // n_bands
     try:
         import torch
         dev = "cuda" if torch.cuda.is_available() else "cpu"
     except Exception:
         dev = "cpu"
     frames = render_frames(wl, nf, dev)   # input synthesis only (torch ops)
-    import oracle
-    rng = np.random.default_rng(5)
+    threads = oracle.set_threads(os.cpu_count() or 1)
     T = oracle.Tsdf(wl.tsdf)
+    outs = oracle_level_outs(wl)
     times = []
     for i in range(n):
-        f = i % nf
-        imgs, depth = frames[f]
-        est, _ = oracle_step(wl, imgs, f, rng, 24)
-        ts = time.perf_counter()
-        T.integrate(depth, wl.rig.ref, wl.world_to_ref[f], wl.local_center(f))
-        t_tsdf = time.perf_counter() - ts
+        f, b = i // n_bands, i % n_bands
+        t0 = time.perf_counter()
+        oracle_band(wl, frames[f][0], b, n_bands, outs)
+        if b == n_bands - 1:
+            oracle_finish_frame(wl, f, outs, T)
         if i >= args.warmup:
-            times.append(est + t_tsdf)
-    per = statistics.mean(times)
-    val = 1.0 / per
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    val = (len(times) / n_bands) / total
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / len(times) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args, wl, nf, world),
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "per step: sweep at 24 random pixels per level extrapolated linearly to the "
-                                       "whole frame, plus full-frame TSDF fusion of the frame's range map"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count() or 1, "threads": threads,
+                             "kind": "oracle",
+                             "sample": f"each step: one of {n_bands} row bands of both levels swept at every pixel; "
+                                       f"every {n_bands}th step also merges, masks and fuses the frame; "
+                                       f"{len(times) / n_bands:.2f} frames timed"},
+            "step_ms": {"median": statistics.median(times) * 1e3, "min": min(times) * 1e3, "max": max(times) * 1e3},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -298,7 +361,7 @@ def run_ours(args):
 
     wl = workload(args, rank_seed(args.seed, rank))
     n_total = args.warmup + args.steps
-    nf = min(n_total, 100 if args.config == "street" else 40)
+    nf = min(n_total, 40 if args.config == "ring" else 100)
     t_r = time.time()
     frames = render_frames(wl, nf, f"cuda:{local}")
     render_s = time.time() - t_r
@@ -339,7 +402,8 @@ def run_ours(args):
     t1 = time.time()
     if world > 1:
         dist.barrier()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
+    step_ms = sorted(a.elapsed_time(b) for a, b in ev)
+    ms = sum(step_ms)
     sweep_ms, n_sw = sw.profile_read()
     tsdf_ms, n_ts = T.profile_read()
     st = T.status(stream)
@@ -420,6 +484,9 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(args, wl, nf, world),
+        "step_ms": {"median": statistics.median(step_ms), "p10": float(np.percentile(step_ms, 10)),
+                    "p90": float(np.percentile(step_ms, 90)), "mean": ms_per_step,
+                    "source": "CUDA events around each step on the launching stream (rank 0)"},
         "sweep": {"value": pix_planes / (depth_ms * 1e-3) / 1e9, "unit": "Gpix·planes/s",
                   "kernel_only": pix_planes / (k_ms * 1e-3) / 1e9,
                   "gpix_plane_cam_per_s": units / (k_ms * 1e-3) / 1e9,
@@ -442,8 +509,9 @@ def run_ours(args):
         "clocks": clk,
         "render_s": render_s,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.config == "street":
-        line["cpu_baseline"] = cpu_baseline(wl, frames)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.config in ("street", "tiny"):
+        import scenes
+        line["cpu_baseline"] = cpu_baseline(wl, frames, scenes.tiny(args.seed) if args.config == "street" else None)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
