@@ -66,6 +66,10 @@ def parse():
                          "whole 1000-frame ring at 2 cm")
     ap.add_argument("--batch-size", type=int, default=64, help="sweeps per batch (--config batch)")
     ap.add_argument("--half", action="store_true", help="FP16 storage of the matching images")
+    ap.add_argument("--shard", action="store_true",
+                    help="N > 1: one sequence split over the ranks (each rank sweeps a plane range of every frame, "
+                         "one all-gather of the per-pixel records, every rank merges; the TSDF as hash parts), "
+                         "strong scaling, instead of independent sequences")
     return ap.parse_args()
 
 
@@ -862,10 +866,85 @@ def run_ringloop(args):
     return 0
 
 
+def run_sharded(args):
+    """One street sequence split over the ranks (strong scaling): each rank
+    sweeps its plane range of every level of each frame, the ranks
+    all-gather the per-pixel records (NCCL, plain device buffers), every
+    rank merges them into the frame's depth map and fuses it into its hash
+    part of the map.  Timed like the default line: CUDA events on the
+    launching stream, max over ranks."""
+    import torch
+    import torch.distributed as dist
+
+    import scenes
+    import paper_1809_06132_gb300 as P
+    from paper_1809_06132_gb300.shard import ShardedFrame
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = workload(args, args.seed)                   # the same sequence on every rank
+    n_total = args.warmup + args.steps
+    nf = min(n_total, 100)
+    frames = render_frames(wl, nf, f"cuda:{local}")
+    imgs_dev = [[torch.from_numpy(i).to(dev) for i in imgs] for imgs, _ in frames]
+    H, W = wl.rig.ref.height, wl.rig.ref.width
+    sw = P.Sweep(wl.rig, wl.levels, image_half=args.half)
+    T = P.Tsdf(wl.tsdf, wl.rig.ref)
+    depth = torch.empty((H, W), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    frame = ShardedFrame(sw, T) if world > 1 else None
+
+    def step(i):
+        f = i % nf
+        if frame is not None:
+            frame.step(imgs_dev[f], boxes=wl.boxes[f], world_to_ref=wl.world_to_ref[f],
+                       local_center=wl.local_center(f), out=depth)
+        else:
+            sw.depth(imgs_dev[f], boxes=wl.boxes[f], out=depth)
+            T.integrate(depth, wl.world_to_ref[f], wl.local_center(f))
+
+    for i in range(args.warmup):
+        step(i)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for k in range(args.steps):
+        step(args.warmup + k)
+    b.record()
+    torch.cuda.synchronize()
+    t1 = time.time()
+    ms = max_over_ranks([a.elapsed_time(b)], dev)[0]
+    clocks.stop()
+    st = T.sync_status()
+    line = {"metric": METRIC, "value": args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload_config(args, wl, nf, world),
+                           parallelism=f"plane ranges x{world} + record all-gather; TSDF hash parts x{world}",
+                           l2="not flushed (the exchange is part of the step)"),
+            "tsdf_status": st, "gpu_launches": args.steps * (2 + 1 + 2 + 4), "clocks": clocks.summary(t0, t1)}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.shard:
+        return run_sharded(args)
     if args.config == "batch":
         return run_batch(args)
     if args.config == "diff":

@@ -176,6 +176,49 @@ int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_box* boxes,
 
 void psweep_destroy(psweep_t* h);
 
+/* Copy the handle's own level outputs (depth, best and second-best cost,
+ * plane index per level pixel, as the last psweep_depth call without
+ * level_out or the last batch run over this handle left them) into the
+ * caller's buffers (level_out: host array of n_levels entries; NULL members
+ * are skipped).  Asynchronous on `stream`; allocates nothing. */
+int psweep_level_outputs(psweep_t* h, const ps_level_out* level_out, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Plane-sharded sweep.  The plane hypotheses of a level are independent
+ * until the winner-take-all (Sec. III-A: every plane's warped images and
+ * costs stand alone; the depth is the plane of least cost), so one frame's
+ * sweep splits into consecutive plane ranges swept on different GPUs, each
+ * reducing its range to a per-pixel record; one exchange of the records
+ * (an all-gather of 7 floats per pixel per level) and psweep_merge_records
+ * on every GPU give exactly psweep_depth's outputs.  The paper pipelines
+ * the stages of its system over three computers (Sec. IV-A); this is the
+ * data-parallel split of the sweep stage itself.
+ *
+ * Sweep planes [plane_lo[l], plane_hi[l]) of each level l (host int32
+ * arrays of n_levels entries; an empty range is allowed) and write each
+ * pixel's record of that range:
+ *   records  host array of n_levels device pointers, each 7 x H_l x W_l
+ *            float32 planes: best cost, second best, the best plane's
+ *            neighbour costs inside the range (+inf at its ends), the
+ *            range's first and last plane cost, the best plane's index as
+ *            int32 bits (-1 = none).
+ * Asynchronous on `stream`; allocates nothing. */
+#define PS_MAX_PARTS 16
+int psweep_depth_planes(psweep_t* h, const uint8_t* const* images, const int32_t* plane_lo,
+                        const int32_t* plane_hi, float* const* records, void* stream);
+
+/* Merge the records of n_parts consecutive plane ranges (part p of level l
+ * starts at plane part_lo[p * n_levels + l]; part 0 at plane 0, the last
+ * part ends at the level's plane count; starts never fall) into each
+ * level's winner-take-all with the sub-plane fit, then merge the levels,
+ * filter and mask exactly as psweep_depth does.  records: host array of
+ * n_parts * n_levels device pointers in the same order (NULL allowed for
+ * empty parts).  The outputs are bit-identical to psweep_depth on the same
+ * images.  Asynchronous on `stream`; allocates nothing. */
+int psweep_merge_records(psweep_t* h, int32_t n_parts, const int32_t* part_lo, const float* const* records,
+                         const ps_box* boxes, int32_t n_boxes, float* depth_out, const ps_level_out* level_out,
+                         void* stream);
+
 /* TSDF volume (Sec. III-C).  Voxels hold {D, w}: D in [-1, 1] is the
  * truncated signed distance normalised by mu (positive in front of
  * surfaces), w the number of fused observations capped at w_max.
@@ -233,6 +276,17 @@ int tsdf_extract(tsdf_t* t, float min_weight, int32_t* keys, float* D, float* W,
 
 /* Synchronises `stream`, returns and clears the latched device status. */
 int tsdf_status(tsdf_t* t, void* stream);
+
+/* Ownership of the map by hash partition, for fusing one sequence on
+ * n_parts GPUs (Sec. III-C: every voxel block is updated only from the
+ * depth map and its own state, so disjoint block sets fuse independently):
+ * from the next tsdf_integrate on, this map allocates only the blocks whose
+ * key hashes to `part` (high half of a 64-bit mix of the key, modulo
+ * n_parts); every GPU fuses the same broadcast depth map into its own
+ * part, and the union of the parts equals the map one GPU would build,
+ * voxel for voxel.  n_parts = 1 restores the whole map.  Hashed maps only
+ * (a dense grid gets PS_ERR_ARG).  Blocks already allocated stay. */
+int tsdf_set_partition(tsdf_t* t, int32_t n_parts, int32_t part);
 
 /* Surface points of the map (Sec. III-C; the paper evaluates the map as a
  * point set): for every voxel a and its +x, +y and +z neighbour b (in the

@@ -391,6 +391,8 @@ void fill_level(const psweep_t* h, int l, int th, int chunk, LevelD& D) {
     D.tiles_x = (D.W + TW - 1) / TW;
     D.tiles_y = (D.H + th - 1) / th;
     D.n_tiles = D.tiles_x * D.tiles_y;
+    D.k_begin = 0;
+    D.k_end = D.n_planes;
     D.chunk = chunk;
     D.n_chunks = (D.n_planes + D.chunk - 1) / D.chunk;
     D.n_items = D.n_tiles * D.n_chunks;
@@ -639,17 +641,16 @@ extern "C" int psweep_create(const ps_sweep_desc* d, psweep_t** out) {
 
 extern "C" void psweep_destroy(psweep_t* h) { free_sweep(h); }
 
-extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_box* boxes, int32_t n_boxes,
-                            float* depth_out, const ps_level_out* level_out, void* stream) {
-    clear_error();
-    PS_ARG(h != nullptr, "psweep_depth: handle is NULL");
-    PS_ARG(images != nullptr, "psweep_depth: images is NULL");
-    for (int i = 0; i <= h->n_cams; ++i) PS_ARG(images[i] != nullptr, "psweep_depth: images[%d] is NULL", i);
-    PS_ARG(depth_out != nullptr, "psweep_depth: depth_out is NULL");
-    PS_ARG(n_boxes >= 0 && n_boxes <= h->boxes_cap, "psweep_depth: n_boxes must be in 0..%d", h->boxes_cap);
-    PS_ARG(n_boxes == 0 || boxes != nullptr, "psweep_depth: boxes is NULL");
-    cudaStream_t s = (cudaStream_t)stream;
+namespace {
 
+// The launches of one sweep up to the level outputs: one prep launch (level
+// images, reference statistics, quads, counters) and the persistent sweep
+// kernel.  With ranges (plane_lo/plane_hi per level, NULL = every plane)
+// and records (per level, NULL = the level outputs) the sweep covers only
+// those planes and writes per-pixel records.  by_level receives each
+// level's record in the handle's level order.
+int launch_sweep(psweep_t* h, const uint8_t* const* images, const int32_t* plane_lo, const int32_t* plane_hi,
+                 float* const* records, const ps_level_out* level_out, cudaStream_t s, LevelD* by_level) {
     SweepParams P;
     std::memset(&P, 0, sizeof(P));
     P.n_levels = h->n_levels;
@@ -709,6 +710,16 @@ extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_
         prep_blocks += R.rs_blocks + R.q_blocks;
         LevelD& D = P.lv[oi];
         fill_level(h, l, TH_SINGLE, h->chunk[l], D);
+        if (plane_lo) {
+            // planes [lo, hi) only, in chunks of at most the handle's chunk (so the
+            // chunk scratch sized for the whole level holds them)
+            D.k_begin = plane_lo[l];
+            D.k_end = plane_hi[l];
+            D.chunk = balanced_chunk(std::max(1, D.k_end - D.k_begin), PLANE_CHUNK);
+            D.n_chunks = std::max(1, (D.k_end - D.k_begin + D.chunk - 1) / D.chunk);
+            D.n_items = D.n_tiles * D.n_chunks;
+        }
+        if (records) D.records = records[l];
         D.partial = h->partial[l];
         D.done = h->done[l];
         R.done = D.done;  // zeroed by the prep launch
@@ -735,13 +746,16 @@ extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_
     sweep_kernel<<<std::min(tiles, h->grid), NT, smem, s>>>(P, h->tile_counter);
     PS_CUDA(cudaGetLastError());
     h->prof.mark(2, s);
+    for (int oi = 0; oi < h->n_levels; ++oi) by_level[order[oi]] = P.lv[oi];
+    return PS_OK;
+}
 
+// The level merge, the filters and the boxes into depth_out (level records
+// in the handle's level order).
+int merge_levels(psweep_t* h, const LevelD* by_level, const ps_box* boxes, int32_t n_boxes, float* depth_out,
+                 cudaStream_t s) {
     MergeP M;
-    {
-        LevelD by_level[PS_MAX_LEVELS];
-        for (int oi = 0; oi < h->n_levels; ++oi) by_level[order[oi]] = P.lv[oi];
-        fill_merge(h, by_level, M);
-    }
+    fill_merge(h, by_level, M);
     const ps_filter& F = h->filter;
     M.n_boxes = n_boxes;
     for (int b = 0; b < n_boxes && b < 16; ++b) M.boxes[b] = boxes[b];
@@ -760,6 +774,136 @@ extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_
         merge_kernel<<<dim3((M.W + 127) / 128, M.H), 128, 0, s>>>(M, h->boxes_dev, depth_out);
     }
     PS_CUDA(cudaGetLastError());
+    return PS_OK;
+}
+
+int check_frame_args(psweep_t* h, const uint8_t* const* images, const char* fn) {
+    PS_ARG(h != nullptr, "%s: handle is NULL", fn);
+    PS_ARG(images != nullptr, "%s: images is NULL", fn);
+    for (int i = 0; i <= h->n_cams; ++i) PS_ARG(images[i] != nullptr, "%s: images[%d] is NULL", fn, i);
+    return PS_OK;
+}
+
+}  // namespace
+
+extern "C" int psweep_depth(psweep_t* h, const uint8_t* const* images, const ps_box* boxes, int32_t n_boxes,
+                            float* depth_out, const ps_level_out* level_out, void* stream) {
+    clear_error();
+    int st = check_frame_args(h, images, "psweep_depth");
+    if (st) return st;
+    PS_ARG(depth_out != nullptr, "psweep_depth: depth_out is NULL");
+    PS_ARG(n_boxes >= 0 && n_boxes <= h->boxes_cap, "psweep_depth: n_boxes must be in 0..%d", h->boxes_cap);
+    PS_ARG(n_boxes == 0 || boxes != nullptr, "psweep_depth: boxes is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    LevelD by_level[PS_MAX_LEVELS];
+    st = launch_sweep(h, images, nullptr, nullptr, nullptr, level_out, s, by_level);
+    if (st) return st;
+    st = merge_levels(h, by_level, boxes, n_boxes, depth_out, s);
+    if (st) return st;
+    h->prof.mark(3, s);
+    h->prof.end_call();
+    return PS_OK;
+}
+
+extern "C" int psweep_level_outputs(psweep_t* h, const ps_level_out* level_out, void* stream) {
+    clear_error();
+    PS_ARG(h != nullptr && level_out != nullptr, "psweep_level_outputs: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int l = 0; l < h->n_levels; ++l) {
+        const size_t n = (size_t)h->lW[l] * h->lH[l];
+        const ps_level_out& o = level_out[l];
+        if (o.depth) PS_CUDA(cudaMemcpyAsync(o.depth, h->out_depth[l], 4 * n, cudaMemcpyDeviceToDevice, s));
+        if (o.best_cost) PS_CUDA(cudaMemcpyAsync(o.best_cost, h->out_c1[l], 4 * n, cudaMemcpyDeviceToDevice, s));
+        if (o.second_cost) PS_CUDA(cudaMemcpyAsync(o.second_cost, h->out_c2[l], 4 * n, cudaMemcpyDeviceToDevice, s));
+        if (o.plane_idx) PS_CUDA(cudaMemcpyAsync(o.plane_idx, h->out_k[l], 4 * n, cudaMemcpyDeviceToDevice, s));
+    }
+    return PS_OK;
+}
+
+extern "C" int psweep_depth_planes(psweep_t* h, const uint8_t* const* images, const int32_t* plane_lo,
+                                   const int32_t* plane_hi, float* const* records, void* stream) {
+    clear_error();
+    int st = check_frame_args(h, images, "psweep_depth_planes");
+    if (st) return st;
+    PS_ARG(plane_lo && plane_hi && records, "psweep_depth_planes: NULL argument");
+    for (int l = 0; l < h->n_levels; ++l) {
+        PS_ARG(0 <= plane_lo[l] && plane_lo[l] <= plane_hi[l] && plane_hi[l] <= h->n_planes[l],
+               "psweep_depth_planes: level %d: need 0 <= plane_lo <= plane_hi <= %d", l, h->n_planes[l]);
+        PS_ARG(records[l] != nullptr, "psweep_depth_planes: records[%d] is NULL", l);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    LevelD by_level[PS_MAX_LEVELS];
+    st = launch_sweep(h, images, plane_lo, plane_hi, records, nullptr, s, by_level);
+    if (st) return st;
+    h->prof.mark(3, s);
+    h->prof.end_call();
+    return PS_OK;
+}
+
+namespace ps {
+namespace {
+
+struct RecordMergeP {
+    LevelD L;
+    int n_parts;
+    const float* rec[PS_MAX_PARTS];
+    int lo[PS_MAX_PARTS];
+};
+
+__global__ void merge_records_kernel(const __grid_constant__ RecordMergeP P) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= P.L.W || y >= P.L.H) return;
+    merge_record_px(P.L, P.rec, P.lo, P.n_parts, x, y);
+}
+
+}  // namespace
+}  // namespace ps
+
+extern "C" int psweep_merge_records(psweep_t* h, int32_t n_parts, const int32_t* part_lo,
+                                    const float* const* records, const ps_box* boxes, int32_t n_boxes,
+                                    float* depth_out, const ps_level_out* level_out, void* stream) {
+    clear_error();
+    PS_ARG(h != nullptr, "psweep_merge_records: handle is NULL");
+    PS_ARG(n_parts >= 1 && n_parts <= PS_MAX_PARTS, "psweep_merge_records: n_parts must be in 1..%d", PS_MAX_PARTS);
+    PS_ARG(part_lo && records && depth_out, "psweep_merge_records: NULL argument");
+    PS_ARG(n_boxes >= 0 && n_boxes <= h->boxes_cap, "psweep_merge_records: n_boxes must be in 0..%d", h->boxes_cap);
+    PS_ARG(n_boxes == 0 || boxes != nullptr, "psweep_merge_records: boxes is NULL");
+    const int NL = h->n_levels;
+    for (int l = 0; l < NL; ++l) {
+        PS_ARG(part_lo[l] == 0, "psweep_merge_records: level %d: the first part must start at plane 0", l);
+        for (int p = 0; p < n_parts; ++p) {
+            const int lo = part_lo[p * NL + l], hi = p + 1 < n_parts ? part_lo[(p + 1) * NL + l] : h->n_planes[l];
+            PS_ARG(lo <= hi && hi <= h->n_planes[l], "psweep_merge_records: level %d: part starts must rise to at most %d",
+                   l, h->n_planes[l]);
+            PS_ARG(hi == lo || records[p * NL + l] != nullptr, "psweep_merge_records: records of part %d level %d is NULL",
+                   p, l);
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    h->prof.mark(0, s);
+    h->prof.mark(1, s);
+    LevelD by_level[PS_MAX_LEVELS];
+    for (int l = 0; l < NL; ++l) {
+        RecordMergeP P;
+        std::memset(&P, 0, sizeof(P));
+        fill_level(h, l, TH_SINGLE, h->chunk[l], P.L);
+        const ps_level_out* lo = level_out ? &level_out[l] : nullptr;
+        if (lo && lo->depth) P.L.depth = lo->depth;
+        if (lo && lo->best_cost) P.L.c1 = lo->best_cost;
+        if (lo && lo->second_cost) P.L.c2 = lo->second_cost;
+        if (lo && lo->plane_idx) P.L.kstar = lo->plane_idx;
+        P.n_parts = n_parts;
+        for (int p = 0; p < n_parts; ++p) {
+            P.rec[p] = records[p * NL + l];
+            P.lo[p] = part_lo[p * NL + l];
+        }
+        merge_records_kernel<<<dim3((P.L.W + 127) / 128, P.L.H), 128, 0, s>>>(P);
+        PS_CUDA(cudaGetLastError());
+        by_level[l] = P.L;
+    }
+    h->prof.mark(2, s);
+    int st = merge_levels(h, by_level, boxes, n_boxes, depth_out, s);
+    if (st) return st;
     h->prof.mark(3, s);
     h->prof.end_call();
     return PS_OK;

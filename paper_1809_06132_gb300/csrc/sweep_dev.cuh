@@ -50,6 +50,7 @@ struct LevelD {
     int n_cams;
     CamJ cams[PS_MAX_CAMS];
     int tiles_x, tiles_y, n_tiles;
+    int k_begin, k_end;            // planes [k_begin, k_end) are swept (the whole level, or one part of it)
     int chunk, n_chunks, n_items;  // planes per work item, items per tile, tiles x items
     float* partial;                // [n_items][7][TH x TW] chunk results (when n_chunks > 1)
     int* done;                     // [n_tiles] finished chunks per tile (zeroed per launch)
@@ -59,7 +60,16 @@ struct LevelD {
     float* c1;
     float* c2;
     int32_t* kstar;
+    float* records;  // non-NULL: write each pixel's record of planes [k_begin, k_end) instead of its outputs
 };
+
+// Per-pixel record of a range of planes, as planes of H x W floats: the
+// range's best cost, its second best, the costs of the best plane's
+// neighbours inside the range (+inf at the range's ends), the costs of the
+// range's first and last plane, and the best plane's index (int bits; -1 =
+// none).  Records of consecutive ranges merge into the whole level's
+// winner-take-all (merge_record_px).
+enum { REC_C1, REC_C2, REC_CM, REC_CP, REC_FIRST, REC_LAST, REC_K, REC_N };
 
 struct SweepParams {
     int n_levels;
@@ -447,6 +457,61 @@ __device__ inline void finish_pixel(const LevelD& L, int gx, int gy, float c1, f
     if (L.kstar) L.kstar[o] = kb;
 }
 
+// Record of pixel (gx, gy) over the planes [k_begin, k_end) of this launch.
+__device__ __forceinline__ void write_record(const LevelD& L, int gx, int gy, float c1, float c2, float cm, float cp,
+                                             float first, float last, int kb) {
+    const size_t n = (size_t)L.W * L.H, o = (size_t)gy * L.W + gx;
+    L.records[REC_C1 * n + o] = c1;
+    L.records[REC_C2 * n + o] = c2;
+    L.records[REC_CM * n + o] = cm;
+    L.records[REC_CP * n + o] = cp;
+    L.records[REC_FIRST * n + o] = first;
+    L.records[REC_LAST * n + o] = last;
+    L.records[REC_K * n + o] = __int_as_float(kb);
+}
+
+// Winner-take-all of one pixel from the records of n_parts consecutive
+// plane ranges (part p covers [lo[p], lo[p + 1]), the last one up to
+// n_planes), then its outputs as finish_pixel writes them.  The same rule as
+// the tile's merge of its plane chunks: the first part holding the lowest
+// cost wins (ties keep the lowest plane), the second best is the minimum of
+// the winner's second best and every other part's best, and a neighbour
+// cost outside the winner's range comes from the adjacent part's first or
+// last plane.
+__device__ inline void merge_record_px(const LevelD& L, const float* const* rec, const int* lo, int n_parts, int gx,
+                                       int gy) {
+    const float inf = __int_as_float(0x7f800000);
+    const size_t n = (size_t)L.W * L.H, o = (size_t)gy * L.W + gx;
+    int wc = -1;
+    float b1 = inf;
+    for (int p = 0; p < n_parts; ++p) {
+        const int hi = p + 1 < n_parts ? lo[p + 1] : L.n_planes;
+        if (hi <= lo[p]) continue;  // empty part
+        const float v = rec[p][REC_C1 * n + o];
+        if (v < b1) {
+            b1 = v;
+            wc = p;
+        }
+    }
+    float b2 = inf, cm = inf, cp = inf;
+    int k = -1;
+    if (wc >= 0) {
+        b2 = rec[wc][REC_C2 * n + o];
+        for (int p = 0; p < n_parts; ++p) {
+            const int hi = p + 1 < n_parts ? lo[p + 1] : L.n_planes;
+            if (p != wc && hi > lo[p]) b2 = fminf(b2, rec[p][REC_C1 * n + o]);
+        }
+        k = __float_as_int(rec[wc][REC_K * n + o]);
+        const int whi = wc + 1 < n_parts ? lo[wc + 1] : L.n_planes;
+        int prev = wc - 1, next = wc + 1;
+        while (prev >= 0 && (prev + 1 < n_parts ? lo[prev + 1] : L.n_planes) <= lo[prev]) --prev;
+        while (next < n_parts && (next + 1 < n_parts ? lo[next + 1] : L.n_planes) <= lo[next]) ++next;
+        cm = k > lo[wc] ? rec[wc][REC_CM * n + o] : (prev >= 0 ? rec[prev][REC_LAST * n + o] : inf);
+        cp = k < whi - 1 ? rec[wc][REC_CP * n + o] : (next < n_parts ? rec[next][REC_FIRST * n + o] : inf);
+    }
+    finish_pixel(L, gx, gy, b1, b2, k, cm, cp);
+}
+
 // End of a work item.  When the item completed its tile and the level counts
 // finished tiles (batched launch), the tile's outputs are made visible to the
 // whole GPU before the count moves.  `finished` is uniform over the CTA.
@@ -466,7 +531,7 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
     constexpr int SEG = G::SEG;
     if (!PS_DCHECK(item >= 0 && item < L.n_items, CHK_ITEM)) return;  // uniform over the CTA
     const int tile = item / L.n_chunks, chunk = item - tile * L.n_chunks;
-    const int k_lo = chunk * L.chunk, k_hi = min(L.n_planes, k_lo + L.chunk);
+    const int k_lo = L.k_begin + chunk * L.chunk, k_hi = min(L.k_end, k_lo + L.chunk);
     constexpr int HH = G::HH, HWL = G::HWL, WS = G::WS, HS = G::HS, NPOS = G::NPOS, N = G::N;
     float4* Hs = reinterpret_cast<float4*>(smem_raw);            // [KP][HH][HS] window sums
     float* Ws = reinterpret_cast<float*>(Hs + KP * HH * HS);      // warped samples (NaN = invalid): KP = 1 [HH][WS],
@@ -671,7 +736,12 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
 #pragma unroll
         for (int i = 0; i < SEG; ++i) {
             int gx = tx * TW + ox, gy = ty * TH + oy0 + i;
-            if (gx < L.W && gy < L.H) finish_pixel(L, gx, gy, c1[i], c2[i], kb[i], cminus[i], cplus[i]);
+            if (gx < L.W && gy < L.H) {
+                if (L.records)
+                    write_record(L, gx, gy, c1[i], c2[i], cminus[i], cplus[i], cfirst[i], cprev[i], kb[i]);
+                else
+                    finish_pixel(L, gx, gy, c1[i], c2[i], kb[i], cminus[i], cplus[i]);
+            }
         }
         tile_finished(L, true);
         return;
@@ -724,14 +794,22 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
                 for (int c = 0; c < L.n_chunks; ++c)
                     if (c != wc) b2 = fminf(b2, __ldcg(base + ((size_t)c * 7 + 0) * (TH * TW) + px));
                 k = __float_as_int(__ldcg(P + 6 * (TH * TW)));
-                const int lo = wc * L.chunk, hi = min(L.n_planes, lo + L.chunk);
+                const int lo = L.k_begin + wc * L.chunk, hi = min(L.k_end, lo + L.chunk);
                 cm = k > lo ? __ldcg(P + 2 * (TH * TW))
                             : (wc > 0 ? __ldcg(base + ((size_t)(wc - 1) * 7 + 5) * (TH * TW) + px) : inf);
                 cp = k < hi - 1 ? __ldcg(P + 3 * (TH * TW))
                                 : (wc + 1 < L.n_chunks ? __ldcg(base + ((size_t)(wc + 1) * 7 + 4) * (TH * TW) + px)
                                                        : inf);
             }
-            if (gx < L.W && gy < L.H) finish_pixel(L, gx, gy, b1, b2, k, cm, cp);
+            if (gx < L.W && gy < L.H) {
+                if (L.records) {
+                    const float first = __ldcg(base + 4 * (TH * TW) + px);
+                    const float last = __ldcg(base + ((size_t)(L.n_chunks - 1) * 7 + 5) * (TH * TW) + px);
+                    write_record(L, gx, gy, b1, b2, cm, cp, first, last, k);
+                } else {
+                    finish_pixel(L, gx, gy, b1, b2, k, cm, cp);
+                }
+            }
         }
     }
     tile_finished(L, *s_flag != 0);

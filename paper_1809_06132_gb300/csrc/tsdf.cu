@@ -44,6 +44,8 @@ __host__ __device__ __forceinline__ unsigned long long pack_key(int x, int y, in
            (((unsigned long long)(z + (1 << 20)) & 0x1FFFFF) << 42);
 }
 
+// The 64-bit finalising mix of MurmurHash3 (fmix64): two multiplications
+// and three xor-shifts that spread every key bit over the whole word.
 __device__ __forceinline__ unsigned long long hash64(unsigned long long k) {
     k ^= k >> 33;
     k *= 0xff51afd7ed558ccdull;
@@ -87,7 +89,14 @@ struct TsdfDev {
     unsigned* status;
     unsigned* dmax_bits;
     const float4* rays;  // depth camera rays (camera frame), NaN = none
+    int n_parts, part;   // hash partition: allocate only blocks with owner(key) == part
 };
+
+// Owner of a block among n_parts maps: the high half of the key's hash (the
+// slot index uses the low bits, so each part still spreads over the table).
+__device__ __forceinline__ int block_owner(int bx, int by, int bz, int n_parts) {
+    return (int)((hash64(pack_key(bx, by, bz)) >> 32) % (unsigned long long)n_parts);
+}
 
 // ----------------------------------------------------------------- hash
 
@@ -215,6 +224,7 @@ __global__ void alloc_kernel(const __grid_constant__ FrameP F, TsdfDev T, const 
                         fabsf(c2 - F.lc[2]) > F.lh[2])
                         continue;
                 }
+                if (T.n_parts > 1 && block_owner(bx, by, bz, T.n_parts) != T.part) continue;
                 hash_insert(T, bx, by, bz);
             }
 }
@@ -311,20 +321,48 @@ __device__ __forceinline__ void update_voxel(const FrameP& F, const float* depth
 
 __global__ void __launch_bounds__(IT) integrate_kernel(const __grid_constant__ FrameP F, TsdfDev T,
                                                        const float* depth) {
-    int nv = *T.n_vis;
-    for (int e = blockIdx.x; e < nv; e += gridDim.x) {
-        int bi = T.vis[e];
-        if (!PS_DCHECK(bi >= 0 && bi < T.pool_cap, CHK_POOL)) continue;  // uniform over the CTA
-        int4 k = T.pool_keys[bi];
-        float4* blk = reinterpret_cast<float4*>(T.vox + (size_t)bi * B3);
-        float4 pr = blk[threadIdx.x];
-        int v0 = 2 * threadIdx.x;  // voxels v0, v0 + 1: same y, z; x and x + 1
-        int x = v0 & 7, y = (v0 >> 3) & 7, z = v0 >> 6;
-        int ax = k.x * B + x - F.ic[0], ay = k.y * B + y - F.ic[1], az = k.z * B + z - F.ic[2];
-        float2 a = make_float2(pr.x, pr.y), b = make_float2(pr.z, pr.w);
-        update_voxel(F, depth, ax, ay, az, a);
-        update_voxel(F, depth, ax + 1, ay, az, b);
-        blk[threadIdx.x] = make_float4(a.x, a.y, b.x, b.y);
+    // The list entry, key and voxels of the CTA's next block are loaded while
+    // the current block is updated, so the dependent loads (list -> slot ->
+    // key and voxels) of one block overlap the arithmetic of the previous one.
+    const int nv = *T.n_vis;
+    int e = blockIdx.x;
+    if (e >= nv) return;
+    int bi = T.vis[e];
+    int4 k = make_int4(0, 0, 0, 0);
+    float4 pr = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool ok = PS_DCHECK(bi >= 0 && bi < T.pool_cap, CHK_POOL);  // uniform over the CTA
+    if (ok) {
+        k = T.pool_keys[bi];
+        pr = reinterpret_cast<const float4*>(T.vox + (size_t)bi * B3)[threadIdx.x];
+    }
+    const int v0 = 2 * threadIdx.x;  // voxels v0, v0 + 1: same y, z; x and x + 1
+    const int x = v0 & 7, y = (v0 >> 3) & 7, z = v0 >> 6;
+    for (; e < nv; e += gridDim.x) {
+        // prefetch the next block of this CTA
+        const int en = e + gridDim.x;
+        int bn = -1;
+        int4 kn = make_int4(0, 0, 0, 0);
+        float4 pn = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool okn = false;
+        if (en < nv) {
+            bn = T.vis[en];
+            okn = PS_DCHECK(bn >= 0 && bn < T.pool_cap, CHK_POOL);
+            if (okn) {
+                kn = T.pool_keys[bn];
+                pn = reinterpret_cast<const float4*>(T.vox + (size_t)bn * B3)[threadIdx.x];
+            }
+        }
+        if (ok) {
+            const int ax = k.x * B + x - F.ic[0], ay = k.y * B + y - F.ic[1], az = k.z * B + z - F.ic[2];
+            float2 a = make_float2(pr.x, pr.y), b = make_float2(pr.z, pr.w);
+            update_voxel(F, depth, ax, ay, az, a);
+            update_voxel(F, depth, ax + 1, ay, az, b);
+            reinterpret_cast<float4*>(T.vox + (size_t)bi * B3)[threadIdx.x] = make_float4(a.x, a.y, b.x, b.y);
+        }
+        bi = bn;
+        k = kn;
+        pr = pn;
+        ok = okn;
     }
 }
 
@@ -898,6 +936,16 @@ extern "C" int tsdf_load(tsdf_t* t, const int32_t* keys, const float* D, const f
 namespace ps {
 int tsdf_sync_status(tsdf_t* t, cudaStream_t s) { return read_status(t, s); }
 }  // namespace ps
+
+extern "C" int tsdf_set_partition(tsdf_t* t, int32_t n_parts, int32_t part) {
+    clear_error();
+    PS_ARG(t != nullptr, "tsdf_set_partition: NULL handle");
+    PS_ARG(!t->dense, "tsdf_set_partition: a dense grid has no block allocation to partition");
+    PS_ARG(n_parts >= 1 && part >= 0 && part < n_parts, "tsdf_set_partition: need 0 <= part < n_parts");
+    t->T.n_parts = n_parts;
+    t->T.part = part;
+    return PS_OK;
+}
 
 extern "C" int tsdf_status(tsdf_t* t, void* stream) {
     clear_error();

@@ -31,7 +31,10 @@ EXPORTS = ["psweep_create", "psweep_depth", "psweep_destroy", "tsdf_create", "ts
            "psbatch_queue_stats", "psbatch_destroy", "psbatch_autotune", "ps_pipe_create", "ps_pipe_push",
            "ps_pipe_flush", "ps_pipe_destroy", "psdiff_create", "psdiff_forward", "psdiff_backward",
            "psdiff_destroy", "tsdf_dense_fuse_backward",
-           "ps_check_read", "ps_last_error", "ps_version", "ps_sync_status"]
+           "ps_check_read", "ps_last_error", "ps_version", "ps_sync_status", "psweep_depth_planes",
+           "psweep_merge_records", "tsdf_set_partition", "psweep_level_outputs"]
+MAX_PARTS = 16
+N_RECORD = 7  # floats per pixel in a plane-range record
 
 
 class PsError(RuntimeError):
@@ -165,6 +168,10 @@ def load(build_if_missing: bool = True):
                                            C.POINTER(ps_pose), P, P, P, P, P]
     L.ps_check_read.argtypes = [C.POINTER(C.c_uint32)]
     L.ps_sync_status.argtypes = [P, P]
+    L.psweep_depth_planes.argtypes = [P, P, P, P, P, P]
+    L.psweep_merge_records.argtypes = [P, C.c_int32, P, P, P, C.c_int32, P, P, P]
+    L.tsdf_set_partition.argtypes = [P, C.c_int32, C.c_int32]
+    L.psweep_level_outputs.argtypes = [P, P, P]
     L.ps_last_error.restype = C.c_char_p
     L.ps_version.restype = C.c_char_p
     _lib = L
@@ -317,6 +324,77 @@ class Sweep:
                     _dev(o["c2"], torch.float32, "c2") if o.get("c2") is not None else None,
                     _dev(o["kstar"], torch.int32, "kstar") if o.get("kstar") is not None else None)
         _check(load().psweep_depth(self.h, ptrs, bx, nb, _dev(out, torch.float32, "out"), lo, _stream_ptr(stream)))
+        return out
+
+    def level_outputs(self, outs=None, stream=None):
+        """The handle's own level outputs (left by the last psweep_depth without
+        level_outs or by the last batch run over this handle), copied out."""
+        if outs is None:
+            outs = self.alloc_level_outputs()
+        lo = (ps_level_out * len(self.levels))()
+        for i, o in enumerate(outs):
+            lo[i] = ps_level_out(_dev(o["depth"], torch.float32, "depth"), _dev(o["c1"], torch.float32, "c1"),
+                                 _dev(o["c2"], torch.float32, "c2"), _dev(o["kstar"], torch.int32, "kstar"))
+        _check(load().psweep_level_outputs(self.h, lo, _stream_ptr(stream)))
+        return outs
+
+    def alloc_records(self, device="cuda"):
+        """Per level, a (7, H_l, W_l) float32 buffer for a plane-range record."""
+        return [torch.empty((N_RECORD, h, w), dtype=torch.float32, device=device) for (h, w) in self.level_shapes()]
+
+    def n_planes(self):
+        return [lv.n_planes for lv in self.levels]
+
+    def depth_planes(self, images: Sequence[torch.Tensor], plane_lo, plane_hi, records=None, stream=None):
+        """Sweep planes [plane_lo[l], plane_hi[l]) of each level; per level a
+        (7, H_l, W_l) record of that range (psweep_depth_planes)."""
+        n = 1 + len(self.rig.cams)
+        if len(images) != n:
+            raise ValueError(f"expected {n} images")
+        nl = len(self.levels)
+        if len(plane_lo) != nl or len(plane_hi) != nl:
+            raise ValueError(f"plane_lo / plane_hi need {nl} entries")
+        if records is None:
+            records = self.alloc_records(images[0].device)
+        for r, (h, w) in zip(records, self.level_shapes()):
+            if tuple(r.shape) != (N_RECORD, h, w):
+                raise ValueError(f"a record buffer must be ({N_RECORD}, {h}, {w})")
+        ptrs = (C.c_void_p * n)(*[_dev(im, torch.uint8, f"images[{i}]") for i, im in enumerate(images)])
+        lo = (C.c_int32 * nl)(*[int(v) for v in plane_lo])
+        hi = (C.c_int32 * nl)(*[int(v) for v in plane_hi])
+        rp = (C.c_void_p * nl)(*[_dev(r, torch.float32, "records") for r in records])
+        _check(load().psweep_depth_planes(self.h, ptrs, lo, hi, rp, _stream_ptr(stream)))
+        return records
+
+    def merge_records(self, part_lo, records, boxes=None, out: Optional[torch.Tensor] = None, level_outs=None,
+                      stream=None, device=None) -> torch.Tensor:
+        """psweep_merge_records: part_lo[p][l] = first plane of part p at level l
+        (part 0 at 0); records[p][l] = that part's (7, H_l, W_l) record."""
+        nl = len(self.levels)
+        n_parts = len(part_lo)
+        if not 1 <= n_parts <= MAX_PARTS or len(records) != n_parts:
+            raise ValueError(f"need 1..{MAX_PARTS} parts with one record list each")
+        for r, (h, w) in zip(records[0], self.level_shapes()):
+            if tuple(r.shape) != (N_RECORD, h, w):
+                raise ValueError(f"a record buffer must be ({N_RECORD}, {h}, {w})")
+        lo = (C.c_int32 * (n_parts * nl))(*[int(part_lo[p][l]) for p in range(n_parts) for l in range(nl)])
+        rp = (C.c_void_p * (n_parts * nl))(*[_dev(records[p][l], torch.float32, "records")
+                                             for p in range(n_parts) for l in range(nl)])
+        if out is None:
+            out = torch.empty((self.rig.ref.height, self.rig.ref.width), dtype=torch.float32,
+                              device=device or records[0][0].device)
+        bx, nb = boxes_array(boxes)
+        lvo = None
+        if level_outs is not None:
+            lvo = (ps_level_out * nl)()
+            for i, o in enumerate(level_outs):
+                lvo[i] = ps_level_out(
+                    _dev(o["depth"], torch.float32, "depth") if o.get("depth") is not None else None,
+                    _dev(o["c1"], torch.float32, "c1") if o.get("c1") is not None else None,
+                    _dev(o["c2"], torch.float32, "c2") if o.get("c2") is not None else None,
+                    _dev(o["kstar"], torch.int32, "kstar") if o.get("kstar") is not None else None)
+        _check(load().psweep_merge_records(self.h, n_parts, lo, rp, bx, nb, _dev(out, torch.float32, "out"), lvo,
+                                           _stream_ptr(stream)))
         return out
 
     def frame_host(self, host_images: Sequence[np.ndarray], boxes=None, tsdf: "Tsdf" = None, world_to_ref=None,
@@ -531,6 +609,10 @@ class Tsdf:
     def sync_status(self, stream=None) -> int:
         """ps_sync_status on this handle (same outcome as status())."""
         return load().ps_sync_status(self.h, _stream_ptr(stream))
+
+    def set_partition(self, n_parts: int, part: int):
+        """Allocate only the blocks whose key hashes to `part` of n_parts (tsdf_set_partition)."""
+        _check(load().tsdf_set_partition(self.h, int(n_parts), int(part)))
 
     def swap_out(self, local_center, capacity: int = None, device="cuda", stream=None):
         """Move the blocks outside the local map out of the map: (keys, D, W) CUDA tensors."""

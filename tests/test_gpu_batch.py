@@ -177,3 +177,52 @@ def test_same_results_with_duplicate_rig_shapes():
     outs = P.Batch([a, c]).run([dev, dev])
     torch.cuda.synchronize()
     assert torch.equal(outs[0], ref) and torch.equal(outs[1], ref)
+
+
+@pytest.fixture(scope="module")
+def oracle_mix():
+    """Five uneven sweeps for the oracle comparison: drawn sizes, plane
+    counts and 1-3 matching cameras, plus one with 4 matching cameras."""
+    wls = scenes.batch_mix(5, n=12, sizes=((256, 200), (320, 256), (640, 512)), planes=(32, 64, 128))
+    four = next(w for w in scenes.batch_mix(11, n=40, sizes=((320, 256),), planes=(64,), max_cams=4)
+                if len(w.rig.cams) == 4)
+    wls = wls[:4] + [four]
+    sweeps, images, host = [], [], []
+    for wl in wls:
+        imgs, _ = scenes.FrameSource(wl, device="cuda").frame(0)
+        host.append([np.ascontiguousarray(i.numpy()) for i in imgs])
+        images.append([torch.from_numpy(h).cuda() for h in host[-1]])
+        sweeps.append(P.Sweep(wl.rig, wl.levels))
+    return dict(wls=wls, sweeps=sweeps, images=images, host=host)
+
+
+@pytest.mark.parametrize("tile_h,kp", [(24, 2), (24, 1), (16, 2), (16, 1)])
+def test_batch_level_maps_against_the_oracle(oracle_mix, tile_h, kp):
+    # every tile shape and pass width of the batched launch, each sweep's
+    # level maps against the FP64 oracle at 2,500 sampled pixels, at the
+    # north-star thresholds
+    import os
+
+    import oracle
+    from tests.parity import assert_sweep_parity
+    oracle.set_threads(os.cpu_count() or 1)
+    m = oracle_mix
+    b = P.Batch(m["sweeps"], tile_h=tile_h, kp=kp, plane_chunk=32)
+    b.run(m["images"], boxes=[w.boxes[0] for w in m["wls"]])
+    torch.cuda.synchronize()
+    assert b.sync_status() == P.PS_OK
+    cams = set()
+    for i, (wl, sw) in enumerate(zip(m["wls"], m["sweeps"])):
+        g = {k: v.cpu().numpy() for k, v in sw.level_outputs()[0].items()}
+        lv = wl.levels[0]
+        H, W = g["kstar"].shape
+        rho = lv.window // 2
+        rng = np.random.default_rng(100 + i)
+        flat = rng.choice((H - 2 * rho) * (W - 2 * rho), 2500, replace=False)
+        pix = np.stack([rho + flat % (W - 2 * rho), rho + flat // (W - 2 * rho)], axis=1).astype(np.int32)
+        o = oracle.sweep_level(wl.rig, lv, m["host"][i], pix=pix)
+        s = assert_sweep_parity(o, {k: v[pix[:, 1], pix[:, 0]] for k, v in g.items()}, min_gated=300,
+                                src=(wl.rig, lv, m["host"][i], pix))
+        print(f"batch th={tile_h} kp={kp} sweep {i} ({W}x{H}, {lv.n_planes} planes, {len(wl.rig.cams)} cams)", s)
+        cams.add(len(wl.rig.cams))
+    assert 4 in cams and len(cams) >= 2
