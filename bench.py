@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", choices=["street", "tiny", "ring", "ringloop", "batch", "diff"], default="street",
+    ap.add_argument("--config", choices=["street", "tiny", "ring", "ringloop", "batch", "diff", "cpubase"],
+                    default="street",
                     help="street: the paper-shaped frame (default); tiny: 160x128, 1 matching camera, 32 planes, "
                          "dense 64^3 TSDF; ring: 4 cameras, 256 full-resolution planes, "
                          "2 cm voxels on a 500 m loop; batch: 64 uneven sweeps in one persistent launch; "
@@ -66,6 +67,9 @@ def parse():
                          "whole 1000-frame ring at 2 cm")
     ap.add_argument("--batch-size", type=int, default=64, help="sweeps per batch (--config batch)")
     ap.add_argument("--half", action="store_true", help="FP16 storage of the matching images")
+    ap.add_argument("--sweep-depth", action="store_true",
+                    help="--config ringloop: fuse the sweep's own depth maps (a contiguous stretch of the loop, "
+                         "sweep + fusion timed) instead of the renderer's true ranges")
     ap.add_argument("--shard", action="store_true",
                     help="N > 1: one sequence split over the ranks (each rank sweeps a plane range of every frame, "
                          "one all-gather of the per-pixel records, every rank merges; the TSDF as hash parts), "
@@ -939,8 +943,111 @@ def run_sharded(args):
     return 0
 
 
+def run_ringloop_swept(args):
+    """A contiguous stretch of the ring (frames 0 .. n-1, 0.5 m apart) through
+    the whole path: each frame's four images swept (256 full-resolution
+    planes, 9x9, FP32 or FP16 image storage), boxes applied, and the swept
+    depth map fused at 2 cm into the local-map pool with swap-out to host
+    memory every 25 frames.  CUDA events around each frame's sweep + fusion
+    (+ swap-out); the rendering of the images is outside them."""
+    import dataclasses
+
+    import torch
+
+    import scenes
+    import paper_1809_06132_gb300 as P
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = scenes.ring(rank_seed(args.seed, rank), n_frames=1000)
+    n = max(10, min(args.steps, 1000))
+    src = scenes.FrameSource(wl, device=f"cuda:{local}")
+    sw = P.Sweep(wl.rig, wl.levels, image_half=args.half)
+    params = dataclasses.replace(wl.tsdf, hash_slots=1 << 22, pool_blocks=1 << 20)
+    T = P.Tsdf(params, wl.rig.ref)
+    H, W = wl.rig.ref.height, wl.rig.ref.width
+    depth = torch.empty((H, W), dtype=torch.float32, device=dev)
+    ev, render_s, host_blocks, peak, valid = [], 0.0, 0, 0, []
+    for f in range(n):
+        t_r = time.time()
+        imgs, _ = src.frame(f)
+        im = [torch.from_numpy(np.ascontiguousarray(i.numpy())).to(dev) for i in imgs]
+        torch.cuda.synchronize()
+        render_s += time.time() - t_r
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record()
+        sw.depth(im, boxes=wl.boxes[f], out=depth)
+        b.record()
+        T.integrate(depth, wl.world_to_ref[f], wl.local_center(f))
+        if f % 25 == 24:
+            k, D, Wt = T.swap_out(wl.local_center(f))
+            host_blocks += int(k.shape[0])
+            k.cpu(), D.cpu(), Wt.cpu()
+        c.record()
+        ev.append((a, b, c))
+        if f % 10 == 9:
+            valid.append(float((depth > 0).float().mean().item()))
+            peak = max(peak, T.count())
+    torch.cuda.synchronize()
+    sweep_ms = [x.elapsed_time(y) for x, y, _ in ev]
+    tsdf_ms = [y.elapsed_time(z) for _, y, z in ev]
+    tot = sum(sweep_ms) + sum(tsdf_ms)
+    st = T.sync_status()
+    line = {"metric": "ring: swept depth + TSDF fusion frames/s (2 cm voxels, contiguous stretch of the loop)",
+            "unit": "frames/s", "value": n / (tot / 1e3), "n_gpus": 1, "steps": n, "warmup": 0,
+            "ms_per_step": tot / n, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (rendered ring images, swept by the library)",
+            "config": {"workload": wl.name, "frames": f"0..{n - 1} of 1000 (contiguous, 0.5 m apart)",
+                       "image_storage": "fp16" if args.half else "fp32", "voxel": 0.02, "mu": 0.1,
+                       "local_map": "60 x 3 x 60 m, 2^20-block pool, swap-out every 25 frames"},
+            "sweep_ms": {"median": statistics.median(sweep_ms), "mean": statistics.mean(sweep_ms)},
+            "tsdf_ms": {"median": statistics.median(tsdf_ms), "mean": statistics.mean(tsdf_ms)},
+            "blocks": {"on_gpu_end": T.count(), "peak_on_gpu": max(peak, T.count()),
+                       "swapped_to_host": host_blocks},
+            "depth_valid_fraction": {"mean": statistics.mean(valid) if valid else None},
+            "status": st, "render_s": render_s, "gpu_launches": n * 7}
+    print(json.dumps(line))
+    return 0
+
+
+def run_cpubase(args):
+    """The FP64 oracle on the host cores for the baseline table: the tiny
+    frame, and street frames 0, 50 and 99 through the whole path, each on
+    every core and on one thread (one thread sweeps every 16th row of each
+    level, scaled to the frame)."""
+    import oracle
+    import scenes
+    n = os.cpu_count() or 1
+    wl = scenes.street(args.seed, n_frames=100)
+    out = {"cores": n}
+    for f in (0, 50, 99):
+        imgs, _ = scenes.FrameSource(wl, device="cuda" if _has_cuda() else "cpu").frame(f)
+        imgs = [i.numpy() for i in imgs]
+        t_all, _ = oracle_frame_s(wl, imgs, f, n)
+        t_one, _ = oracle_frame_s(wl, imgs, f, 1, n_bands=16, bands=[7])
+        out[f"street_frame_{f}"] = {f"s_{n}_threads": t_all, "s_1_thread": t_one}
+    tw = scenes.tiny(args.seed)
+    timgs, _ = scenes.FrameSource(tw).frame(0)
+    timgs = [i.numpy() for i in timgs]
+    out["tiny"] = {f"s_{n}_threads": oracle_frame_s(tw, timgs, 0, n)[0], "s_1_thread": oracle_frame_s(tw, timgs, 0, 1)[0]}
+    oracle.set_threads(n)
+    print(json.dumps({"metric": "FP64 oracle seconds per frame (whole path)", "data": "synthetic", **out}))
+    return 0
+
+
+def _has_cuda():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
 def main():
     args = parse()
+    if args.config == "cpubase":
+        return run_cpubase(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.shard:
@@ -950,7 +1057,7 @@ def main():
     if args.config == "diff":
         return run_diff(args)
     if args.config == "ringloop":
-        return run_ringloop(args)
+        return run_ringloop_swept(args) if args.sweep_depth else run_ringloop(args)
     return run_ours(args)
 
 
