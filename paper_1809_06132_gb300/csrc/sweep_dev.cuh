@@ -299,23 +299,22 @@ __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y
 // is that of the one-plane path, so the costs are bit-identical to it.
 // W2 holds (plane 0, plane 1) sample pairs; H holds, per halo row and output
 // column, (sw0, sw1, sww0, sww1) in the first buffer and (srw0, srw1, m0, m1)
-// in the second (m: invalid samples in the run).  On return cmin0 / cmin1
-// hold the running minimum over cameras of the two planes' costs.
-template <int RHO, bool HALF, int TH>
-__device__ __forceinline__ void pair_pass(const CamS& C, const float* Aj, float d0, float d1, float2* W2,
-                                          const float* Rs, float4* Hs, const float2 (&st)[TH / 8], int base_v,
-                                          float (&cmin0)[TH / 8], float (&cmin1)[TH / 8]) {
+// in the second (m: invalid samples in the run).  cmin0 / cmin1 hold the
+// running minimum over cameras of the two planes' costs.  Each phase is a
+// function of its task (halo position, halo row run, output column segment)
+// alone, so any thread-to-task mapping gives the same results.
+
+// Phase A: warped sample pairs at halo positions p = t0, t0 + stride, ...;
+// returns whether any of this thread's samples is invalid.
+template <int RHO, bool HALF, int TH, int STRIDE>
+__device__ __forceinline__ int pair_phase_a(const CamS& C, const float* Aj, float d0, float d1, float2* W2, int t0) {
     using G = Geo<RHO, TH, 2>;
-    constexpr int SEG = G::SEG, HH = G::HH, HWL = G::HWL, WS = G::WS, WS2 = G::WS2, HS = G::HS;
-    constexpr int NPOS = G::NPOS, N = G::N;
-    const int tid = threadIdx.x;
-    float4* Ha = Hs;
-    float4* Hb = Hs + HH * HS;
-    // phase A: warped sample pairs of the tile + halo
+    constexpr int HWL = G::HWL, WS2 = G::WS2, NPOS = G::NPOS;
+    constexpr int NP = (NPOS + STRIDE - 1) / STRIDE;
     int bad = 0;
-#pragma unroll
-    for (int i = 0; i < G::PPT; ++i) {
-        int p = tid + i * NT;
+#pragma unroll(STRIDE == NT ? NP : 3)
+    for (int i = 0; i < NP; ++i) {
+        int p = t0 + i * STRIDE;
         if (p < NPOS) {
             const float4 a = make_float4(Aj[p], Aj[NPOS + p], Aj[2 * NPOS + p], 0.f);
             float2 w = warp_sample2<HALF>(C, make_float2(fmaf(d0, a.x, C.t[0]), fmaf(d1, a.x, C.t[0])),
@@ -326,9 +325,19 @@ __device__ __forceinline__ void pair_pass(const CamS& C, const float* Aj, float 
             W2[hy * WS2 + hx] = w;
         }
     }
-    bad = __syncthreads_or(bad);
+    return bad;
+}
+
+// Phase H: sliding horizontal sums of both planes along run `hrun` of halo
+// row `hrow` (bad: some sample of the tile is invalid).
+template <int RHO, int TH>
+__device__ __forceinline__ void pair_phase_h(const float2* W2, const float* Rs, float4* Hs, int hrow, int hrun,
+                                             int bad) {
+    using G = Geo<RHO, TH, 2>;
+    constexpr int HH = G::HH, WS = G::WS, WS2 = G::WS2, HS = G::HS;
+    float4* Ha = Hs;
+    float4* Hb = Hs + HH * HS;
     // phase H: sliding horizontal sums of both planes along a run of one halo row
-    const int hrow = tid & 31, hrun = tid >> 5;
     if (hrow < HH && hrun < TW / RUN) {
         const float2* wr = W2 + hrow * WS2 + RUN * hrun;
         const float* rr = Rs + hrow * WS + RUN * hrun;
@@ -394,7 +403,18 @@ __device__ __forceinline__ void pair_pass(const CamS& C, const float* Aj, float 
             }
         }
     }
-    __syncthreads();
+}
+
+// Phase V: sliding vertical sums of both planes down the SEG rows of one
+// output column segment (base_v: its first H entry), ZNCC against the
+// reference statistics st, and the minimum over cameras.
+template <int RHO, int TH>
+__device__ __forceinline__ void pair_phase_v(const float4* Hs, const float2 (&st)[TH / 8], int base_v,
+                                             float (&cmin0)[TH / 8], float (&cmin1)[TH / 8]) {
+    using G = Geo<RHO, TH, 2>;
+    constexpr int SEG = G::SEG, HH = G::HH, HS = G::HS, N = G::N;
+    const float4* Ha = Hs;
+    const float4* Hb = Hs + HH * HS;
     // phase V: sliding vertical sums of both planes down SEG rows, ZNCC, minimum over cameras
     float2 vs = dup2(0.f), vss = dup2(0.f), vrs = dup2(0.f), vm = dup2(0.f);
 #pragma unroll
@@ -426,6 +446,20 @@ __device__ __forceinline__ void pair_pass(const CamS& C, const float* Aj, float 
         cmin0[i] = ok0 ? fminf(cmin0[i], cost.x) : cmin0[i];
         cmin1[i] = ok1 ? fminf(cmin1[i], cost.y) : cmin1[i];
     }
+}
+
+template <int RHO, bool HALF, int TH>
+__device__ __forceinline__ void pair_pass(const CamS& C, const float* Aj, float d0, float d1, float2* W2,
+                                          const float* Rs, float4* Hs, const float2 (&st)[TH / 8], int base_v,
+                                          float (&cmin0)[TH / 8], float (&cmin1)[TH / 8]) {
+    const int tid = threadIdx.x;
+    int bad = pair_phase_a<RHO, HALF, TH, NT>(C, Aj, d0, d1, W2, tid);
+    bad = __syncthreads_or(bad);
+    using G = Geo<RHO, TH, 2>;
+    const int hrow = tid & 31, hrun = tid >> 5;
+    if (hrow < G::HH && hrun < TW / RUN) pair_phase_h<RHO, TH>(W2, Rs, Hs, hrow, hrun, bad);
+    __syncthreads();
+    pair_phase_v<RHO, TH>(Hs, st, base_v, cmin0, cmin1);
 }
 
 // Parabola through the winner and its neighbours in the same plane set, and
@@ -523,6 +557,71 @@ __device__ __forceinline__ void tile_finished(const LevelD& L, bool finished) {
     } else {
         __syncthreads();
     }
+}
+
+// End of a work item whose tile has several plane chunks (its chunk record
+// is written): count it, and when it completes the tile, merge the chunks'
+// records in plane order into the tile's outputs (or records).
+template <int TH>
+__device__ inline void merge_chunks(const LevelD& L, int tile, int* s_flag) {
+    constexpr int SEG = TH / 8;
+    const int tid = threadIdx.x;
+    const int tx = tile % L.tiles_x, ty = tile / L.tiles_x;
+    const int ox = tid % TW, oy0 = (tid / TW) * SEG;
+    const float inf = __int_as_float(0x7f800000);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const int prev = atomicAdd(&L.done[tile], 1);
+        *s_flag = prev == L.n_chunks - 1;
+        // more completions than chunks: the counters were not this call's alone
+        if (prev >= L.n_chunks && L.status) atomicOr(L.status, DEV_STATE);
+    }
+    __syncthreads();
+    if (*s_flag) {
+        __threadfence();
+        const float* base = L.partial + (size_t)tile * L.n_chunks * 7 * (TH * TW);
+#pragma unroll 1
+        for (int i = 0; i < SEG; ++i) {
+            const int gx = tx * TW + ox, gy = ty * TH + oy0 + i;
+            const int px = (oy0 + i) * TW + ox;
+            // global winner (first chunk holding the lowest cost: ties keep the lowest plane)
+            int wc = -1;
+            float b1 = inf;
+            for (int c = 0; c < L.n_chunks; ++c) {
+                float v = __ldcg(base + ((size_t)c * 7 + 0) * (TH * TW) + px);
+                if (v < b1) {
+                    b1 = v;
+                    wc = c;
+                }
+            }
+            float b2 = inf, cm = inf, cp = inf;
+            int k = -1;
+            if (wc >= 0) {
+                const float* P = base + (size_t)wc * 7 * (TH * TW) + px;
+                b2 = __ldcg(P + 1 * (TH * TW));
+                for (int c = 0; c < L.n_chunks; ++c)
+                    if (c != wc) b2 = fminf(b2, __ldcg(base + ((size_t)c * 7 + 0) * (TH * TW) + px));
+                k = __float_as_int(__ldcg(P + 6 * (TH * TW)));
+                const int lo = L.k_begin + wc * L.chunk, hi = min(L.k_end, lo + L.chunk);
+                cm = k > lo ? __ldcg(P + 2 * (TH * TW))
+                            : (wc > 0 ? __ldcg(base + ((size_t)(wc - 1) * 7 + 5) * (TH * TW) + px) : inf);
+                cp = k < hi - 1 ? __ldcg(P + 3 * (TH * TW))
+                                : (wc + 1 < L.n_chunks ? __ldcg(base + ((size_t)(wc + 1) * 7 + 4) * (TH * TW) + px)
+                                                       : inf);
+            }
+            if (gx < L.W && gy < L.H) {
+                if (L.records) {
+                    const float first = __ldcg(base + 4 * (TH * TW) + px);
+                    const float last = __ldcg(base + ((size_t)(L.n_chunks - 1) * 7 + 5) * (TH * TW) + px);
+                    write_record(L, gx, gy, b1, b2, cm, cp, first, last, k);
+                } else {
+                    finish_pixel(L, gx, gy, b1, b2, k, cm, cp);
+                }
+            }
+        }
+    }
+    tile_finished(L, *s_flag != 0);
 }
 
 template <int RHO, bool HALF, int TH, int KP>
@@ -760,66 +859,11 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
         part[5 * TH * TW + px] = cprev[i];  // cost of the item's last plane
         part[6 * TH * TW + px] = __int_as_float(kb[i]);
     }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-        const int prev = atomicAdd(&L.done[tile], 1);
-        *s_flag = prev == L.n_chunks - 1;
-        // more completions than chunks: the counters were not this call's alone
-        if (prev >= L.n_chunks && L.status) atomicOr(L.status, DEV_STATE);
-    }
-    __syncthreads();
-    if (*s_flag) {
-        __threadfence();
-        const float* base = L.partial + (size_t)tile * L.n_chunks * 7 * (TH * TW);
-#pragma unroll 1
-        for (int i = 0; i < SEG; ++i) {
-            const int gx = tx * TW + ox, gy = ty * TH + oy0 + i;
-            const int px = (oy0 + i) * TW + ox;
-            // global winner (first chunk holding the lowest cost: ties keep the lowest plane)
-            int wc = -1;
-            float b1 = inf;
-            for (int c = 0; c < L.n_chunks; ++c) {
-                float v = __ldcg(base + ((size_t)c * 7 + 0) * (TH * TW) + px);
-                if (v < b1) {
-                    b1 = v;
-                    wc = c;
-                }
-            }
-            float b2 = inf, cm = inf, cp = inf;
-            int k = -1;
-            if (wc >= 0) {
-                const float* P = base + (size_t)wc * 7 * (TH * TW) + px;
-                b2 = __ldcg(P + 1 * (TH * TW));
-                for (int c = 0; c < L.n_chunks; ++c)
-                    if (c != wc) b2 = fminf(b2, __ldcg(base + ((size_t)c * 7 + 0) * (TH * TW) + px));
-                k = __float_as_int(__ldcg(P + 6 * (TH * TW)));
-                const int lo = L.k_begin + wc * L.chunk, hi = min(L.k_end, lo + L.chunk);
-                cm = k > lo ? __ldcg(P + 2 * (TH * TW))
-                            : (wc > 0 ? __ldcg(base + ((size_t)(wc - 1) * 7 + 5) * (TH * TW) + px) : inf);
-                cp = k < hi - 1 ? __ldcg(P + 3 * (TH * TW))
-                                : (wc + 1 < L.n_chunks ? __ldcg(base + ((size_t)(wc + 1) * 7 + 4) * (TH * TW) + px)
-                                                       : inf);
-            }
-            if (gx < L.W && gy < L.H) {
-                if (L.records) {
-                    const float first = __ldcg(base + 4 * (TH * TW) + px);
-                    const float last = __ldcg(base + ((size_t)(L.n_chunks - 1) * 7 + 5) * (TH * TW) + px);
-                    write_record(L, gx, gy, b1, b2, cm, cp, first, last, k);
-                } else {
-                    finish_pixel(L, gx, gy, b1, b2, k, cm, cp);
-                }
-            }
-        }
-    }
-    tile_finished(L, *s_flag != 0);
+    merge_chunks<TH>(L, tile, s_flag);
 }
 
-// One work item of a level: stage the matching cameras in shared memory and
-// run the tile routine for the level's window radius and image storage.
-template <int TH, int KP>
-__device__ __forceinline__ void sweep_item(const LevelD& L, int half, int item, CamS* cams, unsigned char* smem,
-                                           int* s_flag) {
+// Stage the matching cameras of a level in shared memory (one thread each).
+__device__ __forceinline__ void stage_cams(const LevelD& L, CamS* cams) {
     if (threadIdx.x < L.n_cams) {
         const CamJ& J = L.cams[threadIdx.x];
         CamS& c = cams[threadIdx.x];
@@ -836,6 +880,14 @@ __device__ __forceinline__ void sweep_item(const LevelD& L, int half, int item, 
         c.k12 = dup2(c.k1); c.k22 = dup2(c.k2); c.p12 = dup2(c.p1); c.p1x2 = dup2(2.0f * c.p1);
         c.p22 = dup2(c.p2); c.p2x2 = dup2(2.0f * c.p2); c.lim2 = dup2(c.lim);
     }
+}
+
+// One work item of a level: stage the matching cameras in shared memory and
+// run the tile routine for the level's window radius and image storage.
+template <int TH, int KP>
+__device__ __forceinline__ void sweep_item(const LevelD& L, int half, int item, CamS* cams, unsigned char* smem,
+                                           int* s_flag) {
+    stage_cams(L, cams);
     __syncthreads();
     if (half) {
         switch (L.rho) {
