@@ -143,10 +143,12 @@ __device__ __forceinline__ void ref_stats_tile(const uint8_t* img, int W, int s,
                                                                                       : make_float2(0.f, -1.f);
 }
 
-// Quad images of the matching cameras of a level.  Each thread forms the
-// level pixels (x, y) and (x, y + 1) and takes the (x + 1) column from its
-// lane neighbour, so every level pixel is computed about twice instead of
-// four times.
+// Quad images of the matching cameras of a level.  A block covers PREP_T
+// columns of QROWS rows; each thread walks down its column forming level
+// pixel (x, y + 1) once per row (row y's value comes from the previous row)
+// and takes the (x + 1) column from its lane neighbour, so every level pixel
+// is computed about once per quad that needs it instead of four times.
+constexpr int QROWS = 8;
 struct QuadJobs {
     const uint8_t* img[PS_MAX_CAMS];
     void* out[PS_MAX_CAMS];
@@ -154,25 +156,34 @@ struct QuadJobs {
     int s, half;
 };
 
-__device__ __forceinline__ void quad_row(const QuadJobs& Q, int j, int xb, int y) {
+__device__ __forceinline__ void quad_rows(const QuadJobs& Q, int j, int xb, int yb) {
     const int Wl = Q.Wl[j], Hl = Q.Hl[j];
-    if (xb * PREP_T >= Wl || y >= Hl) return;  // whole block outside this camera
+    const int y0 = yb * QROWS;
+    if (xb * PREP_T >= Wl || y0 >= Hl) return;  // whole block outside this camera
     const int x = xb * PREP_T + threadIdx.x;
     const uint8_t* img = Q.img[j];
     const int W = Q.W[j], s = Q.s;
-    float a = level_px(img, W, Wl, Hl, s, x, y), b = level_px(img, W, Wl, Hl, s, x, y + 1);
-    float a1 = __shfl_down_sync(0xffffffffu, a, 1), b1 = __shfl_down_sync(0xffffffffu, b, 1);
-    if ((threadIdx.x & 31) == 31) {
-        a1 = level_px(img, W, Wl, Hl, s, x + 1, y);
-        b1 = level_px(img, W, Wl, Hl, s, x + 1, y + 1);
-    }
-    if (x >= Wl) return;
-    const size_t o = (size_t)y * Wl + x;
-    if (Q.half) {  // FP16 storage: four halves in 8 bytes
-        __half2 p = __floats2half2_rn(a, a1), q = __floats2half2_rn(b, b1);
-        static_cast<uint2*>(Q.out[j])[o] = make_uint2(*reinterpret_cast<unsigned*>(&p), *reinterpret_cast<unsigned*>(&q));
-    } else {
-        static_cast<float4*>(Q.out[j])[o] = make_float4(a, a1, b, b1);
+    const bool edge = (threadIdx.x & 31) == 31;
+    float a = level_px(img, W, Wl, Hl, s, x, y0);
+    float a1 = __shfl_down_sync(0xffffffffu, a, 1);
+    if (edge) a1 = level_px(img, W, Wl, Hl, s, x + 1, y0);
+    const int y1 = min(Hl, y0 + QROWS);
+    for (int y = y0; y < y1; ++y) {
+        const float b = level_px(img, W, Wl, Hl, s, x, y + 1);
+        float b1 = __shfl_down_sync(0xffffffffu, b, 1);
+        if (edge) b1 = level_px(img, W, Wl, Hl, s, x + 1, y + 1);
+        if (x < Wl) {
+            const size_t o = (size_t)y * Wl + x;
+            if (Q.half) {  // FP16 storage: four halves in 8 bytes
+                __half2 p = __floats2half2_rn(a, a1), q = __floats2half2_rn(b, b1);
+                static_cast<uint2*>(Q.out[j])[o] =
+                    make_uint2(*reinterpret_cast<unsigned*>(&p), *reinterpret_cast<unsigned*>(&q));
+            } else {
+                static_cast<float4*>(Q.out[j])[o] = make_float4(a, a1, b, b1);
+            }
+        }
+        a = b;
+        a1 = b1;
     }
 }
 
@@ -186,7 +197,7 @@ struct PrepLevel {
     float2* stats;
     int rs_tiles_x, rs_blocks;      // reference tiles
     QuadJobs Q;
-    int n_cams, q_xblocks, q_rows, q_blocks;  // quad blocks: rows of PREP_T pixels x rows x cameras
+    int n_cams, q_xblocks, q_rows, q_blocks;  // quad blocks: PREP_T columns x QROWS-row bands x cameras
     int* done;                      // per-tile chunk counters to zero
     int n_done;
 };
@@ -216,7 +227,7 @@ __global__ void __launch_bounds__(PREP_T) prep_kernel(const __grid_constant__ Pr
         b -= L.rs_blocks;
         if (b < L.q_blocks) {
             const int per_cam = L.q_xblocks * L.q_rows, j = b / per_cam, r = b - j * per_cam;
-            quad_row(L.Q, j, r % L.q_xblocks, r / L.q_xblocks);
+            quad_rows(L.Q, j, r % L.q_xblocks, r / L.q_xblocks);
             return;
         }
         b -= L.q_blocks;
@@ -704,7 +715,7 @@ int launch_sweep(psweep_t* h, const uint8_t* const* images, const int32_t* plane
             Q.half = h->image_half;
             R.n_cams = h->n_cams;
             R.q_xblocks = (wmax + PREP_T - 1) / PREP_T;
-            R.q_rows = hmax;
+            R.q_rows = (hmax + QROWS - 1) / QROWS;
             R.q_blocks = R.q_xblocks * R.q_rows * h->n_cams;
         }
         prep_blocks += R.rs_blocks + R.q_blocks;

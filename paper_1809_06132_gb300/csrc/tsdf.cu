@@ -321,48 +321,20 @@ __device__ __forceinline__ void update_voxel(const FrameP& F, const float* depth
 
 __global__ void __launch_bounds__(IT) integrate_kernel(const __grid_constant__ FrameP F, TsdfDev T,
                                                        const float* depth) {
-    // The list entry, key and voxels of the CTA's next block are loaded while
-    // the current block is updated, so the dependent loads (list -> slot ->
-    // key and voxels) of one block overlap the arithmetic of the previous one.
-    const int nv = *T.n_vis;
-    int e = blockIdx.x;
-    if (e >= nv) return;
-    int bi = T.vis[e];
-    int4 k = make_int4(0, 0, 0, 0);
-    float4 pr = make_float4(0.f, 0.f, 0.f, 0.f);
-    bool ok = PS_DCHECK(bi >= 0 && bi < T.pool_cap, CHK_POOL);  // uniform over the CTA
-    if (ok) {
-        k = T.pool_keys[bi];
-        pr = reinterpret_cast<const float4*>(T.vox + (size_t)bi * B3)[threadIdx.x];
-    }
-    const int v0 = 2 * threadIdx.x;  // voxels v0, v0 + 1: same y, z; x and x + 1
-    const int x = v0 & 7, y = (v0 >> 3) & 7, z = v0 >> 6;
-    for (; e < nv; e += gridDim.x) {
-        // prefetch the next block of this CTA
-        const int en = e + gridDim.x;
-        int bn = -1;
-        int4 kn = make_int4(0, 0, 0, 0);
-        float4 pn = make_float4(0.f, 0.f, 0.f, 0.f);
-        bool okn = false;
-        if (en < nv) {
-            bn = T.vis[en];
-            okn = PS_DCHECK(bn >= 0 && bn < T.pool_cap, CHK_POOL);
-            if (okn) {
-                kn = T.pool_keys[bn];
-                pn = reinterpret_cast<const float4*>(T.vox + (size_t)bn * B3)[threadIdx.x];
-            }
-        }
-        if (ok) {
-            const int ax = k.x * B + x - F.ic[0], ay = k.y * B + y - F.ic[1], az = k.z * B + z - F.ic[2];
-            float2 a = make_float2(pr.x, pr.y), b = make_float2(pr.z, pr.w);
-            update_voxel(F, depth, ax, ay, az, a);
-            update_voxel(F, depth, ax + 1, ay, az, b);
-            reinterpret_cast<float4*>(T.vox + (size_t)bi * B3)[threadIdx.x] = make_float4(a.x, a.y, b.x, b.y);
-        }
-        bi = bn;
-        k = kn;
-        pr = pn;
-        ok = okn;
+    int nv = *T.n_vis;
+    for (int e = blockIdx.x; e < nv; e += gridDim.x) {
+        int bi = T.vis[e];
+        if (!PS_DCHECK(bi >= 0 && bi < T.pool_cap, CHK_POOL)) continue;  // uniform over the CTA
+        int4 k = T.pool_keys[bi];
+        float4* blk = reinterpret_cast<float4*>(T.vox + (size_t)bi * B3);
+        float4 pr = blk[threadIdx.x];
+        int v0 = 2 * threadIdx.x;  // voxels v0, v0 + 1: same y, z; x and x + 1
+        int x = v0 & 7, y = (v0 >> 3) & 7, z = v0 >> 6;
+        int ax = k.x * B + x - F.ic[0], ay = k.y * B + y - F.ic[1], az = k.z * B + z - F.ic[2];
+        float2 a = make_float2(pr.x, pr.y), b = make_float2(pr.z, pr.w);
+        update_voxel(F, depth, ax, ay, az, a);
+        update_voxel(F, depth, ax + 1, ay, az, b);
+        blk[threadIdx.x] = make_float4(a.x, a.y, b.x, b.y);
     }
 }
 
