@@ -419,6 +419,14 @@ def run_ours(args):
     ms_per_step = ms / args.steps
     value = world * args.steps / (ms / 1e3)
     n_blocks = T.count(stream)
+    # rays the allocation stage walks per frame: pixels with a depth in the
+    # merged, masked maps of the timed frames (counted after the timing)
+    rays = []
+    for k in range(min(args.steps, nf)):
+        f = (args.warmup + k) % nf
+        sw.depth(imgs_dev[f], boxes=wl.boxes[f], out=depth, stream=stream)
+        rays.append(int((depth > 0).sum().item()))
+    rays_per_frame = statistics.mean(rays)
 
     # e2e: host images -> device -> depth + fusion -> depth map back to host, per step
     sw.profile(0)
@@ -502,7 +510,10 @@ def run_ours(args):
         "tsdf": {"ms_per_frame": sum(tsdf_ms) / max(1, n_ts),
                  "ms_stages": {"depth_max": tsdf_ms[0] / max(1, n_ts), "alloc": tsdf_ms[1] / max(1, n_ts),
                                "visible": tsdf_ms[2] / max(1, n_ts), "integrate": integ_ms},
-                 "blocks_allocated": n_blocks, "status": st},
+                 "blocks_allocated": n_blocks, "status": st,
+                 "alloc": {"rays_per_frame": rays_per_frame,
+                           "rays_per_s": rays_per_frame / (tsdf_ms[1] / max(1, n_ts) * 1e-3),
+                           "note": "segments [d - mu, d + mu] walked by the allocation stage per second"}},
         "roofline": {"kernel": "sweep_kernel", "bound": "alu", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                      "traffic": SWEEP_DRAM_BYTES_STREET if args.config == "street" and not args.half else None,

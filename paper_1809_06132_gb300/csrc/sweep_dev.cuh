@@ -135,34 +135,10 @@ __device__ __forceinline__ void quad_px(const uint8_t* img, int W, int s, int Wl
 }
 
 // Mean and sum of squared deviations of the window of radius rho centred on
-// base[0] (row stride `stride`), by the two-pass direct sums (row by row,
-// left to right; the unrolled radii add in the same order).
-template <int RHO>
-__device__ __forceinline__ float2 window_stats_r(const float* base, int stride) {
-    float s = 0.f;
-#pragma unroll
-    for (int dy = -RHO; dy <= RHO; ++dy)
-#pragma unroll
-        for (int dx = -RHO; dx <= RHO; ++dx) s += base[dy * stride + dx];
-    float m = s / (float)((2 * RHO + 1) * (2 * RHO + 1));
-    float v = 0.f;
-#pragma unroll
-    for (int dy = -RHO; dy <= RHO; ++dy)
-#pragma unroll
-        for (int dx = -RHO; dx <= RHO; ++dx) {
-            float e = base[dy * stride + dx] - m;
-            v = fmaf(e, e, v);
-        }
-    return make_float2(m, v);
-}
-
+// base[0] (row stride `stride`), by the two-pass direct sums.  (Unrolling
+// the loops per radius took the prep launch from 32 to 95 registers and
+// from 82% to 23% occupancy: 57.8 against 32.6 us per frame.)
 __device__ __forceinline__ float2 window_stats(const float* base, int stride, int rho) {
-    switch (rho) {
-        case 2: return window_stats_r<2>(base, stride);
-        case 3: return window_stats_r<3>(base, stride);
-        case 4: return window_stats_r<4>(base, stride);
-        default: break;
-    }
     float s = 0.f;
     for (int dy = -rho; dy <= rho; ++dy)
         for (int dx = -rho; dx <= rho; ++dx) s += base[dy * stride + dx];
