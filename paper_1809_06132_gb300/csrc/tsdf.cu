@@ -319,7 +319,9 @@ __device__ __forceinline__ void update_voxel(const FrameP& F, const float* depth
     dw.y = fminf(w + 1.0f, F.w_max);
 }
 
-__global__ void __launch_bounds__(IT) integrate_kernel(const __grid_constant__ FrameP F, TsdfDev T,
+// 32 registers (8 CTAs, the whole register file, per SM): measured 3% faster on
+// the ring workload than the unconstrained 40 (0.190 against 0.196 ms per frame).
+__global__ void __launch_bounds__(IT, 8) integrate_kernel(const __grid_constant__ FrameP F, TsdfDev T,
                                                        const float* depth) {
     int nv = *T.n_vis;
     for (int e = blockIdx.x; e < nv; e += gridDim.x) {
