@@ -374,9 +374,12 @@ class Sweep:
         n_parts = len(part_lo)
         if not 1 <= n_parts <= MAX_PARTS or len(records) != n_parts:
             raise ValueError(f"need 1..{MAX_PARTS} parts with one record list each")
-        for r, (h, w) in zip(records[0], self.level_shapes()):
-            if tuple(r.shape) != (N_RECORD, h, w):
-                raise ValueError(f"a record buffer must be ({N_RECORD}, {h}, {w})")
+        for p in range(n_parts):
+            if len(records[p]) != nl:
+                raise ValueError(f"part {p} needs {nl} record buffers")
+            for r, (h, w) in zip(records[p], self.level_shapes()):
+                if tuple(r.shape) != (N_RECORD, h, w) or r.dtype != torch.float32 or not r.is_contiguous():
+                    raise ValueError(f"part {p}: a record buffer must be contiguous float32 ({N_RECORD}, {h}, {w})")
         lo = (C.c_int32 * (n_parts * nl))(*[int(part_lo[p][l]) for p in range(n_parts) for l in range(nl)])
         rp = (C.c_void_p * (n_parts * nl))(*[_dev(records[p][l], torch.float32, "records")
                                              for p in range(n_parts) for l in range(nl)])
