@@ -682,6 +682,45 @@ def run_batch(args):
                 acc.append(a.elapsed_time(b))
         small_lat = sorted(Bs.timing()[0])
     small_pp = sum(w.pix_planes() for w in small)
+    # queue order: the same 64 sweeps queued shortest first, as drawn, largest
+    # first, and largest / smallest alternating (given order of a permutation)
+    work = [wl.pix_planes() * len(wl.rig.cams) for wl in wls]
+    by_size = sorted(range(len(wls)), key=lambda i: work[i])
+    alt = [x for pair in zip(reversed(by_size), by_size) for x in pair][:len(wls)]
+    seen, interleaved = set(), []
+    for i in alt:
+        if i not in seen:
+            seen.add(i)
+            interleaved.append(i)
+    orders = {"shortest_first": (list(range(len(wls))), P.BATCH_SHORTEST_FIRST),
+              "as_drawn": (list(range(len(wls))), P.BATCH_GIVEN_ORDER),
+              "largest_first": (list(reversed(by_size)), P.BATCH_GIVEN_ORDER),
+              "large_small_interleaved": (interleaved, P.BATCH_GIVEN_ORDER)}
+    order_cmp = {}
+    with torch.cuda.stream(stream):
+        for name, (perm, mode) in orders.items():
+            Bo = P.Batch([sweeps[i] for i in perm], opts=P.batch_opts(tile_h=o.tile_h, kp=o.kp,
+                                                                    plane_chunk=o.plane_chunk, order=mode))
+            args_o = ([images[i] for i in perm], [boxes[i] for i in perm], [outs[i] for i in perm])
+            for _ in range(2):
+                Bo.run(args_o[0], boxes=args_o[1], outs=args_o[2], stream=stream)
+            ms_o, lat_o = [], []
+            for _ in range(max(3, args.steps // 2)):
+                flush.zero_()
+                stream.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                Bo.run(args_o[0], boxes=args_o[1], outs=args_o[2], stream=stream)
+                b.record(stream)
+                stream.synchronize()
+                ms_o.append(a.elapsed_time(b))
+                lat_o.extend(Bo.timing()[0])
+            lat_o.sort()
+            order_cmp[name] = {"batch_ms": statistics.median(ms_o),
+                               "gpix_planes_s": pix_planes / (statistics.median(ms_o) * 1e-3) / 1e9,
+                               "latency_p50_ms": lat_o[len(lat_o) // 2],
+                               "latency_p99_ms": lat_o[min(len(lat_o) - 1, int(0.99 * len(lat_o)))]}
+            Bo.close()
     clocks.stop()
     clk = clocks.summary(t0, t1)
     if not clk.get("samples"):
@@ -713,6 +752,7 @@ def run_batch(args):
                       "singles_ms": statistics.median(sl), "speedup_vs_singles": statistics.median(sl) /
                       statistics.median(sb), "gpix_planes_s": small_pp / (statistics.median(sb) * 1e-3) / 1e9,
                       "latency_ms": {"p50": small_lat[len(small_lat) // 2], "p99": small_lat[-1]}},
+        "queue_order": order_cmp,
         "autotune": [{"tile_h": c.tile_h, "kp": c.kp, "plane_chunk": c.plane_chunk, "ms": m}
                      for c, m in zip(cands, tune_ms)],
         "roofline": {"kernel": "batch_kernel", "bound": "alu", "achieved": achieved, "peak": peak_tflops,
