@@ -143,8 +143,10 @@ __global__ void __launch_bounds__(NT, 1) batch_kernel(const __grid_constant__ Ba
     __shared__ __align__(16) LevelD sL;
     __shared__ int4 s_q;
     __shared__ int s_go, s_flag;
+    __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x;
     if (tid == 0) atomicMin(A.t, global_ns());
+    const uint32_t tmem = tm_alloc(&s_tmem);
     for (;;) {
         if (tid == 0) {
             const int t = atomicAdd(A.head, 1);
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(NT, 1) batch_kernel(const __grid_constant__ Ba
             int* dst = reinterpret_cast<int*>(&sL);
             for (int i = tid; i < (int)(sizeof(LevelD) / sizeof(int)); i += NT) dst[i] = src[i];
             __syncthreads();
-            sweep_item<TH, KP>(sL, J.image_half, idx, cams, smem, &s_flag);
+            sweep_item<TH, KP>(sL, J.image_half, idx, cams, smem, &s_flag, tmem);
         } else if (kind == Q_REF || kind == Q_STATS) {
             const PrepD& P = J.prep[lvl];
             const int y0 = idx * PREP_ROWS, n = min(PREP_ROWS, P.Hl - y0) * P.Wl;
@@ -223,6 +225,7 @@ __global__ void __launch_bounds__(NT, 1) batch_kernel(const __grid_constant__ Ba
         }
         __syncthreads();
     }
+    tm_free(tmem);
 }
 
 }  // namespace ps

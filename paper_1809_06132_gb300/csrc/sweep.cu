@@ -240,7 +240,9 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const __grid_constant__ Sw
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ CamS cams[PS_MAX_CAMS];
     __shared__ int s_tile, s_flag;
+    __shared__ uint32_t s_tmem;
     const int total = P.lv[0].n_items + (P.n_levels > 1 ? P.lv[1].n_items : 0);
+    const uint32_t tmem = tm_alloc(&s_tmem);
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1);
         __syncthreads();
@@ -248,10 +250,11 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const __grid_constant__ Sw
         __syncthreads();
         if (t >= total) break;
         if (t < P.lv[0].n_items)
-            sweep_item<TH_SINGLE, KP_SINGLE>(P.lv[0], P.image_half, t, cams, smem, &s_flag);
+            sweep_item<TH_SINGLE, KP_SINGLE>(P.lv[0], P.image_half, t, cams, smem, &s_flag, tmem);
         else
-            sweep_item<TH_SINGLE, KP_SINGLE>(P.lv[1], P.image_half, t - P.lv[0].n_items, cams, smem, &s_flag);
+            sweep_item<TH_SINGLE, KP_SINGLE>(P.lv[1], P.image_half, t - P.lv[0].n_items, cams, smem, &s_flag, tmem);
     }
+    tm_free(tmem);
 }
 
 // ------------------------------------------------------------- merge

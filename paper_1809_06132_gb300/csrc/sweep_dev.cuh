@@ -12,7 +12,8 @@
 namespace ps {
 
 constexpr int TW = 64;   // output tile width (pixels)
-constexpr int NT = 512;  // threads per CTA (one CTA per SM)
+constexpr int NT = 768;  // threads per CTA (one CTA per SM); all of them warp (phase A)
+constexpr int NTV = 512; // threads that own output pixels: phase V, winner-take-all, outputs
 constexpr int RUN = 4;   // outputs per horizontal run (phase H)
 constexpr int PLANE_CHUNK = 32;  // most planes one work item sweeps (default)
 static_assert(NT / 32 >= TW / RUN, "phase H: one warp per run, one lane per halo row");
@@ -251,6 +252,108 @@ __device__ __forceinline__ float2 warp_sample2(const CamS& c, float2 X, float2 Y
                        sample_at<HALF>(c, u.y, v.y, (Z.y > ln.y) && (r2.y <= c.r2_max)));
 }
 
+// Winner-take-all state in tensor memory.  Each output-owning thread keeps
+// the state of its SEG pixels (best and second-best cost, the costs of the
+// previous, first and winner's neighbouring planes, the winner and whether
+// the next plane's cost is owed) in 32 words of TMEM between plane pairs,
+// not in registers: the registers go to the warp instead.  A warp reaches
+// the TMEM lanes of its quadrant (warp id mod 4); the warps of a quadrant
+// take 32 columns each (warps that own no pixels hold an unused copy).  The CTA allocates TMEM_COLS
+// columns once (tm_alloc) and frees them before it exits (tm_free).
+constexpr uint32_t TMEM_COLS = 256;
+static_assert((NT / 32 + 3) / 4 * 32 <= (int)TMEM_COLS, "32 TMEM columns per warp");
+
+__device__ __forceinline__ uint32_t tm_addr(uint32_t base) {
+    const uint32_t w = threadIdx.x >> 5;
+    return base + (((w & 3u) * 32u) << 16) + (w >> 2) * 32u;
+}
+
+// Warp 0 allocates the CTA's columns and writes their address to *slot;
+// every thread reads it after the barrier.
+__device__ __forceinline__ uint32_t tm_alloc(uint32_t* slot) {
+    if (threadIdx.x < 32)
+        asm volatile(
+            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n\t"
+            "tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::"r"((uint32_t)__cvta_generic_to_shared(slot)),
+            "n"(TMEM_COLS)
+            : "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return *slot;
+}
+
+// Every thread's TMEM stores have completed; warp 0 frees the columns.
+__device__ __forceinline__ void tm_free(uint32_t base) {
+    asm volatile("tcgen05.wait::st.sync.aligned;\n\ttcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "n"(TMEM_COLS) : "memory");
+}
+
+// 32 words of this thread's TMEM lane (warp-collective).  The load waits for
+// the thread's earlier stores and for its own completion.
+__device__ __forceinline__ void tm_ld32(uint32_t a, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.wait::st.sync.aligned;\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                 "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                 "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(a)
+        : "memory");
+}
+__device__ __forceinline__ void tm_st32(uint32_t a, const uint32_t (&r)[32]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(a),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+                 "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+                 "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
+                 "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+                 : "memory");
+}
+
+// The state arrays of SEG pixels, packed 8 words per pixel.
+#define PS_WTA_ARGS(Q) Q float (&c1)[SEG], Q float (&c2)[SEG], Q float (&cprev)[SEG], Q float (&cminus)[SEG], \
+    Q float (&cplus)[SEG], Q float (&cfirst)[SEG], Q int (&kb)[SEG], Q bool (&needp)[SEG]
+template <int SEG>
+__device__ __forceinline__ void wta_load(uint32_t a, PS_WTA_ARGS()) {
+    static_assert(8 * SEG <= 32, "the state of SEG pixels fits 32 words");
+    uint32_t r[32];
+    tm_ld32(a, r);
+#pragma unroll
+    for (int i = 0; i < SEG; ++i) {
+        c1[i] = __uint_as_float(r[8 * i]);
+        c2[i] = __uint_as_float(r[8 * i + 1]);
+        cprev[i] = __uint_as_float(r[8 * i + 2]);
+        cminus[i] = __uint_as_float(r[8 * i + 3]);
+        cplus[i] = __uint_as_float(r[8 * i + 4]);
+        cfirst[i] = __uint_as_float(r[8 * i + 5]);
+        kb[i] = (int)r[8 * i + 6];
+        needp[i] = r[8 * i + 7] != 0u;
+    }
+}
+template <int SEG>
+__device__ __forceinline__ void wta_store(uint32_t a, PS_WTA_ARGS(const)) {
+    uint32_t r[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) r[i] = 0u;
+#pragma unroll
+    for (int i = 0; i < SEG; ++i) {
+        r[8 * i] = __float_as_uint(c1[i]);
+        r[8 * i + 1] = __float_as_uint(c2[i]);
+        r[8 * i + 2] = __float_as_uint(cprev[i]);
+        r[8 * i + 3] = __float_as_uint(cminus[i]);
+        r[8 * i + 4] = __float_as_uint(cplus[i]);
+        r[8 * i + 5] = __float_as_uint(cfirst[i]);
+        r[8 * i + 6] = (uint32_t)kb[i];
+        r[8 * i + 7] = needp[i] ? 1u : 0u;
+    }
+    tm_st32(a, r);
+}
+#undef PS_WTA_ARGS
+
 // Tile geometry.  A CTA owns TW x TH output pixels of one level plus a halo of
 // RHO on every side (HH rows x HWL columns of warped samples per plane and
 // camera).  Per plane set, every halo position keeps, per matching camera,
@@ -286,7 +389,7 @@ struct Geo {
         return sizeof(float4) * KP * HH * HS + sizeof(float) * ((KP == 2 ? 2 * HH * WS2 : HH * WS) + HH * WS) +
                sizeof(float) * 3 * (size_t)n_cams * NPOS;
     }
-    static_assert(NT == TW * (TH / SEG) && TH % 8 == 0, "phase V: one thread per column and row segment");
+    static_assert(NTV == TW * (TH / SEG) && TH % 8 == 0 && NTV <= NT, "phase V: one thread per column and row segment");
     static_assert(KP == 1 || KP == 2, "one or two planes per pass");
     static_assert(HH <= 32, "phase H maps one warp lane per halo row");
     static_assert(HWL <= WS && 4 * NV + TW - RUN <= WS, "row stride covers the runs' loads");
@@ -461,7 +564,7 @@ __device__ __forceinline__ void pair_pass(const CamS& C, const float* Aj, float 
     const int hrow = tid & 31, hrun = tid >> 5;
     if (hrow < G::HH && hrun < TW / RUN) pair_phase_h<RHO, TH>(W2, Rs, Hs, hrow, hrun, bad);
     __syncthreads();
-    pair_phase_v<RHO, TH>(Hs, st, base_v, cmin0, cmin1);
+    if (tid < NTV) pair_phase_v<RHO, TH>(Hs, st, base_v, cmin0, cmin1);
 }
 
 // Parabola through the winner and its neighbours in the same plane set, and
@@ -580,7 +683,7 @@ __device__ inline void merge_chunks(const LevelD& L, int tile, int* s_flag) {
         if (prev >= L.n_chunks && L.status) atomicOr(L.status, DEV_STATE);
     }
     __syncthreads();
-    if (*s_flag) {
+    if (*s_flag && tid < NTV) {
         __threadfence();
         const float* base = L.partial + (size_t)tile * L.n_chunks * 7 * (TH * TW);
 #pragma unroll 1
@@ -627,7 +730,8 @@ __device__ inline void merge_chunks(const LevelD& L, int tile, int* s_flag) {
 }
 
 template <int RHO, bool HALF, int TH, int KP>
-__device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, unsigned char* smem_raw, int* s_flag) {
+__device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, unsigned char* smem_raw, int* s_flag,
+                                  uint32_t tmem) {
     using G = Geo<RHO, TH, KP>;
     constexpr int SEG = G::SEG;
     if (!PS_DCHECK(item >= 0 && item < L.n_items, CHK_ITEM)) return;  // uniform over the CTA
@@ -651,25 +755,30 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
         bool in = gx >= 0 && gy >= 0 && gx < L.W && gy < L.H;
         Rs[hy * WS + hx] = in ? L.ref[(size_t)gy * L.W + gx] : 0.0f;
     }
-    // outputs of this thread: column ox, rows oy0 .. oy0 + SEG - 1; their
-    // reference window mean and 1/sqrt(sum of squared deviations), NaN = unusable
+    // outputs of this thread (tid < NTV): column ox, rows oy0 .. oy0 + SEG - 1;
+    // their reference window mean and 1/sqrt(sum of squared deviations), NaN = unusable
+    const bool owner = tid < NTV;  // uniform over each warp
     const int ox = tid % TW, oy0 = (tid / TW) * SEG;
+    const uint32_t tm = tm_addr(tmem);
     float2 st[SEG];
 #pragma unroll
     for (int i = 0; i < SEG; ++i) {
         int gx = tx * TW + ox, gy = ty * TH + oy0 + i;
         float2 v = make_float2(0.f, -1.f);
-        if (gx < L.W && gy < L.H) v = L.stats[(size_t)gy * L.W + gx];
+        if (owner && gx < L.W && gy < L.H) v = L.stats[(size_t)gy * L.W + gx];
         st[i] = v.y >= (float)N * 1e-8f ? make_float2(v.x, rsqrtf(v.y)) : make_float2(nan, nan);
     }
-    float c1[SEG], c2[SEG], cprev[SEG], cminus[SEG], cplus[SEG], cfirst[SEG];
-    int kb[SEG];
-    bool needp[SEG];
+    {
+        float c1[SEG], c2[SEG], cprev[SEG], cminus[SEG], cplus[SEG], cfirst[SEG];
+        int kb[SEG];
+        bool needp[SEG];
 #pragma unroll
-    for (int i = 0; i < SEG; ++i) {
-        c1[i] = c2[i] = cprev[i] = cminus[i] = cplus[i] = cfirst[i] = inf;
-        kb[i] = -1;
-        needp[i] = false;
+        for (int i = 0; i < SEG; ++i) {
+            c1[i] = c2[i] = cprev[i] = cminus[i] = cplus[i] = cfirst[i] = inf;
+            kb[i] = -1;
+            needp[i] = false;
+        }
+        wta_store<SEG>(tm, c1, c2, cprev, cminus, cplus, cfirst, kb, needp);
     }
     const int hrow = tid & 31, hrun = tid >> 5;  // phase H item
     const int base_v = oy0 * HS + ox;            // phase V first H entry
@@ -782,6 +891,7 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
                         }
                     }
                     __syncthreads();
+                    if (!owner) continue;
                     // phase V: sliding vertical sums down SEG rows, ZNCC, minimum over cameras
                     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -805,6 +915,11 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
                 }
             }
             // streaming winner-take-all with each plane's aggregated cost, in plane order
+            if (!owner) continue;
+            float c1[SEG], c2[SEG], cprev[SEG], cminus[SEG], cplus[SEG], cfirst[SEG];
+            int kb[SEG];
+            bool needp[SEG];
+            wta_load<SEG>(tm, c1, c2, cprev, cminus, cplus, cfirst, kb, needp);
 #pragma unroll
             for (int q = 0; q < KP; ++q) {
                 if (q >= np) break;
@@ -830,12 +945,18 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
                     cprev[i] = cc;
                 }
             }
+            wta_store<SEG>(tm, c1, c2, cprev, cminus, cplus, cfirst, kb, needp);
         }
     }
 
+    float c1[SEG], c2[SEG], cprev[SEG], cminus[SEG], cplus[SEG], cfirst[SEG];
+    int kb[SEG];
+    bool needp[SEG];
+    wta_load<SEG>(tm, c1, c2, cprev, cminus, cplus, cfirst, kb, needp);
     if (L.n_chunks == 1) {
 #pragma unroll
         for (int i = 0; i < SEG; ++i) {
+            if (!owner) break;
             int gx = tx * TW + ox, gy = ty * TH + oy0 + i;
             if (gx < L.W && gy < L.H) {
                 if (L.records)
@@ -852,6 +973,7 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
     float* part = L.partial + (size_t)item * 7 * (TH * TW);
 #pragma unroll
     for (int i = 0; i < SEG; ++i) {
+        if (!owner) break;
         const int px = (oy0 + i) * TW + ox;
         part[0 * TH * TW + px] = c1[i];
         part[1 * TH * TW + px] = c2[i];
@@ -888,20 +1010,20 @@ __device__ __forceinline__ void stage_cams(const LevelD& L, CamS* cams) {
 // run the tile routine for the level's window radius and image storage.
 template <int TH, int KP>
 __device__ __forceinline__ void sweep_item(const LevelD& L, int half, int item, CamS* cams, unsigned char* smem,
-                                           int* s_flag) {
+                                           int* s_flag, uint32_t tmem) {
     stage_cams(L, cams);
     __syncthreads();
     if (half) {
         switch (L.rho) {
-            case 2: sweep_tile<2, true, TH, KP>(L, cams, item, smem, s_flag); break;
-            case 3: sweep_tile<3, true, TH, KP>(L, cams, item, smem, s_flag); break;
-            default: sweep_tile<4, true, TH, KP>(L, cams, item, smem, s_flag); break;
+            case 2: sweep_tile<2, true, TH, KP>(L, cams, item, smem, s_flag, tmem); break;
+            case 3: sweep_tile<3, true, TH, KP>(L, cams, item, smem, s_flag, tmem); break;
+            default: sweep_tile<4, true, TH, KP>(L, cams, item, smem, s_flag, tmem); break;
         }
     } else {
         switch (L.rho) {
-            case 2: sweep_tile<2, false, TH, KP>(L, cams, item, smem, s_flag); break;
-            case 3: sweep_tile<3, false, TH, KP>(L, cams, item, smem, s_flag); break;
-            default: sweep_tile<4, false, TH, KP>(L, cams, item, smem, s_flag); break;
+            case 2: sweep_tile<2, false, TH, KP>(L, cams, item, smem, s_flag, tmem); break;
+            case 3: sweep_tile<3, false, TH, KP>(L, cams, item, smem, s_flag, tmem); break;
+            default: sweep_tile<4, false, TH, KP>(L, cams, item, smem, s_flag, tmem); break;
         }
     }
 }
