@@ -19,8 +19,9 @@
 //                      the invalid count with separable sums, ZNCC -> cost,
 //                      minimum over cameras, and a streaming winner-take-all
 //                      that keeps the best, second best and the winner's two
-//                      neighbours in registers.  The cost volume never
-//                      leaves the SM.  Both levels' tiles share one launch.
+//                      neighbours in tensor memory between plane pairs.  The
+//                      cost volume never leaves the SM.  Both levels' tiles
+//                      share one launch.
 //   merge_kernel       full-resolution merge of the levels and box masks.
 #include <algorithm>
 #include <cmath>
