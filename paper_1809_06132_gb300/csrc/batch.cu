@@ -230,7 +230,11 @@ extern "C" int psbatch_create(psweep_t* const* sweeps, int32_t n, const ps_batch
         }
         PB_TRY(cudaFuncSetAttribute(b->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         PB_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b->kernel, NT, smem));
-        const int fit = sms * std::max(1, per_sm);
+        if (per_sm < 1) {
+            free_batch(b);
+            PS_ARG(false, "psbatch_create: the batch kernel does not fit one SM");
+        }
+        const int fit = sms;  // one CTA per SM: each CTA allocates all of its SM's tensor memory
         b->grid = o.grid > 0 ? std::min(o.grid, fit) : fit;
     }
 

@@ -646,7 +646,11 @@ extern "C" int psweep_create(const ps_sweep_desc* d, psweep_t** out) {
         PS_TRY(cudaGetDevice(&dev));
         PS_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         PS_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel, NT, sweep_smem<TH_SINGLE, KP_SINGLE>(4, d->n_cams)));
-        h->grid = sms * std::max(1, per_sm);
+        if (per_sm < 1) {
+            free_sweep(h);
+            PS_ARG(false, "psweep_create: the sweep kernel does not fit one SM");
+        }
+        h->grid = sms;  // one CTA per SM: each CTA allocates all of its SM's tensor memory
     }
     PS_TRY(cudaDeviceSynchronize());
 #undef PS_TRY

@@ -260,12 +260,43 @@ __device__ __forceinline__ float2 warp_sample2(const CamS& c, float2 X, float2 Y
 // the TMEM lanes of its quadrant (warp id mod 4); the warps of a quadrant
 // take 32 columns each (warps that own no pixels hold an unused copy).  The CTA allocates TMEM_COLS
 // columns once (tm_alloc) and frees them before it exits (tm_free).
-constexpr uint32_t TMEM_COLS = 256;
-static_assert((NT / 32 + 3) / 4 * 32 <= (int)TMEM_COLS, "32 TMEM columns per warp");
+// The same lanes also hold each thread's direction tables (see sweep_tile):
+// TM_TAB + 9 j holds, for matching camera j, the three coordinates of the
+// direction of each of the thread's (at most 3) halo positions.
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t TM_WARP_COLS = 80;  // columns of one warp: state, then tables
+constexpr uint32_t TM_TAB = 32;        // first table column of a warp
+static_assert((NT / 32 + 3) / 4 * TM_WARP_COLS <= TMEM_COLS, "TMEM columns of every warp");
+static_assert(TM_TAB + 9 * PS_MAX_CAMS <= TM_WARP_COLS, "state and tables of every camera fit a warp's columns");
 
 __device__ __forceinline__ uint32_t tm_addr(uint32_t base) {
     const uint32_t w = threadIdx.x >> 5;
-    return base + (((w & 3u) * 32u) << 16) + (w >> 2) * 32u;
+    return base + (((w & 3u) * 32u) << 16) + (w >> 2) * TM_WARP_COLS;
+}
+
+// 9 words at TMEM address a (warp-collective; waits for the thread's earlier
+// stores first and for the load's completion).
+__device__ __forceinline__ void tm_ld9(uint32_t a, float (&v)[9]) {
+    uint32_t r[9];
+    asm volatile(
+        "tcgen05.wait::st.sync.aligned;\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%9];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%8}, [%10];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8])
+        : "r"(a), "r"(a + 8u)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tm_st9(uint32_t a, const float (&v)[9]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%2, %3, %4, %5, %6, %7, %8, %9};\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x1.b32 [%1], {%10};" ::"r"(a),
+        "r"(a + 8u), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])),
+        "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8]))
+        : "memory");
 }
 
 // Warp 0 allocates the CTA's columns and writes their address to *slot;
@@ -357,7 +388,8 @@ __device__ __forceinline__ void wta_store(uint32_t a, PS_WTA_ARGS(const)) {
 // Tile geometry.  A CTA owns TW x TH output pixels of one level plus a halo of
 // RHO on every side (HH rows x HWL columns of warped samples per plane and
 // camera).  Per plane set, every halo position keeps, per matching camera,
-// a = R_j r / (n . r), so that the plane at offset d maps it to d a + t_j.
+// a = R_j r / (n . r), so that the plane at offset d maps it to d a + t_j
+// (in the TMEM lane of the thread that warps the position).
 // Phase A: every thread warps PPT halo positions into W.  Phase H: thread
 // (row, run) slides a 2 RHO + 1 window along RUN outputs of one halo row and
 // stores (sum w, sum w^2, sum r w, invalid count) in H.  Phase V: thread
@@ -384,11 +416,11 @@ struct Geo {
     // of phase H, one halo row each, hit distinct bank groups)
     static constexpr int WS2 = 74;
     static constexpr int NV2 = (NRUNPOS + 1) / 2;     // 16-byte loads (two pairs) per run
-    // KP H buffers, W, R and n_cams direction tables (three floats per position)
-    static constexpr size_t smem(int n_cams) {
-        return sizeof(float4) * KP * HH * HS + sizeof(float) * ((KP == 2 ? 2 * HH * WS2 : HH * WS) + HH * WS) +
-               sizeof(float) * 3 * (size_t)n_cams * NPOS;
+    // KP H buffers, W and R (the direction tables are in TMEM)
+    static constexpr size_t smem(int) {
+        return sizeof(float4) * KP * HH * HS + sizeof(float) * ((KP == 2 ? 2 * HH * WS2 : HH * WS) + HH * WS);
     }
+    static_assert(PPT <= 3, "three directions per thread and camera in TMEM");
     static_assert(NTV == TW * (TH / SEG) && TH % 8 == 0 && NTV <= NT, "phase V: one thread per column and row segment");
     static_assert(KP == 1 || KP == 2, "one or two planes per pass");
     static_assert(HH <= 32, "phase H maps one warp lane per halo row");
@@ -409,19 +441,21 @@ __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y
 // function of its task (halo position, halo row run, output column segment)
 // alone, so any thread-to-task mapping gives the same results.
 
-// Phase A: warped sample pairs at halo positions p = t0, t0 + stride, ...;
-// returns whether any of this thread's samples is invalid.
+// Phase A: warped sample pairs at halo positions p = t0 + i STRIDE, whose
+// directions are av[3 i .. 3 i + 2]; returns whether any of this thread's
+// samples is invalid.
 template <int RHO, bool HALF, int TH, int STRIDE>
-__device__ __forceinline__ int pair_phase_a(const CamS& C, const float* Aj, float d0, float d1, float2* W2, int t0) {
+__device__ __forceinline__ int pair_phase_a(const CamS& C, const float (&av)[9], float d0, float d1, float2* W2, int t0) {
     using G = Geo<RHO, TH, 2>;
     constexpr int HWL = G::HWL, WS2 = G::WS2, NPOS = G::NPOS;
     constexpr int NP = (NPOS + STRIDE - 1) / STRIDE;
+    static_assert(NP <= 3, "three directions per thread and camera");
     int bad = 0;
-#pragma unroll(STRIDE == NT ? NP : 3)
+#pragma unroll
     for (int i = 0; i < NP; ++i) {
         int p = t0 + i * STRIDE;
         if (p < NPOS) {
-            const float4 a = make_float4(Aj[p], Aj[NPOS + p], Aj[2 * NPOS + p], 0.f);
+            const float4 a = make_float4(av[3 * i], av[3 * i + 1], av[3 * i + 2], 0.f);
             float2 w = warp_sample2<HALF>(C, make_float2(fmaf(d0, a.x, C.t[0]), fmaf(d1, a.x, C.t[0])),
                                           make_float2(fmaf(d0, a.y, C.t[1]), fmaf(d1, a.y, C.t[1])),
                                           make_float2(fmaf(d0, a.z, C.t[2]), fmaf(d1, a.z, C.t[2])));
@@ -554,11 +588,11 @@ __device__ __forceinline__ void pair_phase_v(const float4* Hs, const float2 (&st
 }
 
 template <int RHO, bool HALF, int TH>
-__device__ __forceinline__ void pair_pass(const CamS& C, const float* Aj, float d0, float d1, float2* W2,
+__device__ __forceinline__ void pair_pass(const CamS& C, const float (&av)[9], float d0, float d1, float2* W2,
                                           const float* Rs, float4* Hs, const float2 (&st)[TH / 8], int base_v,
                                           float (&cmin0)[TH / 8], float (&cmin1)[TH / 8]) {
     const int tid = threadIdx.x;
-    int bad = pair_phase_a<RHO, HALF, TH, NT>(C, Aj, d0, d1, W2, tid);
+    int bad = pair_phase_a<RHO, HALF, TH, NT>(C, av, d0, d1, W2, tid);
     bad = __syncthreads_or(bad);
     using G = Geo<RHO, TH, 2>;
     const int hrow = tid & 31, hrun = tid >> 5;
@@ -742,7 +776,6 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
     float* Ws = reinterpret_cast<float*>(Hs + KP * HH * HS);      // warped samples (NaN = invalid): KP = 1 [HH][WS],
     float2* W2 = reinterpret_cast<float2*>(Ws);                   //   KP = 2 [HH][WS2] pairs (plane k0, plane k0 + 1)
     float* Rs = Ws + (KP == 2 ? 2 * HH * G::WS2 : HH * WS);       // [HH][WS] reference intensities
-    float* A = Rs + HH * WS;                                      // [n_cams][3][NPOS] R_j r / (n . r); NaN = none
     const int tid = threadIdx.x;
     const int tx = tile % L.tiles_x, ty = tile / L.tiles_x;
     const int gx0 = tx * TW - RHO, gy0 = ty * TH - RHO;
@@ -787,21 +820,36 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
         const int s_lo = max(L.sets[s].start, k_lo), k_end = min(L.sets[s].start + L.sets[s].count, k_hi);
         if (s_lo >= k_end) continue;  // the set lies outside this work item's planes
         const float snx = L.sets[s].nx, sny = L.sets[s].ny, snz = L.sets[s].nz;
-        __syncthreads();  // previous users of A are done
-        for (int p = tid; p < NPOS; p += NT) {
-            int hy = p / HWL, hx = p - hy * HWL;
-            int gx = gx0 + hx, gy = gy0 + hy;
+        // this thread's halo positions p = tid + i NT: per matching camera the
+        // directions R_j r / (n . r) (NaN = none), into this thread's TMEM lane
+        float rx[G::PPT], ry[G::PPT], rz[G::PPT], rinv[G::PPT];
+#pragma unroll
+        for (int i = 0; i < G::PPT; ++i) {
+            const int p = tid + i * NT;
+            const int hy = p / HWL, hx = p - hy * HWL;
+            const int gx = gx0 + hx, gy = gy0 + hy;
             float4 r = make_float4(nan, nan, nan, 0.f);
-            if (gx >= 0 && gy >= 0 && gx < L.W && gy < L.H) r = L.rays[(size_t)gy * L.W + gx];
+            if (p < NPOS && gx >= 0 && gy >= 0 && gx < L.W && gy < L.H) r = L.rays[(size_t)gy * L.W + gx];
             float nr = snx * r.x + sny * r.y + snz * r.z;
-            float inv = nr > 0.0f ? 1.0f / nr : nan;
-            for (int j = 0; j < L.n_cams; ++j) {
-                const CamS& C = cams[j];
-                float* Aj = A + j * 3 * NPOS;
-                Aj[p] = inv * fmaf(C.R[0], r.x, fmaf(C.R[1], r.y, C.R[2] * r.z));
-                Aj[NPOS + p] = inv * fmaf(C.R[3], r.x, fmaf(C.R[4], r.y, C.R[5] * r.z));
-                Aj[2 * NPOS + p] = inv * fmaf(C.R[6], r.x, fmaf(C.R[7], r.y, C.R[8] * r.z));
+            rinv[i] = nr > 0.0f ? 1.0f / nr : nan;
+            rx[i] = r.x;
+            ry[i] = r.y;
+            rz[i] = r.z;
+        }
+        for (int j = 0; j < L.n_cams; ++j) {
+            const CamS& C = cams[j];
+            float av[9];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                if (i < G::PPT) {
+                    av[3 * i] = rinv[i] * fmaf(C.R[0], rx[i], fmaf(C.R[1], ry[i], C.R[2] * rz[i]));
+                    av[3 * i + 1] = rinv[i] * fmaf(C.R[3], rx[i], fmaf(C.R[4], ry[i], C.R[5] * rz[i]));
+                    av[3 * i + 2] = rinv[i] * fmaf(C.R[6], rx[i], fmaf(C.R[7], ry[i], C.R[8] * rz[i]));
+                } else {
+                    av[3 * i] = av[3 * i + 1] = av[3 * i + 2] = nan;
+                }
             }
+            tm_st9(tm + TM_TAB + 9 * j, av);
         }
         __syncthreads();
         // planes go in groups of KP: the planes of a group are swept with one camera
@@ -816,11 +864,12 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
                 for (int i = 0; i < SEG; ++i) cmin[q][i] = inf;
             for (int j = 0; j < L.n_cams; ++j) {
                 const CamS& C = cams[j];
-                const float* Aj = A + j * 3 * NPOS;
+                float av[9];
+                tm_ld9(tm + TM_TAB + 9 * j, av);
                 const float d0 = __ldg(&L.planes[k0].d);
                 const float d1 = __ldg(&L.planes[k0 + np - 1].d);
                 if constexpr (KP == 2) {
-                    pair_pass<RHO, HALF, TH>(C, Aj, d0, d1, W2, Rs, Hs, st, base_v, cmin[0], cmin[1]);
+                    pair_pass<RHO, HALF, TH>(C, av, d0, d1, W2, Rs, Hs, st, base_v, cmin[0], cmin[1]);
                 } else {
                     // phase A: warped samples of the tile + halo for the plane
                     int bad = 0;
@@ -828,7 +877,7 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
                     for (int i = 0; i < G::PPT; ++i) {
                         int p = tid + i * NT;
                         if (p < NPOS) {
-                            const float4 a = make_float4(Aj[p], Aj[NPOS + p], Aj[2 * NPOS + p], 0.f);
+                            const float4 a = make_float4(av[3 * i], av[3 * i + 1], av[3 * i + 2], 0.f);
                             float w0 = warp_sample<HALF>(C, fmaf(d0, a.x, C.t[0]), fmaf(d0, a.y, C.t[1]), fmaf(d0, a.z, C.t[2]));
                             bad |= isnan(w0);
                             int hy = p / HWL, hx = p - hy * HWL;
