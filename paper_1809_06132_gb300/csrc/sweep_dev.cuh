@@ -416,9 +416,13 @@ struct Geo {
     // of phase H, one halo row each, hit distinct bank groups)
     static constexpr int WS2 = 74;
     static constexpr int NV2 = (NRUNPOS + 1) / 2;     // 16-byte loads (two pairs) per run
-    // KP H buffers, W and R (the direction tables are in TMEM)
+    // With two planes per pass, two matching cameras go through each step
+    // (CG = 2): W and H hold both cameras' samples and sums.
+    static constexpr int CG = KP == 2 ? 2 : 1;
+    static constexpr int WSZ = KP == 2 ? 2 * HH * WS2 : HH * WS;  // floats of one camera's W
+    // CG x KP H buffers, CG W buffers and R (the direction tables are in TMEM)
     static constexpr size_t smem(int) {
-        return sizeof(float4) * KP * HH * HS + sizeof(float) * ((KP == 2 ? 2 * HH * WS2 : HH * WS) + HH * WS);
+        return sizeof(float4) * CG * KP * HH * HS + sizeof(float) * (CG * WSZ + HH * WS);
     }
     static_assert(PPT <= 3, "three directions per thread and camera in TMEM");
     static_assert(NTV == TW * (TH / SEG) && TH % 8 == 0 && NTV <= NT, "phase V: one thread per column and row segment");
@@ -601,6 +605,35 @@ __device__ __forceinline__ void pair_pass(const CamS& C, const float (&av)[9], f
     if (tid < NTV) pair_phase_v<RHO, TH>(Hs, st, base_v, cmin0, cmin1);
 }
 
+// Two matching cameras in one step (the second camera's samples and sums in
+// the second W and H buffers): one pair of barriers for both.  Each phase
+// computes what it computes for one camera, and the invalid-sample flag is
+// shared (the flagged path gives valid samples the same sums), so the costs
+// are those of two one-camera steps.
+template <int RHO, bool HALF, int TH>
+__device__ __forceinline__ void pair_pass2(const CamS& C0, const CamS& C1, const float (&av0)[9], const float (&av1)[9],
+                                           float d0, float d1, float2* W2, const float* Rs, float4* Hs,
+                                           const float2 (&st)[TH / 8], int base_v, float (&cmin0)[TH / 8],
+                                           float (&cmin1)[TH / 8]) {
+    using G = Geo<RHO, TH, 2>;
+    const int tid = threadIdx.x;
+    float2* W2b = W2 + G::WSZ / 2;
+    float4* Hsb = Hs + 2 * G::HH * G::HS;
+    int bad = pair_phase_a<RHO, HALF, TH, NT>(C0, av0, d0, d1, W2, tid);
+    bad |= pair_phase_a<RHO, HALF, TH, NT>(C1, av1, d0, d1, W2b, tid);
+    bad = __syncthreads_or(bad);
+    const int hrow = tid & 31, hrun = tid >> 5;
+    if (hrow < G::HH && hrun < TW / RUN) {
+        pair_phase_h<RHO, TH>(W2, Rs, Hs, hrow, hrun, bad);
+        pair_phase_h<RHO, TH>(W2b, Rs, Hsb, hrow, hrun, bad);
+    }
+    __syncthreads();
+    if (tid < NTV) {
+        pair_phase_v<RHO, TH>(Hs, st, base_v, cmin0, cmin1);
+        pair_phase_v<RHO, TH>(Hsb, st, base_v, cmin0, cmin1);
+    }
+}
+
 // Parabola through the winner and its neighbours in the same plane set, and
 // the range along the pixel's ray; writes the level outputs of one pixel.
 __device__ inline void finish_pixel(const LevelD& L, int gx, int gy, float c1, float c2, int kb, float cminus, float cplus) {
@@ -772,10 +805,10 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
     const int tile = item / L.n_chunks, chunk = item - tile * L.n_chunks;
     const int k_lo = L.k_begin + chunk * L.chunk, k_hi = min(L.k_end, k_lo + L.chunk);
     constexpr int HH = G::HH, HWL = G::HWL, WS = G::WS, HS = G::HS, NPOS = G::NPOS, N = G::N;
-    float4* Hs = reinterpret_cast<float4*>(smem_raw);            // [KP][HH][HS] window sums
-    float* Ws = reinterpret_cast<float*>(Hs + KP * HH * HS);      // warped samples (NaN = invalid): KP = 1 [HH][WS],
-    float2* W2 = reinterpret_cast<float2*>(Ws);                   //   KP = 2 [HH][WS2] pairs (plane k0, plane k0 + 1)
-    float* Rs = Ws + (KP == 2 ? 2 * HH * G::WS2 : HH * WS);       // [HH][WS] reference intensities
+    float4* Hs = reinterpret_cast<float4*>(smem_raw);            // [CG][KP][HH][HS] window sums
+    float* Ws = reinterpret_cast<float*>(Hs + G::CG * KP * HH * HS);  // [CG] warped samples (NaN = invalid): KP = 1
+    float2* W2 = reinterpret_cast<float2*>(Ws);                   //   [HH][WS], KP = 2 [HH][WS2] pairs (k0, k0 + 1)
+    float* Rs = Ws + G::CG * G::WSZ;                              // [HH][WS] reference intensities
     const int tid = threadIdx.x;
     const int tx = tile % L.tiles_x, ty = tile / L.tiles_x;
     const int gx0 = tx * TW - RHO, gy0 = ty * TH - RHO;
@@ -869,7 +902,15 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
                 const float d0 = __ldg(&L.planes[k0].d);
                 const float d1 = __ldg(&L.planes[k0 + np - 1].d);
                 if constexpr (KP == 2) {
-                    pair_pass<RHO, HALF, TH>(C, av, d0, d1, W2, Rs, Hs, st, base_v, cmin[0], cmin[1]);
+                    if (j + 1 < L.n_cams) {  // two cameras in one step
+                        float av1[9];
+                        tm_ld9(tm + TM_TAB + 9 * (j + 1), av1);
+                        pair_pass2<RHO, HALF, TH>(C, cams[j + 1], av, av1, d0, d1, W2, Rs, Hs, st, base_v, cmin[0],
+                                                  cmin[1]);
+                        ++j;
+                    } else {
+                        pair_pass<RHO, HALF, TH>(C, av, d0, d1, W2, Rs, Hs, st, base_v, cmin[0], cmin[1]);
+                    }
                 } else {
                     // phase A: warped samples of the tile + halo for the plane
                     int bad = 0;
