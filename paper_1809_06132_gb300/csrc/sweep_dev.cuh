@@ -472,77 +472,80 @@ __device__ __forceinline__ int pair_phase_a(const CamS& C, const float (&av)[9],
 }
 
 // Phase H: sliding horizontal sums of both planes along run `hrun` of halo
-// row `hrow` (bad: some sample of the tile is invalid).
-template <int RHO, int TH>
+// row `hrow` (bad: some sample of the tile is invalid), for NC cameras
+// (camera c's samples and sums at W2 + c WSZ / 2 and Hs + 2 c HH HS); the
+// reference samples of the run are loaded once.
+template <int RHO, int TH, int NC = 1>
 __device__ __forceinline__ void pair_phase_h(const float2* W2, const float* Rs, float4* Hs, int hrow, int hrun,
                                              int bad) {
     using G = Geo<RHO, TH, 2>;
     constexpr int HH = G::HH, WS = G::WS, WS2 = G::WS2, HS = G::HS;
-    float4* Ha = Hs;
-    float4* Hb = Hs + HH * HS;
     // phase H: sliding horizontal sums of both planes along a run of one halo row
     if (hrow < HH && hrun < TW / RUN) {
-        const float2* wr = W2 + hrow * WS2 + RUN * hrun;
         const float* rr = Rs + hrow * WS + RUN * hrun;
-        float2 w[2 * G::NV2];
         float r[4 * G::NV];
-#pragma unroll
-        for (int qq = 0; qq < G::NV2; ++qq) {
-            float4 a = *reinterpret_cast<const float4*>(wr + 2 * qq);
-            w[2 * qq] = make_float2(a.x, a.y);
-            w[2 * qq + 1] = make_float2(a.z, a.w);
-        }
 #pragma unroll
         for (int qq = 0; qq < G::NV; ++qq) {
             float4 b = *reinterpret_cast<const float4*>(rr + 4 * qq);
             r[4 * qq] = b.x; r[4 * qq + 1] = b.y; r[4 * qq + 2] = b.z; r[4 * qq + 3] = b.w;
         }
-        float4* ha = Ha + hrow * HS + RUN * hrun;
-        float4* hb = Hb + hrow * HS + RUN * hrun;
-        float2 sw = dup2(0.f), sww = dup2(0.f), srw = dup2(0.f), sm = dup2(0.f);
-        if (!bad) {  // every sample of the tile is valid (the common case)
 #pragma unroll
-            for (int t = 0; t <= 2 * RHO; ++t) {
-                sw = add2(sw, w[t]);
-                sww = fma2(w[t], w[t], sww);
-                srw = fma2(dup2(r[t]), w[t], srw);
+        for (int c = 0; c < NC; ++c) {
+            const float2* wr = W2 + c * (G::WSZ / 2) + hrow * WS2 + RUN * hrun;
+            float2 w[2 * G::NV2];
+#pragma unroll
+            for (int qq = 0; qq < G::NV2; ++qq) {
+                float4 a = *reinterpret_cast<const float4*>(wr + 2 * qq);
+                w[2 * qq] = make_float2(a.x, a.y);
+                w[2 * qq + 1] = make_float2(a.z, a.w);
             }
-            ha[0] = make_float4(sw.x, sw.y, sww.x, sww.y);
-            hb[0] = make_float4(srw.x, srw.y, 0.f, 0.f);
+            float4* ha = Hs + c * 2 * HH * HS + hrow * HS + RUN * hrun;
+            float4* hb = ha + HH * HS;
+            float2 sw = dup2(0.f), sww = dup2(0.f), srw = dup2(0.f), sm = dup2(0.f);
+            if (!bad) {  // every sample of the tile is valid (the common case)
 #pragma unroll
-            for (int o = 1; o < RUN; ++o) {
-                const int a = o + 2 * RHO, b = o - 1;
-                sw = add2(sw, add2(w[a], neg2(w[b])));
-                sww = add2(sww, fma2(w[a], w[a], mul2(neg2(w[b]), w[b])));
-                srw = add2(srw, fma2(dup2(r[a]), w[a], mul2(dup2(-r[b]), w[b])));
-                ha[o] = make_float4(sw.x, sw.y, sww.x, sww.y);
-                hb[o] = make_float4(srw.x, srw.y, 0.f, 0.f);
-            }
-        } else {  // invalid samples: excluded from the sums and counted
+                for (int t = 0; t <= 2 * RHO; ++t) {
+                    sw = add2(sw, w[t]);
+                    sww = fma2(w[t], w[t], sww);
+                    srw = fma2(dup2(r[t]), w[t], srw);
+                }
+                ha[0] = make_float4(sw.x, sw.y, sww.x, sww.y);
+                hb[0] = make_float4(srw.x, srw.y, 0.f, 0.f);
 #pragma unroll
-            for (int t = 0; t <= 2 * RHO; ++t) {
-                const bool bx = isnan(w[t].x), by = isnan(w[t].y);
-                const float2 wt = make_float2(bx ? 0.0f : w[t].x, by ? 0.0f : w[t].y);
-                sw = add2(sw, wt);
-                sww = fma2(wt, wt, sww);
-                srw = fma2(dup2(r[t]), wt, srw);
-                sm = add2(sm, make_float2(bx ? 1.0f : 0.0f, by ? 1.0f : 0.0f));
-            }
-            ha[0] = make_float4(sw.x, sw.y, sww.x, sww.y);
-            hb[0] = make_float4(srw.x, srw.y, sm.x, sm.y);
+                for (int o = 1; o < RUN; ++o) {
+                    const int a = o + 2 * RHO, b = o - 1;
+                    sw = add2(sw, add2(w[a], neg2(w[b])));
+                    sww = add2(sww, fma2(w[a], w[a], mul2(neg2(w[b]), w[b])));
+                    srw = add2(srw, fma2(dup2(r[a]), w[a], mul2(dup2(-r[b]), w[b])));
+                    ha[o] = make_float4(sw.x, sw.y, sww.x, sww.y);
+                    hb[o] = make_float4(srw.x, srw.y, 0.f, 0.f);
+                }
+            } else {  // invalid samples: excluded from the sums and counted
 #pragma unroll
-            for (int o = 1; o < RUN; ++o) {
-                const int a = o + 2 * RHO, b = o - 1;
-                const bool ax = isnan(w[a].x), ay = isnan(w[a].y), bx = isnan(w[b].x), by = isnan(w[b].y);
-                const float2 wa = make_float2(ax ? 0.0f : w[a].x, ay ? 0.0f : w[a].y);
-                const float2 wb = make_float2(bx ? 0.0f : w[b].x, by ? 0.0f : w[b].y);
-                sw = add2(sw, add2(wa, neg2(wb)));
-                sww = add2(sww, fma2(wa, wa, mul2(neg2(wb), wb)));
-                srw = add2(srw, fma2(dup2(r[a]), wa, mul2(dup2(-r[b]), wb)));
-                sm = add2(sm, add2(make_float2(ax ? 1.0f : 0.0f, ay ? 1.0f : 0.0f),
-                                   neg2(make_float2(bx ? 1.0f : 0.0f, by ? 1.0f : 0.0f))));
-                ha[o] = make_float4(sw.x, sw.y, sww.x, sww.y);
-                hb[o] = make_float4(srw.x, srw.y, sm.x, sm.y);
+                for (int t = 0; t <= 2 * RHO; ++t) {
+                    const bool bx = isnan(w[t].x), by = isnan(w[t].y);
+                    const float2 wt = make_float2(bx ? 0.0f : w[t].x, by ? 0.0f : w[t].y);
+                    sw = add2(sw, wt);
+                    sww = fma2(wt, wt, sww);
+                    srw = fma2(dup2(r[t]), wt, srw);
+                    sm = add2(sm, make_float2(bx ? 1.0f : 0.0f, by ? 1.0f : 0.0f));
+                }
+                ha[0] = make_float4(sw.x, sw.y, sww.x, sww.y);
+                hb[0] = make_float4(srw.x, srw.y, sm.x, sm.y);
+#pragma unroll
+                for (int o = 1; o < RUN; ++o) {
+                    const int a = o + 2 * RHO, b = o - 1;
+                    const bool ax = isnan(w[a].x), ay = isnan(w[a].y), bx = isnan(w[b].x), by = isnan(w[b].y);
+                    const float2 wa = make_float2(ax ? 0.0f : w[a].x, ay ? 0.0f : w[a].y);
+                    const float2 wb = make_float2(bx ? 0.0f : w[b].x, by ? 0.0f : w[b].y);
+                    sw = add2(sw, add2(wa, neg2(wb)));
+                    sww = add2(sww, fma2(wa, wa, mul2(neg2(wb), wb)));
+                    srw = add2(srw, fma2(dup2(r[a]), wa, mul2(dup2(-r[b]), wb)));
+                    sm = add2(sm, add2(make_float2(ax ? 1.0f : 0.0f, ay ? 1.0f : 0.0f),
+                                       neg2(make_float2(bx ? 1.0f : 0.0f, by ? 1.0f : 0.0f))));
+                    ha[o] = make_float4(sw.x, sw.y, sww.x, sww.y);
+                    hb[o] = make_float4(srw.x, srw.y, sm.x, sm.y);
+                }
             }
         }
     }
@@ -623,10 +626,7 @@ __device__ __forceinline__ void pair_pass2(const CamS& C0, const CamS& C1, const
     bad |= pair_phase_a<RHO, HALF, TH, NT>(C1, av1, d0, d1, W2b, tid);
     bad = __syncthreads_or(bad);
     const int hrow = tid & 31, hrun = tid >> 5;
-    if (hrow < G::HH && hrun < TW / RUN) {
-        pair_phase_h<RHO, TH>(W2, Rs, Hs, hrow, hrun, bad);
-        pair_phase_h<RHO, TH>(W2b, Rs, Hsb, hrow, hrun, bad);
-    }
+    pair_phase_h<RHO, TH, 2>(W2, Rs, Hs, hrow, hrun, bad);
     __syncthreads();
     if (tid < NTV) {
         pair_phase_v<RHO, TH>(Hs, st, base_v, cmin0, cmin1);
