@@ -607,9 +607,17 @@ extern "C" int psweep_create(const ps_sweep_desc* d, psweep_t** out) {
         PS_TRY(cudaMalloc(&h->stats[l], sizeof(float2) * (size_t)W * H));
         {
             // work items: tiles x chunks of at most PLANE_CHUNK planes, so that
-            // items of both levels cost about the same and balance across SMs
+            // items of both levels cost about the same and balance across SMs;
+            // a level with at least 16 waves of items even at twice that takes
+            // chunks of up to 2 PLANE_CHUNK (half the per-item work: direction
+            // tables, reference tile, chunk records; the tail stays short)
             const int n_tiles = ((W + TW - 1) / TW) * ((H + TH_SINGLE - 1) / TH_SINGLE);
-            h->chunk[l] = balanced_chunk(h->n_planes[l], PLANE_CHUNK);
+            int dev = 0, sms = 0;
+            PS_TRY(cudaGetDevice(&dev));
+            PS_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            const int c2 = balanced_chunk(h->n_planes[l], 2 * PLANE_CHUNK);
+            const long long items2 = (long long)n_tiles * ((h->n_planes[l] + c2 - 1) / c2);
+            h->chunk[l] = items2 >= 16LL * sms ? c2 : balanced_chunk(h->n_planes[l], PLANE_CHUNK);
             const int n_chunks = (h->n_planes[l] + h->chunk[l] - 1) / h->chunk[l];
             if (n_chunks > 1)
                 PS_TRY(cudaMalloc(&h->partial[l], sizeof(float) * 7 * TH_SINGLE * TW * (size_t)n_tiles * n_chunks));
@@ -734,7 +742,7 @@ int launch_sweep(psweep_t* h, const uint8_t* const* images, const int32_t* plane
             // chunk scratch sized for the whole level holds them)
             D.k_begin = plane_lo[l];
             D.k_end = plane_hi[l];
-            D.chunk = balanced_chunk(std::max(1, D.k_end - D.k_begin), PLANE_CHUNK);
+            D.chunk = balanced_chunk(std::max(1, D.k_end - D.k_begin), h->chunk[l]);
             D.n_chunks = std::max(1, (D.k_end - D.k_begin + D.chunk - 1) / D.chunk);
             D.n_items = D.n_tiles * D.n_chunks;
         }
