@@ -613,6 +613,36 @@ __device__ __forceinline__ void pair_pass(const CamS& C, const float (&av)[9], f
 // computes what it computes for one camera, and the invalid-sample flag is
 // shared (the flagged path gives valid samples the same sums), so the costs
 // are those of two one-camera steps.
+// Phase A of a two-camera step: per halo position both cameras' sample
+// pairs (independent work for the scheduler), into W2 and W2b.
+template <int RHO, bool HALF, int TH>
+__device__ __forceinline__ int pair_phase_a2(const CamS& C0, const CamS& C1, const float (&av0)[9], const float (&av1)[9],
+                                             float d0, float d1, float2* W2, float2* W2b, int t0) {
+    using G = Geo<RHO, TH, 2>;
+    constexpr int HWL = G::HWL, WS2 = G::WS2, NPOS = G::NPOS;
+    constexpr int NP = (NPOS + NT - 1) / NT;
+    int bad = 0;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        int p = t0 + i * NT;
+        if (p < NPOS) {
+            int hy = p / HWL, hx = p - hy * HWL;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const CamS& C = c ? C1 : C0;
+                const float (&av)[9] = c ? av1 : av0;
+                const float4 a = make_float4(av[3 * i], av[3 * i + 1], av[3 * i + 2], 0.f);
+                float2 w = warp_sample2<HALF>(C, make_float2(fmaf(d0, a.x, C.t[0]), fmaf(d1, a.x, C.t[0])),
+                                              make_float2(fmaf(d0, a.y, C.t[1]), fmaf(d1, a.y, C.t[1])),
+                                              make_float2(fmaf(d0, a.z, C.t[2]), fmaf(d1, a.z, C.t[2])));
+                bad |= isnan(w.x) | isnan(w.y);
+                (c ? W2b : W2)[hy * WS2 + hx] = w;
+            }
+        }
+    }
+    return bad;
+}
+
 template <int RHO, bool HALF, int TH>
 __device__ __forceinline__ void pair_pass2(const CamS& C0, const CamS& C1, const float (&av0)[9], const float (&av1)[9],
                                            float d0, float d1, float2* W2, const float* Rs, float4* Hs,
@@ -622,8 +652,7 @@ __device__ __forceinline__ void pair_pass2(const CamS& C0, const CamS& C1, const
     const int tid = threadIdx.x;
     float2* W2b = W2 + G::WSZ / 2;
     float4* Hsb = Hs + 2 * G::HH * G::HS;
-    int bad = pair_phase_a<RHO, HALF, TH, NT>(C0, av0, d0, d1, W2, tid);
-    bad |= pair_phase_a<RHO, HALF, TH, NT>(C1, av1, d0, d1, W2b, tid);
+    int bad = pair_phase_a2<RHO, HALF, TH>(C0, C1, av0, av1, d0, d1, W2, W2b, tid);
     bad = __syncthreads_or(bad);
     const int hrow = tid & 31, hrun = tid >> 5;
     pair_phase_h<RHO, TH, 2>(W2, Rs, Hs, hrow, hrun, bad);
