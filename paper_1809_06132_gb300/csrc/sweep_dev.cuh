@@ -420,10 +420,19 @@ struct Geo {
     // (CG = 2): W and H hold both cameras' samples and sums.
     static constexpr int CG = KP == 2 ? 2 : 1;
     static constexpr int WSZ = KP == 2 ? 2 * HH * WS2 : HH * WS;  // floats of one camera's W
-    // CG x KP H buffers, CG W buffers and R (the direction tables are in TMEM)
+    // KP = 2: one camera's H is [HH][HS] float4 (sw0, sw1, sww0, sww1) and
+    // [HH][HS] float2 (srw0, srw1): HCAM4 float4s; the invalid-sample flags
+    // of a step with invalid samples are bytes F [CG][HH][TW] (bit q: some
+    // sample of plane q's horizontal window is invalid).  KP = 1: KP x
+    // [HH][HS] float4 (sw, sww, srw, invalid count).
+    static constexpr int HCAM4 = HH * HS * 3 / 2;
+    static constexpr int HREG4 = KP == 2 ? CG * HCAM4 : KP * HH * HS;
+    static constexpr int FSZ = KP == 2 ? CG * HH * TW : 0;
+    // H, CG W buffers, R and the flags (the direction tables are in TMEM)
     static constexpr size_t smem(int) {
-        return sizeof(float4) * CG * KP * HH * HS + sizeof(float) * (CG * WSZ + HH * WS);
+        return sizeof(float4) * HREG4 + sizeof(float) * (CG * WSZ + HH * WS) + FSZ;
     }
+    static_assert(HH % 2 == 0, "a camera's H blocks stay 16-byte aligned");
     static_assert(PPT <= 3, "three directions per thread and camera in TMEM");
     static_assert(NTV == TW * (TH / SEG) && TH % 8 == 0 && NTV <= NT, "phase V: one thread per column and row segment");
     static_assert(KP == 1 || KP == 2, "one or two planes per pass");
@@ -473,11 +482,12 @@ __device__ __forceinline__ int pair_phase_a(const CamS& C, const float (&av)[9],
 
 // Phase H: sliding horizontal sums of both planes along run `hrun` of halo
 // row `hrow` (bad: some sample of the tile is invalid), for NC cameras
-// (camera c's samples and sums at W2 + c WSZ / 2 and Hs + 2 c HH HS); the
-// reference samples of the run are loaded once.
+// (camera c's samples at W2 + c WSZ / 2, its sums at Hs + c HCAM4 and, when
+// bad, its flags at Fs + c HH TW); the reference samples of the run are
+// loaded once.
 template <int RHO, int TH, int NC = 1>
-__device__ __forceinline__ void pair_phase_h(const float2* W2, const float* Rs, float4* Hs, int hrow, int hrun,
-                                             int bad) {
+__device__ __forceinline__ void pair_phase_h(const float2* W2, const float* Rs, float4* Hs, unsigned char* Fs,
+                                             int hrow, int hrun, int bad) {
     using G = Geo<RHO, TH, 2>;
     constexpr int HH = G::HH, WS = G::WS, WS2 = G::WS2, HS = G::HS;
     // phase H: sliding horizontal sums of both planes along a run of one halo row
@@ -499,8 +509,9 @@ __device__ __forceinline__ void pair_phase_h(const float2* W2, const float* Rs, 
                 w[2 * qq] = make_float2(a.x, a.y);
                 w[2 * qq + 1] = make_float2(a.z, a.w);
             }
-            float4* ha = Hs + c * 2 * HH * HS + hrow * HS + RUN * hrun;
-            float4* hb = ha + HH * HS;
+            float4* ha = Hs + c * G::HCAM4 + hrow * HS + RUN * hrun;
+            float2* hb = reinterpret_cast<float2*>(Hs + c * G::HCAM4 + HH * HS) + hrow * HS + RUN * hrun;
+            unsigned char* fl = Fs + c * HH * TW + hrow * TW + RUN * hrun;
             float2 sw = dup2(0.f), sww = dup2(0.f), srw = dup2(0.f), sm = dup2(0.f);
             if (!bad) {  // every sample of the tile is valid (the common case)
 #pragma unroll
@@ -510,7 +521,7 @@ __device__ __forceinline__ void pair_phase_h(const float2* W2, const float* Rs, 
                     srw = fma2(dup2(r[t]), w[t], srw);
                 }
                 ha[0] = make_float4(sw.x, sw.y, sww.x, sww.y);
-                hb[0] = make_float4(srw.x, srw.y, 0.f, 0.f);
+                hb[0] = srw;
 #pragma unroll
                 for (int o = 1; o < RUN; ++o) {
                     const int a = o + 2 * RHO, b = o - 1;
@@ -518,7 +529,7 @@ __device__ __forceinline__ void pair_phase_h(const float2* W2, const float* Rs, 
                     sww = add2(sww, fma2(w[a], w[a], mul2(neg2(w[b]), w[b])));
                     srw = add2(srw, fma2(dup2(r[a]), w[a], mul2(dup2(-r[b]), w[b])));
                     ha[o] = make_float4(sw.x, sw.y, sww.x, sww.y);
-                    hb[o] = make_float4(srw.x, srw.y, 0.f, 0.f);
+                    hb[o] = srw;
                 }
             } else {  // invalid samples: excluded from the sums and counted
 #pragma unroll
@@ -531,7 +542,8 @@ __device__ __forceinline__ void pair_phase_h(const float2* W2, const float* Rs, 
                     sm = add2(sm, make_float2(bx ? 1.0f : 0.0f, by ? 1.0f : 0.0f));
                 }
                 ha[0] = make_float4(sw.x, sw.y, sww.x, sww.y);
-                hb[0] = make_float4(srw.x, srw.y, sm.x, sm.y);
+                hb[0] = srw;
+                fl[0] = (unsigned char)((sm.x != 0.0f ? 1 : 0) | (sm.y != 0.0f ? 2 : 0));
 #pragma unroll
                 for (int o = 1; o < RUN; ++o) {
                     const int a = o + 2 * RHO, b = o - 1;
@@ -544,7 +556,8 @@ __device__ __forceinline__ void pair_phase_h(const float2* W2, const float* Rs, 
                     sm = add2(sm, add2(make_float2(ax ? 1.0f : 0.0f, ay ? 1.0f : 0.0f),
                                        neg2(make_float2(bx ? 1.0f : 0.0f, by ? 1.0f : 0.0f))));
                     ha[o] = make_float4(sw.x, sw.y, sww.x, sww.y);
-                    hb[o] = make_float4(srw.x, srw.y, sm.x, sm.y);
+                    hb[o] = srw;
+                    fl[o] = (unsigned char)((sm.x != 0.0f ? 1 : 0) | (sm.y != 0.0f ? 2 : 0));
                 }
             }
         }
@@ -555,31 +568,43 @@ __device__ __forceinline__ void pair_phase_h(const float2* W2, const float* Rs, 
 // output column segment (base_v: its first H entry), ZNCC against the
 // reference statistics st, and the minimum over cameras.
 template <int RHO, int TH>
-__device__ __forceinline__ void pair_phase_v(const float4* Hs, const float2 (&st)[TH / 8], int base_v,
+__device__ __forceinline__ void pair_phase_v(const float4* Hs, const unsigned char* Fs, int bad,
+                                             const float2 (&st)[TH / 8], int base_v, int base_f,
                                              float (&cmin0)[TH / 8], float (&cmin1)[TH / 8]) {
     using G = Geo<RHO, TH, 2>;
     constexpr int SEG = G::SEG, HH = G::HH, HS = G::HS, N = G::N;
     const float4* Ha = Hs;
-    const float4* Hb = Hs + HH * HS;
-    // phase V: sliding vertical sums of both planes down SEG rows, ZNCC, minimum over cameras
-    float2 vs = dup2(0.f), vss = dup2(0.f), vrs = dup2(0.f), vm = dup2(0.f);
+    const float2* Hb = reinterpret_cast<const float2*>(Hs + HH * HS);
+    // phase V: sliding vertical sums of both planes down SEG rows, ZNCC, minimum over cameras;
+    // when some sample of the tile is invalid, f0 / f1 count the flagged rows of the window
+    float2 vs = dup2(0.f), vss = dup2(0.f), vrs = dup2(0.f);
+    int f0 = 0, f1 = 0;
 #pragma unroll
     for (int dy = 0; dy <= 2 * RHO; ++dy) {
-        const float4 a = Ha[base_v + dy * HS], b = Hb[base_v + dy * HS];
+        const float4 a = Ha[base_v + dy * HS];
+        const float2 b = Hb[base_v + dy * HS];
         vs = add2(vs, make_float2(a.x, a.y));
         vss = add2(vss, make_float2(a.z, a.w));
-        vrs = add2(vrs, make_float2(b.x, b.y));
-        vm = add2(vm, make_float2(b.z, b.w));
+        vrs = add2(vrs, b);
+        if (bad) {
+            const int f = Fs[base_f + dy * TW];
+            f0 += f & 1;
+            f1 += f >> 1;
+        }
     }
 #pragma unroll
     for (int i = 0; i < SEG; ++i) {
         if (i > 0) {
-            const float4 a = Ha[base_v + (i + 2 * RHO) * HS], b = Hb[base_v + (i + 2 * RHO) * HS];
-            const float4 c = Ha[base_v + (i - 1) * HS], d = Hb[base_v + (i - 1) * HS];
+            const float4 a = Ha[base_v + (i + 2 * RHO) * HS], c = Ha[base_v + (i - 1) * HS];
+            const float2 b = Hb[base_v + (i + 2 * RHO) * HS], d = Hb[base_v + (i - 1) * HS];
             vs = add2(vs, add2(make_float2(a.x, a.y), make_float2(-c.x, -c.y)));
             vss = add2(vss, add2(make_float2(a.z, a.w), make_float2(-c.z, -c.w)));
-            vrs = add2(vrs, add2(make_float2(b.x, b.y), make_float2(-d.x, -d.y)));
-            vm = add2(vm, add2(make_float2(b.z, b.w), make_float2(-d.z, -d.w)));
+            vrs = add2(vrs, add2(b, neg2(d)));
+            if (bad) {
+                const int fa = Fs[base_f + (i + 2 * RHO) * TW], fc = Fs[base_f + (i - 1) * TW];
+                f0 += (fa & 1) - (fc & 1);
+                f1 += (fa >> 1) - (fc >> 1);
+            }
         }
         const float2 var_w = fma2(mul2(neg2(vs), dup2(1.0f / (float)N)), vs, vss);
         const float2 cov = fma2(dup2(-st[i].x), vs, vrs);
@@ -587,8 +612,8 @@ __device__ __forceinline__ void pair_phase_v(const float4* Hs, const float2 (&st
         const float2 z = make_float2(fminf(1.0f, fmaxf(-1.0f, zr.x)), fminf(1.0f, fmaxf(-1.0f, zr.y)));  // |ZNCC| <= 1
         const float2 cost = fma2(dup2(-0.5f), z, dup2(0.5f));
         const bool ref_ok = !isnan(st[i].y);
-        const bool ok0 = vm.x == 0.0f && var_w.x >= (float)N * 1e-8f && ref_ok;
-        const bool ok1 = vm.y == 0.0f && var_w.y >= (float)N * 1e-8f && ref_ok;
+        const bool ok0 = f0 == 0 && var_w.x >= (float)N * 1e-8f && ref_ok;
+        const bool ok1 = f1 == 0 && var_w.y >= (float)N * 1e-8f && ref_ok;
         cmin0[i] = ok0 ? fminf(cmin0[i], cost.x) : cmin0[i];
         cmin1[i] = ok1 ? fminf(cmin1[i], cost.y) : cmin1[i];
     }
@@ -596,16 +621,16 @@ __device__ __forceinline__ void pair_phase_v(const float4* Hs, const float2 (&st
 
 template <int RHO, bool HALF, int TH>
 __device__ __forceinline__ void pair_pass(const CamS& C, const float (&av)[9], float d0, float d1, float2* W2,
-                                          const float* Rs, float4* Hs, const float2 (&st)[TH / 8], int base_v,
-                                          float (&cmin0)[TH / 8], float (&cmin1)[TH / 8]) {
+                                          const float* Rs, float4* Hs, unsigned char* Fs, const float2 (&st)[TH / 8],
+                                          int base_v, int base_f, float (&cmin0)[TH / 8], float (&cmin1)[TH / 8]) {
     const int tid = threadIdx.x;
     int bad = pair_phase_a<RHO, HALF, TH, NT>(C, av, d0, d1, W2, tid);
     bad = __syncthreads_or(bad);
     using G = Geo<RHO, TH, 2>;
     const int hrow = tid & 31, hrun = tid >> 5;
-    if (hrow < G::HH && hrun < TW / RUN) pair_phase_h<RHO, TH>(W2, Rs, Hs, hrow, hrun, bad);
+    if (hrow < G::HH && hrun < TW / RUN) pair_phase_h<RHO, TH>(W2, Rs, Hs, Fs, hrow, hrun, bad);
     __syncthreads();
-    if (tid < NTV) pair_phase_v<RHO, TH>(Hs, st, base_v, cmin0, cmin1);
+    if (tid < NTV) pair_phase_v<RHO, TH>(Hs, Fs, bad, st, base_v, base_f, cmin0, cmin1);
 }
 
 // Two matching cameras in one step (the second camera's samples and sums in
@@ -646,20 +671,20 @@ __device__ __forceinline__ int pair_phase_a2(const CamS& C0, const CamS& C1, con
 template <int RHO, bool HALF, int TH>
 __device__ __forceinline__ void pair_pass2(const CamS& C0, const CamS& C1, const float (&av0)[9], const float (&av1)[9],
                                            float d0, float d1, float2* W2, const float* Rs, float4* Hs,
-                                           const float2 (&st)[TH / 8], int base_v, float (&cmin0)[TH / 8],
-                                           float (&cmin1)[TH / 8]) {
+                                           unsigned char* Fs, const float2 (&st)[TH / 8], int base_v, int base_f,
+                                           float (&cmin0)[TH / 8], float (&cmin1)[TH / 8]) {
     using G = Geo<RHO, TH, 2>;
     const int tid = threadIdx.x;
     float2* W2b = W2 + G::WSZ / 2;
-    float4* Hsb = Hs + 2 * G::HH * G::HS;
+    float4* Hsb = Hs + G::HCAM4;
     int bad = pair_phase_a2<RHO, HALF, TH>(C0, C1, av0, av1, d0, d1, W2, W2b, tid);
     bad = __syncthreads_or(bad);
     const int hrow = tid & 31, hrun = tid >> 5;
-    pair_phase_h<RHO, TH, 2>(W2, Rs, Hs, hrow, hrun, bad);
+    pair_phase_h<RHO, TH, 2>(W2, Rs, Hs, Fs, hrow, hrun, bad);
     __syncthreads();
     if (tid < NTV) {
-        pair_phase_v<RHO, TH>(Hs, st, base_v, cmin0, cmin1);
-        pair_phase_v<RHO, TH>(Hsb, st, base_v, cmin0, cmin1);
+        pair_phase_v<RHO, TH>(Hs, Fs, bad, st, base_v, base_f, cmin0, cmin1);
+        pair_phase_v<RHO, TH>(Hsb, Fs + G::HH * TW, bad, st, base_v, base_f, cmin0, cmin1);
     }
 }
 
@@ -834,10 +859,11 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
     const int tile = item / L.n_chunks, chunk = item - tile * L.n_chunks;
     const int k_lo = L.k_begin + chunk * L.chunk, k_hi = min(L.k_end, k_lo + L.chunk);
     constexpr int HH = G::HH, HWL = G::HWL, WS = G::WS, HS = G::HS, NPOS = G::NPOS, N = G::N;
-    float4* Hs = reinterpret_cast<float4*>(smem_raw);            // [CG][KP][HH][HS] window sums
-    float* Ws = reinterpret_cast<float*>(Hs + G::CG * KP * HH * HS);  // [CG] warped samples (NaN = invalid): KP = 1
+    float4* Hs = reinterpret_cast<float4*>(smem_raw);            // window sums (layout: Geo)
+    float* Ws = reinterpret_cast<float*>(Hs + G::HREG4);          // [CG] warped samples (NaN = invalid): KP = 1
     float2* W2 = reinterpret_cast<float2*>(Ws);                   //   [HH][WS], KP = 2 [HH][WS2] pairs (k0, k0 + 1)
     float* Rs = Ws + G::CG * G::WSZ;                              // [HH][WS] reference intensities
+    unsigned char* Fs = reinterpret_cast<unsigned char*>(Rs + HH * WS);  // KP = 2: invalid-sample flags
     const int tid = threadIdx.x;
     const int tx = tile % L.tiles_x, ty = tile / L.tiles_x;
     const int gx0 = tx * TW - RHO, gy0 = ty * TH - RHO;
@@ -877,6 +903,7 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
     }
     const int hrow = tid & 31, hrun = tid >> 5;  // phase H item
     const int base_v = oy0 * HS + ox;            // phase V first H entry
+    const int base_f = oy0 * TW + ox;            // phase V first flag (KP = 2)
 
     for (int s = 0; s < L.n_sets; ++s) {
         const int s_lo = max(L.sets[s].start, k_lo), k_end = min(L.sets[s].start + L.sets[s].count, k_hi);
@@ -934,11 +961,11 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
                     if (j + 1 < L.n_cams) {  // two cameras in one step
                         float av1[9];
                         tm_ld9(tm + TM_TAB + 9 * (j + 1), av1);
-                        pair_pass2<RHO, HALF, TH>(C, cams[j + 1], av, av1, d0, d1, W2, Rs, Hs, st, base_v, cmin[0],
-                                                  cmin[1]);
+                        pair_pass2<RHO, HALF, TH>(C, cams[j + 1], av, av1, d0, d1, W2, Rs, Hs, Fs, st, base_v,
+                                                  base_f, cmin[0], cmin[1]);
                         ++j;
                     } else {
-                        pair_pass<RHO, HALF, TH>(C, av, d0, d1, W2, Rs, Hs, st, base_v, cmin[0], cmin[1]);
+                        pair_pass<RHO, HALF, TH>(C, av, d0, d1, W2, Rs, Hs, Fs, st, base_v, base_f, cmin[0], cmin[1]);
                     }
                 } else {
                     // phase A: warped samples of the tile + halo for the plane
