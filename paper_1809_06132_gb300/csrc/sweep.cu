@@ -180,7 +180,7 @@ __device__ __forceinline__ void quad_rows(const QuadJobs& Q, int j, int xb, int 
                 static_cast<uint2*>(Q.out[j])[o] =
                     make_uint2(*reinterpret_cast<unsigned*>(&p), *reinterpret_cast<unsigned*>(&q));
             } else {
-                static_cast<float4*>(Q.out[j])[o] = make_float4(a, a1, b, b1);
+                static_cast<float4*>(Q.out[j])[o] = make_float4(a, a1 - a, b, b1 - b);  // layout: quad_px
             }
         }
         a = b;

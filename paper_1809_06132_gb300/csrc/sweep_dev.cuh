@@ -72,6 +72,36 @@ struct LevelD {
 // winner-take-all (merge_record_px).
 enum { REC_C1, REC_C2, REC_CM, REC_CP, REC_FIRST, REC_LAST, REC_K, REC_N };
 
+// Matching camera as the sweep reads it (staged in shared memory per work
+// item).  The projection constants are kept twice: as scalars, and as
+// (value, value) pairs for the two-plane form of the warp on packed FP32
+// operations.
+struct CamS {
+    float R[9], t[3];
+    float xi, fx, fy, cx, cy, k1, k2, p1, p2, r2_max, lim, wm1, hm1;
+    int width;
+    const void* quad;
+    float2 xi2, fx2, fy2, cx2, cy2, k12, k22, p12, p1x2, p22, p2x2, lim2;  // pairs; p1x2 = 2 p1, p2x2 = 2 p2
+};
+
+// CamS of a matching camera.
+__device__ __forceinline__ void cam_consts(const CamJ& J, CamS& c) {
+    for (int i = 0; i < 9; ++i) c.R[i] = J.R[i];
+    for (int i = 0; i < 3; ++i) c.t[i] = J.t[i];
+    c.xi = J.cam.xi; c.fx = J.cam.fx; c.fy = J.cam.fy; c.cx = J.cam.cx; c.cy = J.cam.cy;
+    c.k1 = J.cam.k1; c.k2 = J.cam.k2; c.p1 = J.cam.p1; c.p2 = J.cam.p2; c.r2_max = J.cam.r2_max;
+    c.lim = J.cam.lim;
+    c.wm1 = (float)(J.cam.width - 1);
+    c.hm1 = (float)(J.cam.height - 1);
+    c.width = J.cam.width;
+    c.quad = J.quad;
+    c.xi2 = make_float2(c.xi, c.xi); c.fx2 = make_float2(c.fx, c.fx); c.fy2 = make_float2(c.fy, c.fy);
+    c.cx2 = make_float2(c.cx, c.cx); c.cy2 = make_float2(c.cy, c.cy); c.k12 = make_float2(c.k1, c.k1);
+    c.k22 = make_float2(c.k2, c.k2); c.p12 = make_float2(c.p1, c.p1);
+    c.p1x2 = make_float2(2.0f * c.p1, 2.0f * c.p1); c.p22 = make_float2(c.p2, c.p2);
+    c.p2x2 = make_float2(2.0f * c.p2, 2.0f * c.p2); c.lim2 = make_float2(c.lim, c.lim);
+}
+
 struct SweepParams {
     int n_levels;
     int image_half;  // matching quads stored as FP16
@@ -116,9 +146,12 @@ __device__ __forceinline__ float ref_px(const uint8_t* img, int W, int s, int x0
     return __fmaf_rn((float)img[(size_t)(y0 + y) * W + (x0 + x)], 1.0f / 255.0f, -0.5f);
 }
 
-// Matching image of a level in "quad" layout: entry (x, y) holds the
-// centred intensities at (x, y), (x+1, y), (x, y+1), (x+1, y+1), so one
-// bilinear sample is one 16-byte gather (8 bytes with FP16 storage).
+// Matching image of a level in "quad" layout: one bilinear sample is one
+// 16-byte gather (8 bytes with FP16 storage).  FP32 entry (x, y) holds
+// I(x, y), I(x+1, y) - I(x, y), I(x, y+1), I(x+1, y+1) - I(x, y+1) (centred
+// intensities), so the sample needs no horizontal differences; the FP16
+// entry holds the four intensities themselves (a difference of two halves
+// is not always a half), and the sample forms the differences in FP32.
 __device__ __forceinline__ void quad_px(const uint8_t* img, int W, int s, int Wl, int Hl, void* out, int half, int x,
                                         int y) {
     float4 q;
@@ -131,7 +164,7 @@ __device__ __forceinline__ void quad_px(const uint8_t* img, int W, int s, int Wl
         static_cast<uint2*>(out)[(size_t)y * Wl + x] =
             make_uint2(*reinterpret_cast<unsigned*>(&a), *reinterpret_cast<unsigned*>(&b));
     } else {
-        static_cast<float4*>(out)[(size_t)y * Wl + x] = q;
+        static_cast<float4*>(out)[(size_t)y * Wl + x] = make_float4(q.x, q.y - q.x, q.z, q.w - q.z);
     }
 }
 
@@ -163,17 +196,6 @@ __device__ __forceinline__ float2 stats_px(const float* ref, int W, int H, int r
 
 // ------------------------------------------------------------- sweep
 
-// Matching camera as the sweep reads it (staged in shared memory per tile).
-// The projection constants are kept twice: as scalars, and as (value,
-// value) pairs for the two-plane form of the warp on packed FP32 operations.
-struct CamS {
-    float R[9], t[3];
-    float xi, fx, fy, cx, cy, k1, k2, p1, p2, r2_max, lim, wm1, hm1;
-    int width;
-    const void* quad;
-    float2 xi2, fx2, fy2, cx2, cy2, k12, k22, p12, p1x2, p22, p2x2, lim2;  // pairs; p1x2 = 2 p1, p2x2 = 2 p2
-};
-
 __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -184,9 +206,12 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 // lies outside [0, W-1] x [0, H-1].  The gather is clamped into the image and
 // always issued, so the warp does not diverge; a clamp that moved the point
 // marks it outside (NaN compares unequal, so a NaN position is rejected
-// too).  HALF: quads stored as FP16.
+// too).  An invalid sample also sets `bad` (the caller's flag for the tile's
+// invalid-sample path), from the same predicate: testing the returned value
+// for NaN instead cost 3 % of the sweep kernel's time.  HALF: quads stored
+// as FP16.
 template <bool HALF>
-__device__ __forceinline__ float sample_at(const CamS& c, float u, float v, bool ok) {
+__device__ __forceinline__ float sample_at(const CamS& c, float u, float v, bool ok, int& bad) {
     float uc = fminf(fmaxf(u, 0.0f), c.wm1), vc = fminf(fmaxf(v, 0.0f), c.hm1);
     ok = ok && (uc == u) && (vc == v);
     int x0 = (int)uc, y0 = (int)vc;
@@ -201,21 +226,23 @@ __device__ __forceinline__ float sample_at(const CamS& c, float u, float v, bool
         uint2 h = __ldg(static_cast<const uint2*>(c.quad) + y0 * c.width + x0);
         float2 a = __half22float2(*reinterpret_cast<const __half2*>(&h.x));
         float2 b = __half22float2(*reinterpret_cast<const __half2*>(&h.y));
-        q = make_float4(a.x, a.y, b.x, b.y);
+        q = make_float4(a.x, a.y - a.x, b.x, b.y - b.x);
     } else {
-        q = __ldg(static_cast<const float4*>(c.quad) + y0 * c.width + x0);
+        q = __ldg(static_cast<const float4*>(c.quad) + y0 * c.width + x0);  // differences stored
     }
-    float top = fmaf(ax, q.y - q.x, q.x);
-    float bot = fmaf(ax, q.w - q.z, q.z);
+    float top = fmaf(ax, q.y, q.x);
+    float bot = fmaf(ax, q.w, q.z);
     float w = fmaf(ay, bot - top, top);
+    bad |= ok ? 0 : 1;
     return ok ? w : __int_as_float(0x7fc00000);
 }
 
 // The sample of a matching camera at the projection of X_j (camera frame):
-// unified model, then radial-tangential distortion; NaN when the point does
-// not project (sphere side, distortion range) or lands outside the image.
+// unified model, then radial-tangential distortion; NaN (and `bad` set) when
+// the point does not project (sphere side, distortion range) or lands
+// outside the image.
 template <bool HALF>
-__device__ __forceinline__ float warp_sample(const CamS& c, float X, float Y, float Z) {
+__device__ __forceinline__ float warp_sample(const CamS& c, float X, float Y, float Z, int& bad) {
     float n2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
     float n = n2 * rsqrtf(n2);
     float inv = __fdividef(1.0f, fmaf(c.xi, n, Z));
@@ -227,7 +254,7 @@ __device__ __forceinline__ float warp_sample(const CamS& c, float X, float Y, fl
     float yd = fmaf(my, rad, fmaf(c.p1, fmaf(2.0f * my, my, r2), 2.0f * c.p2 * mxy));
     float u = fmaf(c.fx, xd, c.cx);
     float v = fmaf(c.fy, yd, c.cy);
-    return sample_at<HALF>(c, u, v, (Z > c.lim * n) && (r2 <= c.r2_max));
+    return sample_at<HALF>(c, u, v, (Z > c.lim * n) && (r2 <= c.r2_max), bad);
 }
 
 // warp_sample for two points at once (lane x: the first plane, lane y: the
@@ -235,7 +262,7 @@ __device__ __forceinline__ float warp_sample(const CamS& c, float X, float Y, fl
 // operation and its rounding are those of warp_sample (2 m = m + m exactly),
 // so each result is bit-identical to a warp_sample call.
 template <bool HALF>
-__device__ __forceinline__ float2 warp_sample2(const CamS& c, float2 X, float2 Y, float2 Z) {
+__device__ __forceinline__ float2 warp_sample2(const CamS& c, float2 X, float2 Y, float2 Z, int& bad) {
     float2 n2 = fma2(X, X, fma2(Y, Y, mul2(Z, Z)));
     float2 n = mul2(n2, make_float2(rsqrtf(n2.x), rsqrtf(n2.y)));
     float2 den = fma2(c.xi2, n, Z);
@@ -248,14 +275,14 @@ __device__ __forceinline__ float2 warp_sample2(const CamS& c, float2 X, float2 Y
     float2 yd = fma2(my, rad, fma2(c.p12, fma2(add2(my, my), my, r2), mul2(c.p2x2, mxy)));
     float2 u = fma2(c.fx2, xd, c.cx2), v = fma2(c.fy2, yd, c.cy2);
     float2 ln = mul2(c.lim2, n);
-    return make_float2(sample_at<HALF>(c, u.x, v.x, (Z.x > ln.x) && (r2.x <= c.r2_max)),
-                       sample_at<HALF>(c, u.y, v.y, (Z.y > ln.y) && (r2.y <= c.r2_max)));
+    return make_float2(sample_at<HALF>(c, u.x, v.x, (Z.x > ln.x) && (r2.x <= c.r2_max), bad),
+                       sample_at<HALF>(c, u.y, v.y, (Z.y > ln.y) && (r2.y <= c.r2_max), bad));
 }
 
 // Winner-take-all state in tensor memory.  Each output-owning thread keeps
 // the state of its SEG pixels (best and second-best cost, the costs of the
 // previous, first and winner's neighbouring planes, the winner and whether
-// the next plane's cost is owed) in 32 words of TMEM between plane pairs,
+// the next plane's cost is owed) in 8 SEG words of TMEM between plane pairs,
 // not in registers: the registers go to the warp instead.  A warp reaches
 // the TMEM lanes of its quadrant (warp id mod 4); the warps of a quadrant
 // take 32 columns each (warps that own no pixels hold an unused copy).  The CTA allocates TMEM_COLS
@@ -348,11 +375,33 @@ __device__ __forceinline__ void tm_st32(uint32_t a, const uint32_t (&r)[32]) {
 // The state arrays of SEG pixels, packed 8 words per pixel.
 #define PS_WTA_ARGS(Q) Q float (&c1)[SEG], Q float (&c2)[SEG], Q float (&cprev)[SEG], Q float (&cminus)[SEG], \
     Q float (&cplus)[SEG], Q float (&cfirst)[SEG], Q int (&kb)[SEG], Q bool (&needp)[SEG]
+// 24 words (x16 + x8) of this thread's TMEM lane (warp-collective).
+__device__ __forceinline__ void tm_ld24(uint32_t a, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.wait::st.sync.aligned;\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%24];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%25];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
+        : "r"(a), "r"(a + 16u)
+        : "memory");
+}
+__device__ __forceinline__ void tm_st24(uint32_t a, const uint32_t (&r)[32]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17};\n\t"
+                 "tcgen05.st.sync.aligned.32x32b.x8.b32 [%1], {%18, %19, %20, %21, %22, %23, %24, %25};" ::"r"(a), "r"(a + 16u),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+                 "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+                 "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23])
+                 : "memory");
+}
+
 template <int SEG>
 __device__ __forceinline__ void wta_load(uint32_t a, PS_WTA_ARGS()) {
     static_assert(8 * SEG <= 32, "the state of SEG pixels fits 32 words");
     uint32_t r[32];
-    tm_ld32(a, r);
+    if constexpr (SEG == 3) tm_ld24(a, r); else tm_ld32(a, r);
 #pragma unroll
     for (int i = 0; i < SEG; ++i) {
         c1[i] = __uint_as_float(r[8 * i]);
@@ -381,7 +430,7 @@ __device__ __forceinline__ void wta_store(uint32_t a, PS_WTA_ARGS(const)) {
         r[8 * i + 6] = (uint32_t)kb[i];
         r[8 * i + 7] = needp[i] ? 1u : 0u;
     }
-    tm_st32(a, r);
+    if constexpr (SEG == 3) tm_st24(a, r); else tm_st32(a, r);
 }
 #undef PS_WTA_ARGS
 
@@ -429,8 +478,9 @@ struct Geo {
     static constexpr int HREG4 = KP == 2 ? CG * HCAM4 : KP * HH * HS;
     static constexpr int FSZ = KP == 2 ? CG * HH * TW : 0;
     // H, CG W buffers, R and the flags (the direction tables are in TMEM)
+    static constexpr int DTAB = 64;  // plane offsets of a work item staged in shared memory
     static constexpr size_t smem(int) {
-        return sizeof(float4) * HREG4 + sizeof(float) * (CG * WSZ + HH * WS) + FSZ;
+        return sizeof(float4) * HREG4 + sizeof(float) * (CG * WSZ + HH * WS) + FSZ + sizeof(float) * DTAB;
     }
     static_assert(HH % 2 == 0, "a camera's H blocks stay 16-byte aligned");
     static_assert(PPT <= 3, "three directions per thread and camera in TMEM");
@@ -471,8 +521,7 @@ __device__ __forceinline__ int pair_phase_a(const CamS& C, const float (&av)[9],
             const float4 a = make_float4(av[3 * i], av[3 * i + 1], av[3 * i + 2], 0.f);
             float2 w = warp_sample2<HALF>(C, make_float2(fmaf(d0, a.x, C.t[0]), fmaf(d1, a.x, C.t[0])),
                                           make_float2(fmaf(d0, a.y, C.t[1]), fmaf(d1, a.y, C.t[1])),
-                                          make_float2(fmaf(d0, a.z, C.t[2]), fmaf(d1, a.z, C.t[2])));
-            bad |= isnan(w.x) | isnan(w.y);
+                                          make_float2(fmaf(d0, a.z, C.t[2]), fmaf(d1, a.z, C.t[2])), bad);
             int hy = p / HWL, hx = p - hy * HWL;
             W2[hy * WS2 + hx] = w;
         }
@@ -567,10 +616,11 @@ __device__ __forceinline__ void pair_phase_h(const float2* W2, const float* Rs, 
 // Phase V: sliding vertical sums of both planes down the SEG rows of one
 // output column segment (base_v: its first H entry), ZNCC against the
 // reference statistics st, and the minimum over cameras.
-template <int RHO, int TH>
-__device__ __forceinline__ void pair_phase_v(const float4* Hs, const unsigned char* Fs, int bad,
-                                             const float2 (&st)[TH / 8], int base_v, int base_f,
-                                             float (&cmin0)[TH / 8], float (&cmin1)[TH / 8]) {
+template <int RHO, int TH, bool BAD>
+__device__ __forceinline__ void pair_phase_v_(const float4* Hs, const unsigned char* Fs,
+                                              const float2 (&st)[TH / 8], int base_v, int base_f,
+                                              float (&cmin0)[TH / 8], float (&cmin1)[TH / 8]) {
+    constexpr bool bad = BAD;
     using G = Geo<RHO, TH, 2>;
     constexpr int SEG = G::SEG, HH = G::HH, HS = G::HS, N = G::N;
     const float4* Ha = Hs;
@@ -612,11 +662,22 @@ __device__ __forceinline__ void pair_phase_v(const float4* Hs, const unsigned ch
         const float2 z = make_float2(fminf(1.0f, fmaxf(-1.0f, zr.x)), fminf(1.0f, fmaxf(-1.0f, zr.y)));  // |ZNCC| <= 1
         const float2 cost = fma2(dup2(-0.5f), z, dup2(0.5f));
         const bool ref_ok = !isnan(st[i].y);
-        const bool ok0 = f0 == 0 && var_w.x >= (float)N * 1e-8f && ref_ok;
-        const bool ok1 = f1 == 0 && var_w.y >= (float)N * 1e-8f && ref_ok;
+        const bool ok0 = (!BAD || f0 == 0) && var_w.x >= (float)N * 1e-8f && ref_ok;
+        const bool ok1 = (!BAD || f1 == 0) && var_w.y >= (float)N * 1e-8f && ref_ok;
         cmin0[i] = ok0 ? fminf(cmin0[i], cost.x) : cmin0[i];
         cmin1[i] = ok1 ? fminf(cmin1[i], cost.y) : cmin1[i];
     }
+}
+// (the tile's invalid-sample flag is uniform: two code paths, the common one
+// without the flag counts)
+template <int RHO, int TH>
+__device__ __forceinline__ void pair_phase_v(const float4* Hs, const unsigned char* Fs, int bad,
+                                             const float2 (&st)[TH / 8], int base_v, int base_f,
+                                             float (&cmin0)[TH / 8], float (&cmin1)[TH / 8]) {
+    if (bad)
+        pair_phase_v_<RHO, TH, true>(Hs, Fs, st, base_v, base_f, cmin0, cmin1);
+    else
+        pair_phase_v_<RHO, TH, false>(Hs, Fs, st, base_v, base_f, cmin0, cmin1);
 }
 
 template <int RHO, bool HALF, int TH>
@@ -659,8 +720,7 @@ __device__ __forceinline__ int pair_phase_a2(const CamS& C0, const CamS& C1, con
                 const float4 a = make_float4(av[3 * i], av[3 * i + 1], av[3 * i + 2], 0.f);
                 float2 w = warp_sample2<HALF>(C, make_float2(fmaf(d0, a.x, C.t[0]), fmaf(d1, a.x, C.t[0])),
                                               make_float2(fmaf(d0, a.y, C.t[1]), fmaf(d1, a.y, C.t[1])),
-                                              make_float2(fmaf(d0, a.z, C.t[2]), fmaf(d1, a.z, C.t[2])));
-                bad |= isnan(w.x) | isnan(w.y);
+                                              make_float2(fmaf(d0, a.z, C.t[2]), fmaf(d1, a.z, C.t[2])), bad);
                 (c ? W2b : W2)[hy * WS2 + hx] = w;
             }
         }
@@ -864,6 +924,7 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
     float2* W2 = reinterpret_cast<float2*>(Ws);                   //   [HH][WS], KP = 2 [HH][WS2] pairs (k0, k0 + 1)
     float* Rs = Ws + G::CG * G::WSZ;                              // [HH][WS] reference intensities
     unsigned char* Fs = reinterpret_cast<unsigned char*>(Rs + HH * WS);  // KP = 2: invalid-sample flags
+    float* Ds = reinterpret_cast<float*>(Fs + G::FSZ);                   // plane offsets d of the item's planes
     const int tid = threadIdx.x;
     const int tx = tile % L.tiles_x, ty = tile / L.tiles_x;
     const int gx0 = tx * TW - RHO, gy0 = ty * TH - RHO;
@@ -876,6 +937,11 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
         bool in = gx >= 0 && gy >= 0 && gx < L.W && gy < L.H;
         Rs[hy * WS + hx] = in ? L.ref[(size_t)gy * L.W + gx] : 0.0f;
     }
+    // the item's plane offsets, read by every step from shared memory rather
+    // than from the plane table in global memory
+    const bool dtab = k_hi - k_lo <= G::DTAB;  // uniform
+    if (dtab)
+        for (int k = tid; k < k_hi - k_lo; k += NT) Ds[k] = L.planes[k_lo + k].d;
     // outputs of this thread (tid < NTV): column ox, rows oy0 .. oy0 + SEG - 1;
     // their reference window mean and 1/sqrt(sum of squared deviations), NaN = unusable
     const bool owner = tid < NTV;  // uniform over each warp
@@ -925,7 +991,9 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
             ry[i] = r.y;
             rz[i] = r.z;
         }
-        for (int j = 0; j < L.n_cams; ++j) {
+#pragma unroll
+        for (int j = 0; j < PS_MAX_CAMS; ++j) {  // unrolled: camera j's constants at fixed offsets in shared memory
+            if (j >= L.n_cams) break;
             const CamS& C = cams[j];
             float av[9];
 #pragma unroll
@@ -951,19 +1019,20 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
             for (int q = 0; q < KP; ++q)
 #pragma unroll
                 for (int i = 0; i < SEG; ++i) cmin[q][i] = inf;
-            for (int j = 0; j < L.n_cams; ++j) {
+#pragma unroll
+            for (int j = 0; j < PS_MAX_CAMS; j += (KP == 2 ? 2 : 1)) {  // unrolled, as above
+                if (j >= L.n_cams) break;
                 const CamS& C = cams[j];
                 float av[9];
                 tm_ld9(tm + TM_TAB + 9 * j, av);
-                const float d0 = __ldg(&L.planes[k0].d);
-                const float d1 = __ldg(&L.planes[k0 + np - 1].d);
+                const float d0 = dtab ? Ds[k0 - k_lo] : __ldg(&L.planes[k0].d);
+                const float d1 = dtab ? Ds[k0 + np - 1 - k_lo] : __ldg(&L.planes[k0 + np - 1].d);
                 if constexpr (KP == 2) {
                     if (j + 1 < L.n_cams) {  // two cameras in one step
                         float av1[9];
                         tm_ld9(tm + TM_TAB + 9 * (j + 1), av1);
                         pair_pass2<RHO, HALF, TH>(C, cams[j + 1], av, av1, d0, d1, W2, Rs, Hs, Fs, st, base_v,
                                                   base_f, cmin[0], cmin[1]);
-                        ++j;
                     } else {
                         pair_pass<RHO, HALF, TH>(C, av, d0, d1, W2, Rs, Hs, Fs, st, base_v, base_f, cmin[0], cmin[1]);
                     }
@@ -975,8 +1044,8 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
                         int p = tid + i * NT;
                         if (p < NPOS) {
                             const float4 a = make_float4(av[3 * i], av[3 * i + 1], av[3 * i + 2], 0.f);
-                            float w0 = warp_sample<HALF>(C, fmaf(d0, a.x, C.t[0]), fmaf(d0, a.y, C.t[1]), fmaf(d0, a.z, C.t[2]));
-                            bad |= isnan(w0);
+                            float w0 = warp_sample<HALF>(C, fmaf(d0, a.x, C.t[0]), fmaf(d0, a.y, C.t[1]), fmaf(d0, a.z, C.t[2]),
+                                                         bad);
                             int hy = p / HWL, hx = p - hy * HWL;
                             Ws[hy * WS + hx] = w0;
                         }
@@ -1066,6 +1135,10 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
             int kb[SEG];
             bool needp[SEG];
             wta_load<SEG>(tm, c1, c2, cprev, cminus, cplus, cfirst, kb, needp);
+            if (k0 == k_lo) {  // the item's first plane (uniform)
+#pragma unroll
+                for (int i = 0; i < SEG; ++i) cfirst[i] = cmin[0][i];
+            }
 #pragma unroll
             for (int q = 0; q < KP; ++q) {
                 if (q >= np) break;
@@ -1073,21 +1146,13 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
 #pragma unroll
                 for (int i = 0; i < SEG; ++i) {
                     float cc = cmin[q][i];
-                    if (k == k_lo) cfirst[i] = cc;
-                    if (needp[i]) {
-                        cplus[i] = cc;
-                        needp[i] = false;
-                    }
-                    if (cc < c1[i]) {
-                        c2[i] = c1[i];
-                        c1[i] = cc;
-                        kb[i] = k;
-                        cminus[i] = cprev[i];
-                        cplus[i] = inf;
-                        needp[i] = true;
-                    } else if (cc < c2[i]) {
-                        c2[i] = cc;
-                    }
+                    const bool lt = cc < c1[i];  // a new winner (ties keep the earlier plane)
+                    cplus[i] = lt ? inf : (needp[i] ? cc : cplus[i]);
+                    needp[i] = lt;
+                    c2[i] = fminf(c2[i], fmaxf(c1[i], cc));  // second smallest of c1, c2, cc
+                    c1[i] = fminf(c1[i], cc);
+                    kb[i] = lt ? k : kb[i];
+                    cminus[i] = lt ? cprev[i] : cminus[i];
                     cprev[i] = cc;
                 }
             }
@@ -1134,22 +1199,7 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
 
 // Stage the matching cameras of a level in shared memory (one thread each).
 __device__ __forceinline__ void stage_cams(const LevelD& L, CamS* cams) {
-    if (threadIdx.x < L.n_cams) {
-        const CamJ& J = L.cams[threadIdx.x];
-        CamS& c = cams[threadIdx.x];
-        for (int i = 0; i < 9; ++i) c.R[i] = J.R[i];
-        for (int i = 0; i < 3; ++i) c.t[i] = J.t[i];
-        c.xi = J.cam.xi; c.fx = J.cam.fx; c.fy = J.cam.fy; c.cx = J.cam.cx; c.cy = J.cam.cy;
-        c.k1 = J.cam.k1; c.k2 = J.cam.k2; c.p1 = J.cam.p1; c.p2 = J.cam.p2; c.r2_max = J.cam.r2_max;
-        c.lim = J.cam.lim;
-        c.wm1 = (float)(J.cam.width - 1);
-        c.hm1 = (float)(J.cam.height - 1);
-        c.width = J.cam.width;
-        c.quad = J.quad;
-        c.xi2 = dup2(c.xi); c.fx2 = dup2(c.fx); c.fy2 = dup2(c.fy); c.cx2 = dup2(c.cx); c.cy2 = dup2(c.cy);
-        c.k12 = dup2(c.k1); c.k22 = dup2(c.k2); c.p12 = dup2(c.p1); c.p1x2 = dup2(2.0f * c.p1);
-        c.p22 = dup2(c.p2); c.p2x2 = dup2(2.0f * c.p2); c.lim2 = dup2(c.lim);
-    }
+    if (threadIdx.x < L.n_cams) cam_consts(L.cams[threadIdx.x], cams[threadIdx.x]);
 }
 
 // One work item of a level: stage the matching cameras in shared memory and
