@@ -419,6 +419,7 @@ def run_ours(args):
     ms_per_step = ms / args.steps
     value = world * args.steps / (ms / 1e3)
     n_blocks = T.count(stream)
+    n_listed = T.listed(stream)  # the last timed frame's visible-block list
     # rays the allocation stage walks per frame: pixels with a depth in the
     # merged, masked maps of the timed frames (counted after the timing)
     rays = []
@@ -511,6 +512,10 @@ def run_ours(args):
                  "ms_stages": {"depth_max": tsdf_ms[0] / max(1, n_ts), "alloc": tsdf_ms[1] / max(1, n_ts),
                                "visible": tsdf_ms[2] / max(1, n_ts), "integrate": integ_ms},
                  "blocks_allocated": n_blocks, "status": st,
+                 "integrate_bw": {"listed_blocks": n_listed,
+                                  "gbs": n_listed * 512 * BYTES_PER_VOXEL / (integ_ms * 1e-3) / 1e9 if integ_ms else None,
+                                  "note": "16 B per voxel of the last timed frame's listed blocks over the mean "
+                                          "integrate time per frame (the listed count varies little between frames)"},
                  "alloc": {"rays_per_frame": rays_per_frame,
                            "rays_per_s": rays_per_frame / (tsdf_ms[1] / max(1, n_ts) * 1e-3),
                            "note": "segments [d - mu, d + mu] walked by the allocation stage per second"}},

@@ -264,6 +264,14 @@ int tsdf_integrate(tsdf_t* t, const float* depth, const ps_pose* world_to_cam, c
  * the latched device status (then clears it). */
 int tsdf_count(tsdf_t* t, int64_t* n_blocks, void* stream);
 
+/* Synchronises `stream`; *n_blocks = number of blocks on the visible-block
+ * list of the last tsdf_integrate call (the blocks whose voxels Eq. 2 was
+ * applied to, Sec. III-C), 0 before the first call.  For measurement: the
+ * integration stage reads and writes 16 bytes per voxel of these blocks.
+ * Returns PS_OK or PS_ERR_ARG (NULL argument); the latched status is left
+ * for tsdf_count / tsdf_status. */
+int tsdf_listed(tsdf_t* t, int64_t* n_blocks, void* stream);
+
 /* Synchronises `stream` and copies out every allocated block, in pool-slot
  * order (for a dense grid: block bx + nbx (by + nby bz)): keys (device int32, capacity x 3 block indices), D and W (device
  * float32, capacity x 512 voxels each, voxel index x + 8 y + 64 z).

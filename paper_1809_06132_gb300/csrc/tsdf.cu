@@ -764,6 +764,17 @@ extern "C" int tsdf_count(tsdf_t* t, int64_t* n_blocks, void* stream) {
     return read_status(t, s);
 }
 
+extern "C" int tsdf_listed(tsdf_t* t, int64_t* n_blocks, void* stream) {
+    clear_error();
+    PS_ARG(t != nullptr && n_blocks != nullptr, "tsdf_listed: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int n = 0;
+    PS_CUDA(cudaMemcpyAsync(&n, t->T.n_vis, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PS_CUDA(cudaStreamSynchronize(s));
+    *n_blocks = n;
+    return PS_OK;
+}
+
 // Live slots in slot order into t->T.vis (scratch outside integrate calls); returns their number.
 int live_slots(tsdf_t* t, cudaStream_t s, int64_t* n_live) {
     compact_live_kernel<<<1, 1024, 0, s>>>(t->T, t->T.vis, t->n_tmp);

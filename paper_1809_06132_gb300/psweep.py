@@ -24,7 +24,7 @@ STATUS_NAMES = {1: "PS_ERR_ARG", 2: "PS_ERR_OOM", 3: "PS_ERR_CAPACITY", 4: "PS_E
 MAX_SETS, MAX_CAMS, MAX_LEVELS = 4, 4, 2
 
 # every symbol include/psweep.h declares
-EXPORTS = ["psweep_create", "psweep_depth", "psweep_destroy", "tsdf_create", "tsdf_integrate", "tsdf_count",
+EXPORTS = ["psweep_create", "psweep_depth", "psweep_destroy", "tsdf_create", "tsdf_integrate", "tsdf_count", "tsdf_listed",
            "tsdf_extract", "tsdf_status", "tsdf_destroy", "psweep_frame_host", "psweep_profile",
            "psweep_profile_read", "tsdf_profile", "tsdf_profile_read", "tsdf_integrate_dense_static",
            "tsdf_swap_out", "tsdf_load", "tsdf_extract_points", "psbatch_create", "psbatch_run", "psbatch_timing", "psbatch_status",
@@ -131,6 +131,7 @@ def load(build_if_missing: bool = True):
     L.tsdf_create.argtypes = [C.POINTER(ps_tsdf_desc), C.POINTER(C.c_void_p)]
     L.tsdf_integrate.argtypes = [P, P, C.POINTER(ps_pose), P, P]
     L.tsdf_count.argtypes = [P, C.POINTER(C.c_int64), P]
+    L.tsdf_listed.argtypes = [P, C.POINTER(C.c_int64), P]
     L.tsdf_extract.argtypes = [P, C.c_float, P, P, P, C.c_int64, C.POINTER(C.c_int64), P]
     L.tsdf_status.argtypes = [P, P]
     L.tsdf_destroy.argtypes = [P]
@@ -604,6 +605,12 @@ class Tsdf:
     def count(self, stream=None) -> int:
         n = C.c_int64()
         _check(load().tsdf_count(self.h, C.byref(n), _stream_ptr(stream)))
+        return n.value
+
+    def listed(self, stream=None) -> int:
+        """Blocks on the last integrate call's visible-block list (tsdf_listed)."""
+        n = C.c_int64()
+        _check(load().tsdf_listed(self.h, C.byref(n), _stream_ptr(stream)))
         return n.value
 
     def status(self, stream=None) -> int:

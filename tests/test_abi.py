@@ -74,6 +74,9 @@ def test_argument_errors_without_gpu():
     assert L.tsdf_create(C.byref(td), C.byref(h)) == P.PS_ERR_ARG
     assert L.psweep_depth(None, None, None, 0, None, None, None) == P.PS_ERR_ARG
     assert L.tsdf_integrate(None, None, None, None, None) == P.PS_ERR_ARG
+    n = C.c_int64()
+    assert L.tsdf_listed(None, C.byref(n), None) == P.PS_ERR_ARG
+    assert b"tsdf_listed" in L.ps_last_error()
 
 
 def test_batch_argument_errors_without_gpu():

@@ -208,6 +208,7 @@ def test_street_full_size_parity():
     n_amb_blocks = len(amb_blocks)
     print("street full-size fusion", s, "blocks", len(gset), len(oset), "fully marked blocks", n_amb_blocks)
     assert len(gset) > 1000 and s["n_updated"] > 200000
+    assert 0 < T.listed() <= len(gset)              # the last frame's visible-block list
     # the rounding marks exempt few voxels and few whole blocks (measured:
     # 3.4% of the voxels, most of them in the 2.1% of blocks whose first
     # allocation frame is rounding-sensitive): a drift in the band logic
