@@ -675,8 +675,11 @@ __device__ __forceinline__ void pair_phase_v_(const float4* Hs, const unsigned c
         const float2 var_w = fma2(mul2(neg2(vs), dup2(1.0f / (float)N)), vs, vss);
         const float2 cov = fma2(dup2(-st[i].x), vs, vrs);
         const float2 zr = mul2(mul2(cov, dup2(st[i].y)), make_float2(rsqrt_ftz(var_w.x), rsqrt_ftz(var_w.y)));
-        const float2 z = make_float2(fminf(1.0f, fmaxf(-1.0f, zr.x)), fminf(1.0f, fmaxf(-1.0f, zr.y)));  // |ZNCC| <= 1
-        const float2 cost = fma2(dup2(-0.5f), z, dup2(0.5f));
+        // cost = (1 - z) / 2 with |ZNCC| <= 1: saturating the FMA to [0, 1] gives
+        // exactly the values of clamping z to [-1, 1] first (the ends map to
+        // 0.5 -+ 0.5 exactly), in one instruction per plane
+        const float2 cost = make_float2(__saturatef(__fmaf_rn(-0.5f, zr.x, 0.5f)),
+                                        __saturatef(__fmaf_rn(-0.5f, zr.y, 0.5f)));
         const bool ref_ok = !isnan(st[i].y);
         const bool ok0 = (!BAD || f0 == 0) && var_w.x >= (float)N * 1e-8f && ref_ok;
         const bool ok1 = (!BAD || f1 == 0) && var_w.y >= (float)N * 1e-8f && ref_ok;
@@ -1142,8 +1145,8 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
                         float var_w = fmaf(-v.x * (1.0f / (float)N), v.x, v.y);
                         float cov = fmaf(-st[i].x, v.x, v.z);
                         bool ok = v.w == 0.0f && var_w >= (float)N * 1e-8f && !isnan(st[i].y);
-                        float z = fminf(1.0f, fmaxf(-1.0f, cov * st[i].y * rsqrt_ftz(var_w)));  // |ZNCC| <= 1
-                        float cost = fmaf(-0.5f, z, 0.5f);
+                        // (1 - z) / 2 saturated to [0, 1], as in pair_phase_v_
+                        float cost = __saturatef(__fmaf_rn(-0.5f, cov * st[i].y * rsqrt_ftz(var_w), 0.5f));
                         cmin[0][i] = ok ? fminf(cmin[0][i], cost) : cmin[0][i];
                     }
                 }
