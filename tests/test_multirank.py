@@ -77,3 +77,26 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     ns = argparse.Namespace(gpus=2, steps=1, warmup=0, impl="reference", seed=0, no_cpu_baseline=True,
                             config="street", half=False, batch_size=64)
     assert bench.run_reference(ns) == 0      # rank 1: no work, exit 0
+
+
+def test_reference_arm_json_line_on_the_tiny_frame():
+    # the reference arm (the FP64 oracle on the host cores) prints one JSON
+    # line with the keys the bench contract asks for; the tiny frame keeps it
+    # to a few seconds of CPU work
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--config", "tiny",
+                        "--steps", "2", "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "frames/s" and d["value"] > 0
+    assert d["n_gpus"] == 1 and d["steps"] == 2 and d["warmup"] == 1 and d["higher_is_better"] is True
+    assert d["config"]["workload"].startswith("tiny-160x128")
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+    assert d["ms_per_step"] > 0
