@@ -721,16 +721,21 @@ __device__ __forceinline__ void pair_pass(const CamS& C, const float (&av)[9], f
 // Phase A of a two-camera step: the first camera's sample pairs at the
 // thread's halo positions, then the second's, into W2 and W2b (measured
 // faster than interleaving the cameras per position since the compiler
-// issues flush-to-zero reciprocals: street 0.766 against 0.770 ms).
+// issues flush-to-zero reciprocals: street 0.766 against 0.770 ms).  The
+// second camera's directions (TMEM address tab1) are loaded only when its
+// warp starts, so they hold no registers during the first camera's
+// (0.759 against 0.766 ms).
 template <int RHO, bool HALF, int TH>
-__device__ __forceinline__ int pair_phase_a2(const CamS& C0, const CamS& C1, const float (&av0)[9], const float (&av1)[9],
+__device__ __forceinline__ int pair_phase_a2(const CamS& C0, const CamS& C1, const float (&av0)[9], uint32_t tab1,
                                              float d0, float d1, float2* W2, float2* W2b, int t0) {
     using G = Geo<RHO, TH, 2>;
     constexpr int HWL = G::HWL, WS2 = G::WS2, NPOS = G::NPOS;
     constexpr int NP = (NPOS + NT - 1) / NT;
     int bad = 0;
+    float av1[9];  // the second camera's directions, loaded once the first camera's warp is done
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
+        if (c == 1) tm_ld9(tab1, av1);
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
             int p = t0 + i * NT;
@@ -738,7 +743,7 @@ __device__ __forceinline__ int pair_phase_a2(const CamS& C0, const CamS& C1, con
             int hy = p / HWL, hx = p - hy * HWL;
             {
                 const CamS& C = c ? C1 : C0;
-                const float (&av)[9] = c ? av1 : av0;
+                const float* av = c ? static_cast<const float*>(av1) : static_cast<const float*>(av0);
                 const float4 a = make_float4(av[3 * i], av[3 * i + 1], av[3 * i + 2], 0.f);
                 float2 w = warp_sample2<HALF>(C, make_float2(fmaf(d0, a.x, C.t[0]), fmaf(d1, a.x, C.t[0])),
                                               make_float2(fmaf(d0, a.y, C.t[1]), fmaf(d1, a.y, C.t[1])),
@@ -751,7 +756,7 @@ __device__ __forceinline__ int pair_phase_a2(const CamS& C0, const CamS& C1, con
 }
 
 template <int RHO, bool HALF, int TH>
-__device__ __forceinline__ void pair_pass2(const CamS& C0, const CamS& C1, const float (&av0)[9], const float (&av1)[9],
+__device__ __forceinline__ void pair_pass2(const CamS& C0, const CamS& C1, const float (&av0)[9], uint32_t tab1,
                                            float d0, float d1, float2* W2, const float* Rs, float4* Hs,
                                            unsigned char* Fs, const float2 (&st)[TH / 8], int base_v, int base_f,
                                            float (&cmin0)[TH / 8], float (&cmin1)[TH / 8]) {
@@ -759,7 +764,7 @@ __device__ __forceinline__ void pair_pass2(const CamS& C0, const CamS& C1, const
     const int tid = threadIdx.x;
     float2* W2b = W2 + G::WSZ / 2;
     float4* Hsb = Hs + G::HCAM4;
-    int bad = pair_phase_a2<RHO, HALF, TH>(C0, C1, av0, av1, d0, d1, W2, W2b, tid);
+    int bad = pair_phase_a2<RHO, HALF, TH>(C0, C1, av0, tab1, d0, d1, W2, W2b, tid);
     bad = __syncthreads_or(bad);
     const int hrow = tid & 31, hrun = tid >> 5;
     pair_phase_h<RHO, TH, 2>(W2, Rs, Hs, Fs, hrow, hrun, bad);
@@ -1051,9 +1056,7 @@ __device__ inline void sweep_tile(const LevelD& L, const CamS* cams, int item, u
                 const float d1 = dtab ? Ds[k0 + np - 1 - k_lo] : __ldg(&L.planes[k0 + np - 1].d);
                 if constexpr (KP == 2) {
                     if (j + 1 < L.n_cams) {  // two cameras in one step
-                        float av1[9];
-                        tm_ld9(tm + TM_TAB + 9 * (j + 1), av1);
-                        pair_pass2<RHO, HALF, TH>(C, cams[j + 1], av, av1, d0, d1, W2, Rs, Hs, Fs, st, base_v,
+                        pair_pass2<RHO, HALF, TH>(C, cams[j + 1], av, tm + TM_TAB + 9 * (j + 1), d0, d1, W2, Rs, Hs, Fs, st, base_v,
                                                   base_f, cmin[0], cmin[1]);
                     } else {
                         pair_pass<RHO, HALF, TH>(C, av, d0, d1, W2, Rs, Hs, Fs, st, base_v, base_f, cmin[0], cmin[1]);
